@@ -1,0 +1,318 @@
+/*
+ * Sector-signature carving oracle: a plain, slow, obviously correct CPU implementation.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path (the CUDA library and its Python
+ * binding) links, loads or calls this file. Only the test suite, the package's smoke check
+ * and the benchmark's CPU-baseline leg do. It shares no code, header, table or constant
+ * generator with the CUDA path.
+ *
+ * What it computes (paper, Section 1 and Section 3.1, "alerts the host ... byte-for-byte
+ * comparison"): given master files and a disk image, every triple (i, f, s) such that disk
+ * sector i is byte-for-byte equal to sector s of master file f, sorted lexicographically.
+ *
+ *   - A sector is 512 bytes (Section 2). Only whole sectors count: a master file's partial
+ *     tail and an image's trailing partial sector are ignored.
+ *   - A master sector whose 512 bytes are all equal (all zero, or one byte repeated) is
+ *     excluded from the master set. The paper has no such rule; the library applies the
+ *     same one, so both sides agree on it.
+ *
+ * Two matchers:
+ *   oracle_match_brute  - the definition itself: memcmp of every disk sector against every
+ *                         kept master sector. Tiny inputs only. Parity pinned by construction.
+ *   oracle_match_hash   - the method's route (Section 3.1): a signature per master sector,
+ *                         the disk sector's signature looked up among them, equal signatures
+ *                         reported. The signature is MD5 (Section 2.1, RFC 1321) over the
+ *                         512-byte sector with standard padding (9 compressions). The lookup
+ *                         is a sorted array + binary search (the paper's Section 4.2 names
+ *                         binary search as an alternative to its hash tables); the table
+ *                         layout does not change the result.
+ *
+ * MD5 (oracle_md5) follows the prose of RFC 1321 Section 3: pad with one 1-bit then zeros to
+ * 448 mod 512 bits, append the 64-bit little-endian bit length, then for every 512-bit block
+ * run four rounds of sixteen operations a = b + ((a + F(b,c,d) + X[k] + T[i]) <<< s), where
+ * T[i] is the integer part of 4294967296 * |sin(i)| (i in radians, i = 1..64), computed here
+ * at first use in double precision. Parity is pinned by the test suite against two
+ * independent MD5 implementations (Python's hashlib, backed by OpenSSL, and the md5sum tool).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define SECTOR 512u
+
+typedef struct {
+  uint64_t disk_sector;
+  uint32_t file_id;
+  uint32_t file_sector;
+} oracle_triple;
+
+/* ---------------------------------------------------------------- MD5, RFC 1321 Section 3 */
+
+static uint32_t T_sine[65]; /* 1-based, as in the RFC */
+static int T_ready = 0;
+
+static void md5_init_table(void) {
+  if (T_ready) return;
+  for (int i = 1; i <= 64; i++) T_sine[i] = (uint32_t)floor(4294967296.0 * fabs(sin((double)i)));
+  T_ready = 1;
+}
+
+/* Per-round left-rotation amounts s (RFC 1321 Section 3.4, each round cycles four amounts). */
+static const int rot_amount[4][4] = {{7, 12, 17, 22}, {5, 9, 14, 20}, {4, 11, 16, 23}, {6, 10, 15, 21}};
+
+static uint32_t rotl32(uint32_t x, int s) { return (x << s) | (x >> (32 - s)); }
+
+static uint32_t aux_F(uint32_t x, uint32_t y, uint32_t z) { return (x & y) | (~x & z); }
+static uint32_t aux_G(uint32_t x, uint32_t y, uint32_t z) { return (x & z) | (y & ~z); }
+static uint32_t aux_H(uint32_t x, uint32_t y, uint32_t z) { return x ^ y ^ z; }
+static uint32_t aux_I(uint32_t x, uint32_t y, uint32_t z) { return y ^ (x | ~z); }
+
+/* Process one 64-byte block into the state ABCD (RFC 1321 Section 3.4). */
+static void md5_block(uint32_t st[4], const uint8_t blk[64]) {
+  uint32_t X[16];
+  for (int j = 0; j < 16; j++)
+    X[j] = (uint32_t)blk[4 * j] | ((uint32_t)blk[4 * j + 1] << 8) | ((uint32_t)blk[4 * j + 2] << 16) |
+           ((uint32_t)blk[4 * j + 3] << 24);
+  uint32_t a = st[0], b = st[1], c = st[2], d = st[3];
+  for (int i = 0; i < 64; i++) {
+    int round = i / 16, j = i % 16;
+    uint32_t f;
+    int k;
+    switch (round) {
+      case 0: f = aux_F(b, c, d); k = j; break;                 /* X[0], X[1], ... X[15]   */
+      case 1: f = aux_G(b, c, d); k = (1 + 5 * j) % 16; break;  /* X[1], X[6], X[11], ...  */
+      case 2: f = aux_H(b, c, d); k = (5 + 3 * j) % 16; break;  /* X[5], X[8], X[11], ...  */
+      default: f = aux_I(b, c, d); k = (7 * j) % 16; break;     /* X[0], X[7], X[14], ...  */
+    }
+    uint32_t t = b + rotl32(a + f + X[k] + T_sine[i + 1], rot_amount[round][j % 4]);
+    /* the operation updates a; the four registers then rotate roles (a,b,c,d) <- (d,a,b,c) */
+    a = d;
+    d = c;
+    c = b;
+    b = t;
+  }
+  st[0] += a;
+  st[1] += b;
+  st[2] += c;
+  st[3] += d;
+}
+
+/* MD5 of an arbitrary byte string (RFC 1321 Sections 3.1-3.5). */
+void oracle_md5(const uint8_t* msg, uint64_t len, uint8_t out[16]) {
+  md5_init_table();
+  uint32_t st[4] = {0x67452301u, 0xefcdab89u, 0x98badcfeu, 0x10325476u}; /* Section 3.3 */
+  uint64_t full = len / 64;
+  for (uint64_t b = 0; b < full; b++) md5_block(st, msg + 64 * b);
+  /* Sections 3.1 and 3.2: the tail, a single 1 bit, zeros to 56 mod 64 bytes, bit length LE */
+  uint8_t tail[128];
+  memset(tail, 0, sizeof tail);
+  uint64_t rem = len - 64 * full;
+  memcpy(tail, msg + 64 * full, (size_t)rem);
+  tail[rem] = 0x80;
+  uint64_t tail_len = (rem < 56) ? 64 : 128;
+  uint64_t bits = len * 8u;
+  for (int j = 0; j < 8; j++) tail[tail_len - 8 + j] = (uint8_t)(bits >> (8 * j));
+  md5_block(st, tail);
+  if (tail_len == 128) md5_block(st, tail + 64);
+  for (int j = 0; j < 4; j++)
+    for (int q = 0; q < 4; q++) out[4 * j + q] = (uint8_t)(st[j] >> (8 * q)); /* Section 3.5 */
+}
+
+/* MD5 of n consecutive 512-byte sectors; out holds 16 bytes per sector. */
+void oracle_md5_sectors(const uint8_t* data, uint64_t n_sectors, uint8_t* out) {
+  md5_init_table();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < (int64_t)n_sectors; i++) oracle_md5(data + (uint64_t)i * SECTOR, SECTOR, out + 16 * i);
+}
+
+/* ------------------------------------------------------------------ the exclusion rule */
+
+/* A master sector is excluded iff all 512 of its bytes are equal. */
+int oracle_sector_trivial(const uint8_t* sector) {
+  for (uint32_t j = 1; j < SECTOR; j++)
+    if (sector[j] != sector[0]) return 0;
+  return 1;
+}
+
+/* ---------------------------------------------------------------- shared result helpers */
+
+static int triple_cmp(const void* pa, const void* pb) {
+  const oracle_triple* a = (const oracle_triple*)pa;
+  const oracle_triple* b = (const oracle_triple*)pb;
+  if (a->disk_sector != b->disk_sector) return a->disk_sector < b->disk_sector ? -1 : 1;
+  if (a->file_id != b->file_id) return a->file_id < b->file_id ? -1 : 1;
+  if (a->file_sector != b->file_sector) return a->file_sector < b->file_sector ? -1 : 1;
+  return 0;
+}
+
+/* ------------------------------------------------------------- brute force (definition) */
+
+/* Every (i, f, s) with disk sector i byte-equal to kept master sector s of file f, sorted.
+ * Returns the number of triples; writes at most cap of them into out. */
+int64_t oracle_match_brute(const uint8_t* image, uint64_t image_bytes, const uint8_t* const* files,
+                           const uint64_t* file_bytes, uint32_t n_files, oracle_triple* out, uint64_t cap) {
+  uint64_t n_disk = image_bytes / SECTOR;
+  uint64_t n = 0;
+  for (uint64_t i = 0; i < n_disk; i++) {
+    const uint8_t* d = image + i * SECTOR;
+    for (uint32_t f = 0; f < n_files; f++) {
+      uint64_t n_fs = file_bytes[f] / SECTOR;
+      for (uint64_t s = 0; s < n_fs; s++) {
+        const uint8_t* m = files[f] + s * SECTOR;
+        if (oracle_sector_trivial(m)) continue;
+        if (memcmp(d, m, SECTOR) != 0) continue;
+        if (n < cap) {
+          out[n].disk_sector = i;
+          out[n].file_id = f;
+          out[n].file_sector = (uint32_t)s;
+        }
+        n++;
+      }
+    }
+  }
+  if (n <= cap) qsort(out, (size_t)n, sizeof(oracle_triple), triple_cmp);
+  return (int64_t)n;
+}
+
+/* ------------------------------------------------------ signature lookup (the method) */
+
+typedef struct {
+  uint8_t digest[16];
+  uint32_t file_id;
+  uint32_t file_sector;
+} db_entry;
+
+typedef struct {
+  db_entry* e;
+  uint64_t n;
+} oracle_db;
+
+static int db_cmp(const void* pa, const void* pb) {
+  const db_entry* a = (const db_entry*)pa;
+  const db_entry* b = (const db_entry*)pb;
+  int c = memcmp(a->digest, b->digest, 16);
+  if (c) return c;
+  if (a->file_id != b->file_id) return a->file_id < b->file_id ? -1 : 1;
+  if (a->file_sector != b->file_sector) return a->file_sector < b->file_sector ? -1 : 1;
+  return 0;
+}
+
+/* The signature database: one (MD5, f, s) entry per kept master sector, sorted. */
+oracle_db* oracle_db_build(const uint8_t* const* files, const uint64_t* file_bytes, uint32_t n_files) {
+  md5_init_table();
+  uint64_t total = 0;
+  for (uint32_t f = 0; f < n_files; f++) total += file_bytes[f] / SECTOR;
+  oracle_db* db = (oracle_db*)calloc(1, sizeof(oracle_db));
+  if (!db) return NULL;
+  db->e = (db_entry*)malloc(sizeof(db_entry) * (total ? total : 1));
+  if (!db->e) {
+    free(db);
+    return NULL;
+  }
+  uint64_t n = 0;
+  for (uint32_t f = 0; f < n_files; f++) {
+    uint64_t n_fs = file_bytes[f] / SECTOR;
+    for (uint64_t s = 0; s < n_fs; s++) {
+      const uint8_t* m = files[f] + s * SECTOR;
+      if (oracle_sector_trivial(m)) continue;
+      db->e[n].file_id = f;
+      db->e[n].file_sector = (uint32_t)s;
+      n++;
+    }
+  }
+  /* hash in parallel; every entry is independent */
+#pragma omp parallel for schedule(static)
+  for (int64_t q = 0; q < (int64_t)n; q++)
+    oracle_md5(files[db->e[q].file_id] + (uint64_t)db->e[q].file_sector * SECTOR, SECTOR, db->e[q].digest);
+  qsort(db->e, (size_t)n, sizeof(db_entry), db_cmp);
+  db->n = n;
+  return db;
+}
+
+uint64_t oracle_db_size(const oracle_db* db) { return db->n; }
+
+void oracle_db_free(oracle_db* db) {
+  if (!db) return;
+  free(db->e);
+  free(db);
+}
+
+/* First entry whose digest is >= key (binary search over the sorted database). */
+static uint64_t db_lower_bound(const oracle_db* db, const uint8_t key[16]) {
+  uint64_t lo = 0, hi = db->n;
+  while (lo < hi) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if (memcmp(db->e[mid].digest, key, 16) < 0)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+/* Look up n_sectors consecutive disk sectors whose first one has index first_index. Every
+ * triple found is written (at most cap) and the total is returned, sorted. */
+int64_t oracle_db_lookup(const oracle_db* db, const uint8_t* sectors, uint64_t n_sectors, uint64_t first_index,
+                         oracle_triple* out, uint64_t cap) {
+  uint64_t* lo = (uint64_t*)malloc(sizeof(uint64_t) * (n_sectors ? n_sectors : 1));
+  uint64_t* cnt = (uint64_t*)malloc(sizeof(uint64_t) * (n_sectors ? n_sectors : 1));
+  if (!lo || !cnt) {
+    free(lo);
+    free(cnt);
+    return -1;
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < (int64_t)n_sectors; i++) {
+    uint8_t dg[16];
+    oracle_md5(sectors + (uint64_t)i * SECTOR, SECTOR, dg);
+    uint64_t a = db_lower_bound(db, dg), b = a;
+    while (b < db->n && memcmp(db->e[b].digest, dg, 16) == 0) b++;
+    lo[i] = a;
+    cnt[i] = b - a;
+  }
+  uint64_t n = 0;
+  for (uint64_t i = 0; i < n_sectors; i++)
+    for (uint64_t q = 0; q < cnt[i]; q++) {
+      if (n < cap) {
+        out[n].disk_sector = first_index + i;
+        out[n].file_id = db->e[lo[i] + q].file_id;
+        out[n].file_sector = db->e[lo[i] + q].file_sector;
+      }
+      n++;
+    }
+  free(lo);
+  free(cnt);
+  if (n <= cap) qsort(out, (size_t)n, sizeof(oracle_triple), triple_cmp);
+  return (int64_t)n;
+}
+
+/* The whole method over one image: database, lookup of every whole sector, sorted result. */
+int64_t oracle_match_hash(const uint8_t* image, uint64_t image_bytes, const uint8_t* const* files,
+                          const uint64_t* file_bytes, uint32_t n_files, oracle_triple* out, uint64_t cap) {
+  oracle_db* db = oracle_db_build(files, file_bytes, n_files);
+  if (!db) return -1;
+  int64_t n = oracle_db_lookup(db, image, image_bytes / SECTOR, 0, out, cap);
+  oracle_db_free(db);
+  return n;
+}
+
+/* Threads the parallel loops use (1 when built without OpenMP). */
+int oracle_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}

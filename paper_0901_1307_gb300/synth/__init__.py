@@ -1,0 +1,305 @@
+"""Seeded synthetic workloads: disk images and master files shaped like the paper's data.
+
+Input generation only (no signature, table or matching arithmetic), shared by the tests, the
+CPU oracle's inputs and the benchmark. Every byte is defined once in ``synth_def.h`` and produced
+either on the host (``synth_host.c``, gcc) or on the device (``synth_cuda.cu``, nvcc); the two are
+byte-identical, which the GPU tests check.
+
+The paper scans disks whose 4 KiB clusters (8 sectors of 512 bytes, Section 2) may hold
+fragments of known files; its experiments use random-data files (Section 4). A ``Plan`` places
+a fraction of each master file's clusters at distinct cluster-aligned image positions, and
+overwrites the first 1-4 sectors of some of them with fresh bytes (a newer file reusing the
+cluster, Section 2). Every other sector is background: 70% random, 15% zero, 15% text.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+SECTOR = 512
+CLUSTER = 8
+TRIPLE_DTYPE = np.dtype([("disk_sector", "<u8"), ("file_id", "<u4"), ("file_sector", "<u4")])
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_HOST_SRC = os.path.join(_HERE, "synth_host.c")
+_CUDA_SRC = os.path.join(_HERE, "synth_cuda.cu")
+_DEF = os.path.join(_HERE, "synth_def.h")
+_HOST_LIB = os.path.join(_HERE, "libcvsynth.so")
+_CUDA_LIB = os.path.join(_HERE, "libcvsynth_cuda.so")
+_lock = threading.Lock()
+_host = None
+_cuda = None
+
+
+def _stale(lib: str, srcs) -> bool:
+    if not os.path.exists(lib):
+        return True
+    t = os.path.getmtime(lib)
+    return any(os.path.getmtime(s) > t for s in srcs)
+
+
+def build_host(force: bool = False) -> str:
+    if force or _stale(_HOST_LIB, [_HOST_SRC, _DEF]):
+        tmp = _HOST_LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-shared", "-fPIC", "-std=c11", "-fopenmp", _HOST_SRC, "-o", tmp]
+        try:
+            subprocess.run(cmd, check=True, capture_output=True)
+        except subprocess.CalledProcessError:
+            cmd.remove("-fopenmp")
+            subprocess.run(cmd, check=True, capture_output=True)
+        os.replace(tmp, _HOST_LIB)
+    return _HOST_LIB
+
+
+def build_cuda(force: bool = False, nvcc: str = "nvcc") -> str:
+    if force or _stale(_CUDA_LIB, [_CUDA_SRC, _DEF]):
+        tmp = _CUDA_LIB + f".tmp{os.getpid()}"
+        cmd = [nvcc, "-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+               "-gencode", "arch=compute_103a,code=sm_103a", _CUDA_SRC, "-o", tmp]
+        subprocess.run(cmd, check=True, capture_output=True)
+        os.replace(tmp, _CUDA_LIB)
+    return _CUDA_LIB
+
+
+def _host_lib():
+    global _host
+    with _lock:
+        if _host is None:
+            lib = ctypes.CDLL(build_host())
+            vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+            lib.synth_vocab.argtypes = [u64, vp]
+            lib.synth_image.argtypes = [u64, u64, vp, vp, vp, u64, vp, vp, u64, u64, vp]
+            lib.synth_master.argtypes = [u64, u32, u32, u32, vp]
+            lib.synth_random.argtypes = [u64, u64, u64, u64, vp]
+            lib.synth_hash.argtypes = [u64, u64, u64, u64]
+            lib.synth_hash.restype = u64
+            for f in (lib.synth_vocab, lib.synth_image, lib.synth_master, lib.synth_random):
+                f.restype = None
+            _host = lib
+        return _host
+
+
+def _cuda_lib():
+    global _cuda
+    with _lock:
+        if _cuda is None:
+            lib = ctypes.CDLL(build_cuda())
+            vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+            lib.synth_image_cuda.argtypes = [u64, u64, vp, vp, vp, u64, vp, vp, u64, u64, vp, vp]
+            lib.synth_image_cuda.restype = ctypes.c_int
+            lib.synth_masters_cuda.argtypes = [u64, vp, u32, u64, vp, vp]
+            lib.synth_masters_cuda.restype = ctypes.c_int
+            _cuda = lib
+        return _cuda
+
+
+def sy_hash(seed: int, stream: int, a: int, b: int) -> int:
+    return int(_host_lib().synth_hash(seed, stream, a, b))
+
+
+def vocab(sigma: int) -> np.ndarray:
+    out = np.zeros(2000 * 16, np.uint8)
+    _host_lib().synth_vocab(sigma, out.ctypes.data)
+    return out
+
+
+def random_sectors(seed: int, n: int, first: int = 0, stream: int = 99) -> np.ndarray:
+    """n fresh random sectors (uint8, n*512) that no master or image stream produces."""
+    out = np.zeros(n * SECTOR, np.uint8)
+    if n:
+        _host_lib().synth_random(seed, stream, first, n, out.ctypes.data)
+    return out
+
+
+@dataclasses.dataclass
+class Plan:
+    """One synthetic image and its master set."""
+
+    image_seed: int
+    master_seed: int
+    n_sectors: int
+    file_nsect: np.ndarray      # uint32 [n_files]: whole sectors per master file
+    plant_file: np.ndarray      # int32 [n_clusters]: planted file id or -1
+    plant_fcluster: np.ndarray  # uint32 [n_clusters]
+    plant_over: np.ndarray      # uint8 [n_clusters]: leading sectors overwritten
+
+    @property
+    def n_files(self) -> int:
+        return int(self.file_nsect.size)
+
+    @property
+    def n_master_sectors(self) -> int:
+        return int(self.file_nsect.sum(dtype=np.uint64))
+
+    @property
+    def n_bytes(self) -> int:
+        return self.n_sectors * SECTOR
+
+    def file_base(self) -> np.ndarray:
+        base = np.zeros(self.n_files + 1, np.uint64)
+        np.cumsum(self.file_nsect, dtype=np.uint64, out=base[1:])
+        return base
+
+    # ------------------------------------------------------------------ host generation
+    def _args(self):
+        self._vocab = vocab(self.image_seed)
+        return (self.image_seed, self.master_seed, self.plant_file.ctypes.data, self.plant_fcluster.ctypes.data,
+                self.plant_over.ctypes.data, self.plant_file.size, self.file_nsect.ctypes.data,
+                self._vocab.ctypes.data)
+
+    def image_host(self, first: int = 0, n: int | None = None) -> np.ndarray:
+        """Image sectors [first, first+n) as uint8 (n*512)."""
+        if n is None:
+            n = self.n_sectors - first
+        out = np.zeros(n * SECTOR, np.uint8)
+        if n:
+            _host_lib().synth_image(*self._args(), first, n, out.ctypes.data)
+        return out
+
+    def master_host(self, f: int, s0: int = 0, n: int | None = None) -> np.ndarray:
+        if n is None:
+            n = int(self.file_nsect[f]) - s0
+        out = np.zeros(n * SECTOR, np.uint8)
+        if n:
+            _host_lib().synth_master(self.master_seed, f, s0, n, out.ctypes.data)
+        return out
+
+    def masters_host(self) -> list:
+        """Every master file as a uint8 array (whole sectors)."""
+        return [self.master_host(f) for f in range(self.n_files)]
+
+    # ---------------------------------------------------------------- device generation
+    def image_device(self, out_ptr: int, first: int = 0, n: int | None = None, stream: int = 0,
+                     dev_plan=None) -> None:
+        """Write image sectors [first, first+n) to device memory at out_ptr (8-byte aligned).
+
+        dev_plan is the tuple returned by ``device_plan`` (device copies of the plan arrays,
+        kept alive by the caller)."""
+        if n is None:
+            n = self.n_sectors - first
+        pf, pc, po, fn, vc = dev_plan
+        rc = _cuda_lib().synth_image_cuda(self.image_seed, self.master_seed, pf, pc, po, self.plant_file.size,
+                                          fn, vc, first, n, out_ptr, stream)
+        if rc != 0:
+            raise RuntimeError(f"synth_image_cuda failed: cuda error {rc}")
+
+    def masters_device(self, out_ptr: int, file_base_ptr: int, stream: int = 0) -> None:
+        """All master files concatenated (file order, whole sectors) into device memory."""
+        rc = _cuda_lib().synth_masters_cuda(self.master_seed, file_base_ptr, self.n_files,
+                                            self.n_master_sectors, out_ptr, stream)
+        if rc != 0:
+            raise RuntimeError(f"synth_masters_cuda failed: cuda error {rc}")
+
+    # --------------------------------------------------------------------- plant log
+    def planted(self) -> np.ndarray:
+        """Image cluster indices that carry a planted master cluster."""
+        return np.nonzero(self.plant_file >= 0)[0]
+
+    def expected_intact(self) -> np.ndarray:
+        """Every planted master sector that survived the overwrites, as sorted triples.
+
+        This is a subset of the match result (exactly the result when master sectors are
+        random and unique, as in every configuration here)."""
+        q = self.planted()
+        if q.size == 0:
+            return np.zeros(0, TRIPLE_DTYPE)
+        f = self.plant_file[q].astype(np.int64)
+        c = self.plant_fcluster[q].astype(np.int64)
+        ov = self.plant_over[q].astype(np.int64)
+        k = np.arange(CLUSTER, dtype=np.int64)
+        s = c[:, None] * CLUSTER + k[None, :]
+        i = q.astype(np.int64)[:, None] * CLUSTER + k[None, :]
+        keep = (k[None, :] >= ov[:, None]) & (s < self.file_nsect[f][:, None].astype(np.int64)) & (i < self.n_sectors)
+        out = np.zeros(int(keep.sum()), TRIPLE_DTYPE)
+        out["disk_sector"] = i[keep]
+        out["file_id"] = np.broadcast_to(f[:, None], s.shape)[keep]
+        out["file_sector"] = s[keep]
+        out.sort(order=["disk_sector", "file_id", "file_sector"])
+        return out
+
+
+def make_plan(image_seed: int, n_sectors: int, file_nsect, plant_frac: float, overwrite_frac: float = 0.10,
+              master_seed: int | None = None, plan_seed: int | None = None) -> Plan:
+    """Place round(plant_frac * clusters) clusters of every master file at distinct, uniformly
+    drawn cluster-aligned image positions; overwrite the first 1-4 sectors of
+    round(overwrite_frac * planted) of them."""
+    file_nsect = np.asarray(file_nsect, dtype=np.uint32)
+    master_seed = image_seed + 0x5EED if master_seed is None else master_seed
+    rng = np.random.default_rng([image_seed, 0xC1A5] if plan_seed is None else plan_seed)
+    n_clusters = (n_sectors + CLUSTER - 1) // CLUSTER
+    files, fcl = [], []
+    for f, ns in enumerate(file_nsect.tolist()):
+        nc = (ns + CLUSTER - 1) // CLUSTER
+        k = int(round(plant_frac * nc))
+        if k:
+            chosen = np.sort(rng.choice(nc, size=k, replace=False))
+            files.append(np.full(k, f, np.int32))
+            fcl.append(chosen.astype(np.uint32))
+    plant_file = np.full(n_clusters, -1, np.int32)
+    plant_fcluster = np.zeros(n_clusters, np.uint32)
+    plant_over = np.zeros(n_clusters, np.uint8)
+    if files:
+        pf = np.concatenate(files)
+        pc = np.concatenate(fcl)
+        P = pf.size
+        if P > n_clusters:
+            raise ValueError(f"{P} planted clusters do not fit in {n_clusters} image clusters")
+        slots = rng.choice(n_clusters, size=P, replace=False)
+        plant_file[slots] = pf
+        plant_fcluster[slots] = pc
+        n_over = int(round(overwrite_frac * P))
+        if n_over:
+            which = rng.choice(P, size=n_over, replace=False)
+            plant_over[slots[which]] = rng.integers(1, 5, size=n_over).astype(np.uint8)
+    return Plan(image_seed, master_seed, n_sectors, file_nsect, plant_file, plant_fcluster, plant_over)
+
+
+def log_uniform_sizes(rng, n: int, lo_bytes: int, hi_bytes: int) -> np.ndarray:
+    return np.exp(rng.uniform(np.log(lo_bytes), np.log(hi_bytes), size=n))
+
+
+def scale_to_total(sizes_sectors: np.ndarray, total: int, min_sectors: int) -> np.ndarray:
+    """Scale sizes by a common factor so they sum exactly to ``total`` whole sectors."""
+    s = np.maximum(np.round(sizes_sectors * (total / sizes_sectors.sum())), min_sectors).astype(np.int64)
+    diff = total - int(s.sum())
+    order = np.argsort(-s)
+    i = 0
+    while diff != 0:
+        j = order[i % s.size]
+        step = 1 if diff > 0 else -1
+        if s[j] + step >= min_sectors:
+            s[j] += step
+            diff -= step
+        i += 1
+    return s.astype(np.uint32)
+
+
+def config_plan(name: str) -> Plan:
+    """The named workloads.
+
+    tiny  : 64 MiB image (131,072 sectors), seed 0; 150 master files of uniform 16-256 KiB
+            (32-512 sectors); 40% of each file's clusters planted, 10% of those partly overwritten.
+    scale : 32 GiB image (67,108,864 sectors), seed 1; 20,000 master files with log-uniform
+            8 KiB-1 MiB sizes scaled to 4,194,304 sectors in total (minimum 16); 25% planted.
+    """
+    if name == "tiny":
+        rng = np.random.default_rng(0)
+        nsect = rng.integers(32, 513, size=150)
+        return make_plan(0, 131072, nsect, 0.40)
+    if name == "scale":
+        rng = np.random.default_rng(1)
+        raw = log_uniform_sizes(rng, 20000, 8 << 10, 1 << 20) / SECTOR
+        nsect = scale_to_total(raw, 4194304, 16)
+        return make_plan(1, 67108864, nsect, 0.25)
+    if name.startswith("small:"):
+        # small:<sectors>:<files>:<seed> -- a scaled-down image for fast tests
+        _, ns, nf, seed = name.split(":")
+        rng = np.random.default_rng(int(seed))
+        nsect = rng.integers(16, 129, size=int(nf))
+        return make_plan(int(seed), int(ns), nsect, 0.40)
+    raise KeyError(name)

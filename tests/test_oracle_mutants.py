@@ -1,0 +1,93 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of ``oracle/oracle.c`` (a dropped term, a wrong index, a
+wrong constant, a wrong comparison), builds that copy on the CPU, and checks that at least one
+pin of tests/test_oracle.py fails against it. The real oracle is never modified.
+"""
+import ctypes
+import hashlib
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from test_oracle import as_list, py_match, tricky_case
+
+MUTANTS = {
+    "rotation amount": ("{7, 12, 17, 22}", "{7, 12, 17, 21}"),
+    "round-2 message index": ("(1 + 5 * j) % 16", "(5 * j) % 16"),
+    "round-3 message index": ("(5 + 3 * j) % 16", "(3 + 5 * j) % 16"),
+    "round-3 function": ("return x ^ y ^ z;", "return x ^ y ^ ~z;"),
+    "round-4 function": ("return y ^ (x | ~z);", "return y ^ (x | z);"),
+    "round-1 function": ("return (x & y) | (~x & z);", "return (x & y) | (x & z);"),
+    "sine index": ("T_sine[i + 1]", "T_sine[i]"),
+    "sine scale": ("4294967296.0 * fabs", "4294967295.0 * fabs"),
+    "padding boundary": ("(rem < 56) ? 64 : 128", "(rem <= 56) ? 64 : 128"),
+    "length in bytes not bits": ("uint64_t bits = len * 8u;", "uint64_t bits = len;"),
+    "feed-forward dropped": ("st[3] += d;", "st[3] = d;"),
+    "register roles": ("c = b;\n    b = t;", "c = t;\n    b = b;"),
+    "big-endian words": ("(uint32_t)blk[4 * j] | ((uint32_t)blk[4 * j + 1] << 8)",
+                         "(uint32_t)blk[4 * j + 1] | ((uint32_t)blk[4 * j] << 8)"),
+    "initial state": ("0x98badcfeu", "0x98badcffu"),
+    "trivial rule only zero": ("if (sector[j] != sector[0]) return 0;", "if (sector[j] != 0) return 0;"),
+    "trivial rule off": ("for (uint32_t j = 1; j < SECTOR; j++)\n    if (sector[j] != sector[0]) return 0;\n  return 1;",
+                         "return 0;"),
+    "first equal digest only": ("while (b < db->n && memcmp(db->e[b].digest, dg, 16) == 0) b++;",
+                                "if (b < db->n && memcmp(db->e[b].digest, dg, 16) == 0) b++;"),
+    "sort by file descending": ("if (a->file_id != b->file_id) return a->file_id < b->file_id ? -1 : 1;\n  if (a->file_sector != b->file_sector) return a->file_sector < b->file_sector ? -1 : 1;\n  return 0;\n}\n\n/* ------------------------------------------------------------- brute",
+                                "if (a->file_id != b->file_id) return a->file_id > b->file_id ? -1 : 1;\n  if (a->file_sector != b->file_sector) return a->file_sector < b->file_sector ? -1 : 1;\n  return 0;\n}\n\n/* ------------------------------------------------------------- brute"),
+    "window offset dropped": ("out[n].disk_sector = first_index + i;", "out[n].disk_sector = i;"),
+    "last master sector dropped": ("uint64_t n_fs = file_bytes[f] / SECTOR;\n    for (uint64_t s = 0; s < n_fs; s++) {\n      const uint8_t* m = files[f] + s * SECTOR;\n      if (oracle_sector_trivial(m)) continue;\n      db",
+                                   "uint64_t n_fs = file_bytes[f] / SECTOR;\n    if (n_fs) n_fs--;\n    for (uint64_t s = 0; s < n_fs; s++) {\n      const uint8_t* m = files[f] + s * SECTOR;\n      if (oracle_sector_trivial(m)) continue;\n      db"),
+}
+
+
+def _build_mutant(src: str, old: str, new: str, td: str) -> str:
+    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    path = os.path.join(td, "m.c")
+    with open(path, "w") as fh:
+        fh.write(src.replace(old, new))
+    lib = os.path.join(td, "libm.so")
+    subprocess.run(["gcc", "-O1", "-shared", "-fPIC", "-std=c11", path, "-o", lib, "-lm"], check=True,
+                   capture_output=True)
+    return lib
+
+
+def _pins_pass() -> bool:
+    """The pins of tests/test_oracle.py, condensed; False as soon as one fails."""
+    rng = np.random.default_rng(5)
+    for length in (0, 1, 55, 56, 63, 64, 100, 512, 1000):
+        d = rng.integers(0, 256, length, dtype=np.uint8).tobytes()
+        if oracle.md5(d) != hashlib.md5(d).digest():
+            return False
+    for seed in range(4):
+        image, files = tricky_case(seed)
+        want = py_match(image.tobytes(), [f.tobytes() for f in files])
+        if as_list(oracle.match_brute(image, files)) != want:
+            return False
+        if as_list(oracle.match_hash(image, files)) != want:
+            return False
+        db = oracle.OracleDB(files)
+        part = as_list(db.lookup(image[3 * 512:20 * 512], 3))
+        db.close()
+        if part != [t for t in want if 3 <= t[0] < 20]:
+            return False
+    return True
+
+
+def test_real_oracle_passes_condensed_pins():
+    assert _pins_pass()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, monkeypatch):
+    with open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")) as fh:
+        src = fh.read()
+    old, new = MUTANTS[name]
+    with tempfile.TemporaryDirectory() as td:
+        lib = oracle.bind(ctypes.CDLL(_build_mutant(src, old, new, td)))
+        monkeypatch.setattr(oracle, "_lib", lib)
+        assert not _pins_pass(), f"mutant '{name}' passed every pin"
