@@ -1,0 +1,170 @@
+/*
+ * cv.h -- C ABI of the GB300 sector-signature carving library (libcv.so).
+ *
+ * The operation (paper Section 1 and Section 3.1): the sectors of known master files are hashed
+ * into a signature table on the GPU; every 512-byte sector of a disk image is hashed on the GPU
+ * and looked up in that table; every (disk sector, master file, master sector) whose signatures
+ * are equal is reported. The signature is MD5 (RFC 1321; paper Section 2.1) over the 512-byte
+ * sector with standard padding, 9 compressions per sector. The table is open addressing with
+ * linear probing on the digest's low word (paper Eq. 3), optionally fronted by a blocked Bloom
+ * filter. Results are sorted by (disk_sector, file_id, file_sector).
+ *
+ * Rules that both the library and its tests follow:
+ *   - Only whole sectors count. A master file's trailing partial sector and an image's trailing
+ *     partial sector are ignored.
+ *   - A master sector whose 512 bytes are all equal (all zero or one repeated byte) is excluded.
+ *   - Every master sector with the matched digest is reported (duplicates within or across
+ *     master files all appear).
+ *
+ * Conventions:
+ *   - Every call returns CV_OK (0) or a negative CV_E* code; nothing aborts or throws.
+ *   - Buffers (cv_buf.data) may be host memory (pageable or pinned) or device memory of the
+ *     current device; the kind is detected per buffer. Device buffers must be 16-byte aligned.
+ *     Inputs are borrowed for the duration of the call only.
+ *   - Handles (cv_master, cv_result) and the result arrays they own belong to the library until
+ *     cv_free. Handles are not thread-safe; distinct handles may be used from distinct threads.
+ *   - All device work runs on the stream given in the options (a cudaStream_t; NULL means the
+ *     legacy default stream). The calls return after that work has finished.
+ *   - Indices are 0-based: file_id indexes the files[] array given to cv_master_build;
+ *     file_sector and disk_sector count 512-byte sectors from the start of their buffer.
+ */
+#ifndef CV_H
+#define CV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CV_SECTOR_BYTES 512u
+
+/* Return codes. */
+#define CV_OK 0
+#define CV_EINVAL -1     /* bad argument: NULL pointer, misaligned device buffer, size limit */
+#define CV_ENOMEM -2     /* device or host allocation failed */
+#define CV_ECUDA -3      /* a CUDA call failed (see cv_last_cuda_error) */
+#define CV_ETABLEFULL -4 /* the signature table could not take every master sector */
+#define CV_ECORRUPT -5   /* a device-side consistency check failed (status word set) */
+#define CV_ETIMEOUT -6   /* a device-side wait ran out of time; the results were discarded */
+#define CV_ENODEV -7     /* no usable CUDA device (the library has no CPU path) */
+#define CV_ERANGE -8     /* image_index out of range, or an output buffer too small */
+
+/* One match: disk sector i of image k equals sector file_sector of master file file_id. */
+typedef struct {
+  uint64_t disk_sector;
+  uint32_t file_id;
+  uint32_t file_sector;
+} cv_match; /* 16 bytes */
+
+/* A borrowed byte buffer in host or device memory. */
+typedef struct {
+  const void* data;
+  uint64_t n_bytes;
+} cv_buf;
+
+typedef struct cv_master cv_master; /* signature table of a master set, resident on the GPU */
+typedef struct cv_result cv_result; /* the results of one scan */
+
+#define CV_BLOOM_AUTO 0xFFFFFFFFu
+
+typedef struct {
+  uint32_t struct_size;         /* sizeof(cv_master_opts) */
+  float max_load;               /* table load factor cap in (0, 0.9]; 0 selects 0.5 */
+  uint32_t bloom_bits_per_key;  /* 0 = no Bloom prefilter; CV_BLOOM_AUTO = 16 */
+  uint32_t reserved;
+  void* stream;                 /* cudaStream_t */
+} cv_master_opts;
+
+/* cv_scan_opts.flags */
+#define CV_KEEP_ON_DEVICE 1u /* cv_matches returns device pointers (no device-to-host copy) */
+
+typedef struct {
+  uint32_t struct_size;       /* sizeof(cv_scan_opts) */
+  uint32_t flags;             /* CV_KEEP_ON_DEVICE */
+  void* stream;               /* cudaStream_t */
+  uint64_t chunk_bytes;       /* host images are streamed in chunks of this size; 0 = 256 MiB */
+  uint32_t kernel_config;     /* 0 = the tuned default; k + 1 selects configuration k */
+  uint32_t reserved;
+} cv_scan_opts;
+
+/* Kernel configurations of the scan (tile rows, ring stages, staging width). Every
+ * configuration gives the same results; they differ in speed. */
+int cv_kernel_config_count(void);
+const char* cv_kernel_config_name(int k); /* NULL when k is out of range */
+
+/*
+ * Build the signature table of n_files master files (paper Section 3.1: the table S is built
+ * by hashing every master sector and inserting its signature; collisions by linear probing,
+ * Eq. 3). files[f] is file f. Total whole, non-excluded master sectors must be below 2^27.
+ * On success *out receives a handle owning the device table. Errors: CV_EINVAL, CV_ENOMEM,
+ * CV_ECUDA, CV_ETABLEFULL, CV_ENODEV.
+ */
+int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts* opts, cv_master** out);
+
+typedef struct {
+  uint32_t n_files;
+  uint32_t reserved;
+  uint64_t n_sectors;        /* whole master sectors */
+  uint64_t n_kept;           /* after the exclusion rule */
+  uint64_t n_unique;         /* distinct digests among the kept sectors */
+  uint64_t n_slots;          /* table slots (power of two) */
+  uint64_t bloom_bytes;      /* 0 when there is no Bloom prefilter */
+  uint32_t max_probe;        /* longest linear-probe run of any stored digest, plus one */
+  uint32_t reserved2;
+  uint64_t device_bytes;     /* device memory the handle holds */
+} cv_master_info;
+
+int cv_master_get_info(const cv_master* m, cv_master_info* info);
+
+/*
+ * Scan n_images disk images against the table (paper Section 3.1-3.2: every sector hashed,
+ * its signature looked up, matches reported to the host). Device images are scanned in one
+ * launch; host images are streamed through device buffers in chunks, copies overlapping the
+ * hashing. On success *out receives a handle owning the sorted results of every image.
+ * Errors: CV_EINVAL, CV_ENOMEM, CV_ECUDA, CV_ETIMEOUT, CV_ECORRUPT, CV_ENODEV.
+ */
+int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const cv_scan_opts* opts,
+            cv_result** out);
+
+/*
+ * The sorted matches of image image_index: *out points at *n_out entries owned by the result
+ * handle (host memory, or device memory when the scan used CV_KEEP_ON_DEVICE), valid until
+ * cv_free(result). Errors: CV_EINVAL, CV_ERANGE.
+ */
+int cv_matches(const cv_result* r, uint32_t image_index, const cv_match** out, uint64_t* n_out);
+
+typedef struct {
+  uint64_t sectors;        /* whole sectors scanned */
+  uint64_t matches;        /* triples over all images */
+  uint64_t hit_sectors;    /* disk sectors with at least one match */
+  float kernel_ms;         /* device time of the hashing/probe launches */
+  float total_ms;          /* device time from the first copy to the last result copy */
+} cv_scan_stats;
+
+int cv_scan_get_stats(const cv_result* r, cv_scan_stats* st);
+
+/* Free a cv_master or cv_result handle (NULL is ignored). */
+void cv_free(void* handle);
+
+/* Text for a return code. */
+const char* cv_strerror(int code);
+
+/* The last CUDA error code seen by the calling thread inside the library (0 if none). */
+int cv_last_cuda_error(void);
+
+/*
+ * MD5 (RFC 1321, standard padding) of n_sectors consecutive 512-byte sectors, for testing and
+ * for callers that want signatures only. in: device pointer, 16-byte aligned, n_sectors*512
+ * bytes. digests: device pointer, 16 bytes per sector (the RFC's byte order). trivial: device
+ * pointer to one byte per sector set to 1 when all 512 bytes are equal, or NULL. Runs on
+ * stream and returns without waiting. Errors: CV_EINVAL, CV_ECUDA, CV_ENODEV.
+ */
+int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t* trivial, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CV_H */

@@ -1,0 +1,752 @@
+// Host runtime of libcv.so: the C ABI of include/cv.h.
+//
+// cv_master_build  master bytes -> device arena -> per-sector MD5 (scan kernel, digest mode)
+//                  -> table insert -> radix sort by slot -> postings + slots -> Bloom filter.
+// cv_scan          images -> segments (tensor maps over device memory, or host chunks copied
+//                  into a double-buffered device ring on a side stream) -> scan launches ->
+//                  tile offsets -> exact-size output -> expand -> per-image sorted matches.
+//
+// Temporaries come from a library-owned stream-ordered memory pool; long-lived objects (the
+// table, results) from cudaMalloc. Every CUDA error is returned as a CV_E* code.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "cv.h"
+#include "cv_internal.h"
+#include "cv_launch.h"
+#include "table_build.cuh"
+
+using namespace cvk;
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+
+int cuda_fail(cudaError_t e) {
+  g_last_cuda = (int)e;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? CV_ENOMEM : CV_ECUDA;
+}
+
+#define CV_CUDA(expr)                           \
+  do {                                          \
+    cudaError_t e_ = (expr);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+#define CV_TRY(expr)           \
+  do {                         \
+    int r_ = (expr);           \
+    if (r_ != CV_OK) return r_; \
+  } while (0)
+
+constexpr uint32_t kMagicMaster = 0xC7A57E01u;
+constexpr uint32_t kMagicResult = 0xC7A57E02u;
+
+// ------------------------------------------------------------------ per-device state
+struct DevCtx {
+  bool ready = false;
+  int dev = -1;
+  int sms = 0;
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  std::vector<int> blocks_per_sm;  // per scan configuration (scan mode)
+  std::vector<int> blocks_per_sm_digest;
+  int cfg_index = 0;               // default scan configuration
+};
+
+constexpr int kMaxDevices = 64;
+std::mutex g_ctx_mutex;
+DevCtx g_ctx[kMaxDevices];
+
+int find_cfg(const char* name) {
+  int n;
+  const ScanCfg* c = scan_configs(&n);
+  for (int i = 0; i < n; i++)
+    if (strcmp(c[i].name, name) == 0) return i;
+  return -1;
+}
+
+int get_ctx(DevCtx** out) {
+  int dev;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    g_last_cuda = (int)e;
+    cudaGetLastError();
+    return CV_ENODEV;
+  }
+  if (dev < 0 || dev >= kMaxDevices) return CV_ENODEV;
+  std::lock_guard<std::mutex> lk(g_ctx_mutex);
+  DevCtx& c = g_ctx[dev];
+  if (!c.ready) {
+    cudaDeviceProp prop;
+    CV_CUDA(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major < 10) return CV_ENODEV;
+    c.dev = dev;
+    c.sms = prop.multiProcessorCount;
+    cudaMemPoolProps pp;
+    memset(&pp, 0, sizeof pp);
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.handleTypes = cudaMemHandleTypeNone;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = dev;
+    CV_CUDA(cudaMemPoolCreate(&c.pool, &pp));
+    uint64_t thr = UINT64_MAX;
+    CV_CUDA(cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    CV_CUDA(cudaStreamCreateWithFlags(&c.copy_stream, cudaStreamNonBlocking));
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    CV_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) return CV_ENODEV;
+    c.encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    int n;
+    const ScanCfg* cfgs = scan_configs(&n);
+    c.blocks_per_sm.assign(n, 0);
+    c.blocks_per_sm_digest.assign(n, 0);
+    for (int i = 0; i < n; i++) {
+      CV_CUDA(cudaFuncSetAttribute(cfgs[i].scan_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfgs[i].smem));
+      CV_CUDA(cudaFuncSetAttribute(cfgs[i].digest_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfgs[i].smem));
+      CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.blocks_per_sm[i], cfgs[i].scan_fn, cfgs[i].T + 32,
+                                                            cfgs[i].smem));
+      CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.blocks_per_sm_digest[i], cfgs[i].digest_fn,
+                                                            cfgs[i].T + 32, cfgs[i].smem));
+      if (c.blocks_per_sm[i] < 1 || c.blocks_per_sm_digest[i] < 1) return CV_ECUDA;
+    }
+    c.cfg_index = 0;
+    const char* env = getenv("CV_SCAN_CONFIG");
+    if (env && *env) {
+      int k = find_cfg(env);
+      if (k < 0) return CV_EINVAL;
+      c.cfg_index = k;
+    }
+    c.ready = true;
+  }
+  *out = &c;
+  return CV_OK;
+}
+
+// Stream-ordered temporaries, returned to the pool when the scope ends.
+struct Temps {
+  DevCtx* ctx;
+  cudaStream_t stream;
+  std::vector<void*> ptrs;
+  Temps(DevCtx* c, cudaStream_t s) : ctx(c), stream(s) {}
+  ~Temps() {
+    for (void* p : ptrs) cudaFreeAsync(p, stream);
+  }
+  template <typename P>
+  int alloc(P** out, size_t bytes) {
+    void* p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, ctx->pool, stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    ptrs.push_back(p);
+    *out = (P*)p;
+    return CV_OK;
+  }
+};
+
+enum BufKind { kHost = 0, kDevice = 1 };
+
+int classify(DevCtx* ctx, const void* p, BufKind* kind) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *kind = kHost;
+    return CV_OK;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+    if (a.device != ctx->dev) return CV_EINVAL;
+    *kind = kDevice;
+  } else {
+    *kind = kHost;
+  }
+  return CV_OK;
+}
+
+int make_tmap(DevCtx* ctx, const ScanCfg& cfg, const void* base, uint64_t n_sectors, CUtensorMap* out) {
+  cuuint64_t dims[2] = {128, (cuuint64_t)n_sectors};
+  cuuint64_t strides[1] = {512};
+  cuuint32_t box[2] = {(cuuint32_t)(cfg.BOXB / 4), (cuuint32_t)cfg.T};
+  cuuint32_t es[2] = {1, 1};
+  CUtensorMapSwizzle sw = cfg.BOXB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  CUresult r = ctx->encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(base), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    g_last_cuda = (int)r;
+    return CV_ECUDA;
+  }
+  return CV_OK;
+}
+
+// A list of segments, each a contiguous device range of whole sectors with its tensor map.
+struct Job {
+  std::vector<Segment> segs;
+  std::vector<CUtensorMap> maps;
+  std::vector<const void*> bases;
+  uint64_t n_tiles = 0;
+  uint64_t n_sectors = 0;
+
+  // Append one device range (split at kMaxSegmentSectors). `base` may be null for ranges whose
+  // tensor map is made later (streamed chunks).
+  int add(DevCtx* ctx, const ScanCfg& cfg, const void* base, uint64_t n_sectors_in, uint64_t sector_base,
+          uint32_t image) {
+    uint64_t done = 0;
+    while (done < n_sectors_in) {
+      uint64_t n = std::min<uint64_t>(n_sectors_in - done, kMaxSegmentSectors);
+      Segment s;
+      s.n_sectors = n;
+      s.tile_base = n_tiles;
+      s.sector_base = sector_base + done;
+      s.image = image;
+      s.pad = 0;
+      CUtensorMap m;
+      memset(&m, 0, sizeof m);
+      const void* b = base ? (const uint8_t*)base + done * kSector : nullptr;
+      if (b) CV_TRY(make_tmap(ctx, cfg, b, n, &m));
+      segs.push_back(s);
+      maps.push_back(m);
+      bases.push_back(b);
+      n_tiles += (n + cfg.T - 1) / cfg.T;
+      n_sectors += n;
+      done += n;
+    }
+    return CV_OK;
+  }
+};
+
+// Launch the scan (or digest) kernel over segments [s0, s1) of the job.
+int launch_range(DevCtx* ctx, int cfg_i, bool digest, const Job& job, size_t s0, size_t s1, const CUtensorMap* maps_d,
+                 const Segment* segs_d, ScanParams base_params, cudaStream_t stream) {
+  if (s1 <= s0) return CV_OK;
+  int n;
+  const ScanCfg& cfg = scan_configs(&n)[cfg_i];
+  ScanParams p = base_params;
+  p.tmaps = maps_d + s0;
+  p.segs = segs_d + s0;
+  p.n_segs = (uint32_t)(s1 - s0);
+  p.tile_begin = job.segs[s0].tile_base;
+  const uint64_t tile_end = (s1 < job.segs.size()) ? job.segs[s1].tile_base : job.n_tiles;
+  p.n_tiles = tile_end - p.tile_begin;
+  if (p.n_tiles == 0) return CV_OK;
+  const int bps = digest ? ctx->blocks_per_sm_digest[cfg_i] : ctx->blocks_per_sm[cfg_i];
+  const uint64_t grid = std::min<uint64_t>(p.n_tiles, (uint64_t)ctx->sms * bps);
+  void* args[] = {&p};
+  CV_CUDA(cudaLaunchKernel(digest ? cfg.digest_fn : cfg.scan_fn, dim3((unsigned)grid), dim3(cfg.T + 32), args,
+                           cfg.smem, stream));
+  return CV_OK;
+}
+
+uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+unsigned grid_for(uint64_t n, int threads, int sms) {
+  uint64_t g = (n + threads - 1) / threads;
+  uint64_t cap = (uint64_t)sms * 16;
+  if (g > cap) g = cap;
+  return (unsigned)(g ? g : 1);
+}
+
+}  // namespace
+
+// ======================================================================== handles
+struct cv_master {
+  uint32_t magic;
+  int dev;
+  TableView tab;
+  void* slots;
+  void* postings;
+  void* bloom;
+  cv_master_info info;
+};
+
+struct cv_result {
+  uint32_t magic;
+  int dev;
+  bool on_device;
+  uint32_t n_images;
+  std::vector<uint64_t> off;  // n_images + 1
+  MatchOut* host;
+  MatchOut* dev_out;
+  cv_scan_stats st;
+};
+
+// ======================================================================= C ABI
+extern "C" {
+
+const char* cv_strerror(int code) {
+  switch (code) {
+    case CV_OK: return "ok";
+    case CV_EINVAL: return "invalid argument";
+    case CV_ENOMEM: return "out of memory";
+    case CV_ECUDA: return "CUDA error";
+    case CV_ETABLEFULL: return "signature table full";
+    case CV_ECORRUPT: return "device consistency check failed";
+    case CV_ETIMEOUT: return "device wait timed out";
+    case CV_ENODEV: return "no usable CUDA device";
+    case CV_ERANGE: return "index or size out of range";
+    default: return "unknown error";
+  }
+}
+
+int cv_last_cuda_error(void) { return g_last_cuda; }
+
+int cv_kernel_config_count(void) {
+  int n;
+  scan_configs(&n);
+  return n;
+}
+
+const char* cv_kernel_config_name(int k) {
+  int n;
+  const ScanCfg* c = scan_configs(&n);
+  return (k >= 0 && k < n) ? c[k].name : nullptr;
+}
+
+static int digest_job(DevCtx* ctx, Job& job, uint4* digests, uint8_t* trivial, uint32_t* status, cudaStream_t stream,
+                      Temps& tmp) {
+  const int cfg_i = ctx->cfg_index;
+  CUtensorMap* maps_d;
+  Segment* segs_d;
+  CV_TRY(tmp.alloc(&maps_d, job.maps.size() * sizeof(CUtensorMap)));
+  CV_TRY(tmp.alloc(&segs_d, job.segs.size() * sizeof(Segment)));
+  CV_CUDA(cudaMemcpyAsync(maps_d, job.maps.data(), job.maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                          stream));
+  CV_CUDA(cudaMemcpyAsync(segs_d, job.segs.data(), job.segs.size() * sizeof(Segment), cudaMemcpyHostToDevice, stream));
+  ScanParams p;
+  memset(&p, 0, sizeof p);
+  p.status = status;
+  p.digests = digests;
+  p.trivial = trivial;
+  CV_TRY(launch_range(ctx, cfg_i, true, job, 0, job.segs.size(), maps_d, segs_d, p, stream));
+  return CV_OK;
+}
+
+int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t* trivial, void* stream_) {
+  if (n_sectors == 0) return CV_OK;
+  if (!in || !digests) return CV_EINVAL;
+  if (((uintptr_t)in & 15u) || ((uintptr_t)digests & 15u)) return CV_EINVAL;
+  DevCtx* ctx;
+  CV_TRY(get_ctx(&ctx));
+  cudaStream_t stream = (cudaStream_t)stream_;
+  int n;
+  const ScanCfg& cfg = scan_configs(&n)[ctx->cfg_index];
+  Temps tmp(ctx, stream);
+  Job job;
+  CV_TRY(job.add(ctx, cfg, in, n_sectors, 0, 0));
+  uint32_t* status;
+  CV_TRY(tmp.alloc(&status, 4));
+  CV_CUDA(cudaMemsetAsync(status, 0, 4, stream));
+  return digest_job(ctx, job, (uint4*)digests, trivial, status, stream, tmp);
+}
+
+int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts* opts, cv_master** out) {
+  if (!out || (n_files && !files)) return CV_EINVAL;
+  *out = nullptr;
+  if (opts && opts->struct_size < sizeof(cv_master_opts)) return CV_EINVAL;
+  float max_load = (opts && opts->max_load > 0.f) ? opts->max_load : 0.5f;
+  if (!(max_load > 0.f && max_load <= 0.9f)) return CV_EINVAL;
+  uint32_t bpk = opts ? opts->bloom_bits_per_key : CV_BLOOM_AUTO;
+  if (bpk == CV_BLOOM_AUTO) bpk = 16;
+  if (bpk > 64) return CV_EINVAL;
+  cudaStream_t stream = opts ? (cudaStream_t)opts->stream : nullptr;
+  DevCtx* ctx;
+  CV_TRY(get_ctx(&ctx));
+  int ncfg;
+  const ScanCfg& cfg = scan_configs(&ncfg)[ctx->cfg_index];
+
+  // whole sectors of every file, concatenated
+  std::vector<uint64_t> file_base(n_files + 1, 0);
+  for (uint32_t f = 0; f < n_files; f++) {
+    if (files[f].n_bytes && !files[f].data) return CV_EINVAL;
+    file_base[f + 1] = file_base[f] + files[f].n_bytes / kSector;
+  }
+  const uint64_t M = file_base[n_files];
+  if (M >= (1ull << 27)) return CV_EINVAL;
+
+  cv_master* m = (cv_master*)calloc(1, sizeof(cv_master));
+  if (!m) return CV_ENOMEM;
+  m->magic = kMagicMaster;
+  m->dev = ctx->dev;
+  int rc = CV_OK;
+  {
+    Temps tmp(ctx, stream);
+    auto body = [&]() -> int {
+      const uint64_t n_slots = std::max<uint64_t>(next_pow2((uint64_t)((double)M / max_load) + 1), 2);
+      if (n_slots > (1ull << 31)) return CV_EINVAL;
+      const uint32_t mask = (uint32_t)(n_slots - 1);
+      uint8_t* arena;
+      uint4* dig;
+      uint8_t* trivial;
+      uint32_t *owner, *cnt, *slot_of, *keys2, *vals, *vals2, *counters;
+      uint64_t* file_base_d;
+      CV_TRY(tmp.alloc(&arena, M * kSector));
+      CV_TRY(tmp.alloc(&dig, M * sizeof(uint4)));
+      CV_TRY(tmp.alloc(&trivial, M));
+      CV_TRY(tmp.alloc(&owner, n_slots * 4));
+      CV_TRY(tmp.alloc(&cnt, n_slots * 4));
+      CV_TRY(tmp.alloc(&slot_of, M * 4));
+      CV_TRY(tmp.alloc(&keys2, M * 4));
+      CV_TRY(tmp.alloc(&vals, M * 4));
+      CV_TRY(tmp.alloc(&vals2, M * 4));
+      CV_TRY(tmp.alloc(&counters, 16));  // max_disp, n_kept, n_unique, status
+      CV_TRY(tmp.alloc(&file_base_d, (n_files + 1) * 8));
+      CV_CUDA(cudaMemsetAsync(owner, 0, n_slots * 4, stream));
+      CV_CUDA(cudaMemsetAsync(cnt, 0, n_slots * 4, stream));
+      CV_CUDA(cudaMemsetAsync(counters, 0, 16, stream));
+      CV_CUDA(cudaMemcpyAsync(file_base_d, file_base.data(), (n_files + 1) * 8, cudaMemcpyHostToDevice, stream));
+      for (uint32_t f = 0; f < n_files; f++) {
+        const uint64_t ns = file_base[f + 1] - file_base[f];
+        if (ns)
+          CV_CUDA(cudaMemcpyAsync(arena + file_base[f] * kSector, files[f].data, ns * kSector, cudaMemcpyDefault,
+                                  stream));
+      }
+      // long-lived table memory
+      CV_CUDA(cudaMalloc(&m->slots, n_slots * 32));
+      CV_CUDA(cudaMalloc(&m->postings, std::max<uint64_t>(M, 1) * 8));
+      CV_CUDA(cudaMemsetAsync(m->slots, 0, n_slots * 32, stream));
+      uint64_t n_blocks = 0;
+      if (bpk) {
+        n_blocks = std::max<uint64_t>(next_pow2((M * bpk + 255) / 256), 1);
+        CV_CUDA(cudaMalloc(&m->bloom, n_blocks * 32));
+        CV_CUDA(cudaMemsetAsync(m->bloom, 0, n_blocks * 32, stream));
+      }
+      if (M) {
+        Job job;
+        CV_TRY(job.add(ctx, cfg, arena, M, 0, 0));
+        CV_TRY(digest_job(ctx, job, dig, trivial, counters + 3, stream, tmp));
+        const unsigned g = grid_for(M, 256, ctx->sms);
+        insert_kernel<<<g, 256, 0, stream>>>(dig, trivial, M, owner, cnt, slot_of, mask, counters, counters + 1,
+                                            counters + 3);
+        CV_CUDA(cudaGetLastError());
+        iota_kernel<<<g, 256, 0, stream>>>(vals, M);
+        CV_CUDA(cudaGetLastError());
+        // stable LSD radix sort of (slot_of, m) by slot_of; keys <= n_slots
+        int bits = 1;
+        while ((1ull << bits) <= n_slots) bits++;
+        const uint32_t nb = (uint32_t)((M + kRsChunk - 1) / kRsChunk);
+        uint32_t* hist;
+        CV_TRY(tmp.alloc(&hist, (uint64_t)nb * 256 * 4));
+        uint32_t *kin = slot_of, *vin = vals, *kout = keys2, *vout = vals2;
+        for (int shift = 0; shift < bits; shift += 8) {
+          rs_hist_kernel<<<nb, kRsThreads, 0, stream>>>(kin, M, shift, hist, nb);
+          exclusive_scan_u32_kernel<<<1, 1024, 0, stream>>>(hist, (uint64_t)nb * 256);
+          rs_scatter_kernel<<<nb, kRsThreads, 0, stream>>>(kin, vin, kout, vout, M, shift, hist, nb);
+          CV_CUDA(cudaGetLastError());
+          std::swap(kin, kout);
+          std::swap(vin, vout);
+        }
+        fill_kernel<<<g, 256, 0, stream>>>(kin, vin, M, (uint32_t)n_slots, owner, cnt, dig, file_base_d, n_files,
+                                          (uint4*)m->slots, (uint2*)m->postings, counters + 2);
+        CV_CUDA(cudaGetLastError());
+        if (bpk) {
+          bloom_kernel<<<grid_for(n_slots, 256, ctx->sms), 256, 0, stream>>>((const uint4*)m->slots,
+                                                                             (uint32_t)n_slots, (uint32_t*)m->bloom,
+                                                                             (uint32_t)(n_blocks - 1));
+          CV_CUDA(cudaGetLastError());
+        }
+      }
+      uint32_t hc[4];
+      CV_CUDA(cudaMemcpyAsync(hc, counters, 16, cudaMemcpyDeviceToHost, stream));
+      CV_CUDA(cudaStreamSynchronize(stream));
+      if (hc[3] & kStTableFull) return CV_ETABLEFULL;
+      if (hc[3] & kStTimeout) return CV_ETIMEOUT;
+      if (hc[3]) return CV_ECORRUPT;
+      m->tab.slots = (const uint4*)m->slots;
+      m->tab.postings = (const uint2*)m->postings;
+      m->tab.bloom = (const uint4*)m->bloom;
+      m->tab.slot_mask = mask;
+      m->tab.bloom_mask = bpk ? (uint32_t)(n_blocks - 1) : 0u;
+      m->tab.max_probe = hc[0] + 1;
+      m->tab.use_bloom = bpk ? 1u : 0u;
+      m->info.n_files = n_files;
+      m->info.n_sectors = M;
+      m->info.n_kept = hc[1];
+      m->info.n_unique = hc[2];
+      m->info.n_slots = n_slots;
+      m->info.bloom_bytes = n_blocks * 32;
+      m->info.max_probe = hc[0] + 1;
+      m->info.device_bytes = n_slots * 32 + std::max<uint64_t>(M, 1) * 8 + n_blocks * 32;
+      return CV_OK;
+    };
+    rc = body();
+  }
+  if (rc == CV_OK) {
+    cudaError_t e = cudaStreamSynchronize(stream);  // temporaries returned
+    if (e != cudaSuccess) rc = cuda_fail(e);
+  }
+  if (rc != CV_OK) {
+    cv_free(m);
+    return rc;
+  }
+  *out = m;
+  return CV_OK;
+}
+
+int cv_master_get_info(const cv_master* m, cv_master_info* info) {
+  if (!m || !info || m->magic != kMagicMaster) return CV_EINVAL;
+  *info = m->info;
+  return CV_OK;
+}
+
+int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const cv_scan_opts* opts, cv_result** out) {
+  if (!m || m->magic != kMagicMaster || !out || (n_images && !images)) return CV_EINVAL;
+  *out = nullptr;
+  if (opts && opts->struct_size < sizeof(cv_scan_opts)) return CV_EINVAL;
+  const uint32_t flags = opts ? opts->flags : 0u;
+  cudaStream_t stream = opts ? (cudaStream_t)opts->stream : nullptr;
+  uint64_t chunk = (opts && opts->chunk_bytes) ? opts->chunk_bytes : (256ull << 20);
+  chunk = chunk / kSector * kSector;
+  if (chunk == 0) return CV_EINVAL;
+  DevCtx* ctx;
+  CV_TRY(get_ctx(&ctx));
+  if (ctx->dev != m->dev) return CV_EINVAL;
+  int ncfg;
+  const ScanCfg* cfgs = scan_configs(&ncfg);
+  int cfg_i = ctx->cfg_index;
+  if (opts && opts->kernel_config) {
+    if (opts->kernel_config > (uint32_t)ncfg) return CV_EINVAL;
+    cfg_i = (int)opts->kernel_config - 1;
+  }
+  const ScanCfg& cfg = cfgs[cfg_i];
+
+  // ------------------------------------------------------------ plan the segments
+  std::vector<BufKind> kind(n_images);
+  Job job;
+  std::vector<size_t> first_seg(n_images + 1, 0);
+  struct HostChunk {
+    size_t seg;
+    const uint8_t* src;
+    uint64_t bytes;
+  };
+  std::vector<HostChunk> hchunks;
+  for (uint32_t i = 0; i < n_images; i++) {
+    first_seg[i] = job.segs.size();
+    const uint64_t ns = images[i].n_bytes / kSector;
+    if (ns == 0) continue;
+    if (!images[i].data) return CV_EINVAL;
+    CV_TRY(classify(ctx, images[i].data, &kind[i]));
+    if (kind[i] == kDevice) {
+      if ((uintptr_t)images[i].data & 15u) return CV_EINVAL;
+      CV_TRY(job.add(ctx, cfg, images[i].data, ns, 0, i));
+    } else {
+      const uint64_t per = chunk / kSector;
+      for (uint64_t s0 = 0; s0 < ns; s0 += per) {
+        const uint64_t n = std::min(per, ns - s0);
+        hchunks.push_back(HostChunk{job.segs.size(), (const uint8_t*)images[i].data + s0 * kSector, n * kSector});
+        CV_TRY(job.add(ctx, cfg, nullptr, n, s0, i));
+      }
+    }
+  }
+  first_seg[n_images] = job.segs.size();
+
+  cv_result* r = new (std::nothrow) cv_result();
+  if (!r) return CV_ENOMEM;
+  r->magic = kMagicResult;
+  r->dev = ctx->dev;
+  r->on_device = (flags & CV_KEEP_ON_DEVICE) != 0;
+  r->n_images = n_images;
+  r->off.assign(n_images + 1, 0);
+  r->host = nullptr;
+  r->dev_out = nullptr;
+  memset(&r->st, 0, sizeof r->st);
+  r->st.sectors = job.n_sectors;
+
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ring_copied[2] = {nullptr, nullptr}, ring_free[2] = {nullptr, nullptr};
+  int rc;
+  {
+    Temps tmp(ctx, stream);
+    auto body = [&]() -> int {
+      for (auto& e : ev) CV_CUDA(cudaEventCreate(&e));
+      CV_CUDA(cudaEventRecord(ev[0], stream));
+      const size_t nseg = job.segs.size();
+      const uint64_t nt = job.n_tiles;
+      uint64_t total = 0;
+      std::vector<uint64_t> seg_off(nseg + 2, 0);
+      uint32_t* status_keep = nullptr;
+      if (nseg) {
+        void* ring[2] = {nullptr, nullptr};
+        if (!hchunks.empty()) {
+          const uint64_t ring_bytes = std::min<uint64_t>(chunk, [&] {
+            uint64_t mx = 0;
+            for (auto& h : hchunks) mx = std::max(mx, h.bytes);
+            return mx;
+          }());
+          for (int b = 0; b < 2; b++) {
+            CV_TRY(tmp.alloc(&ring[b], ring_bytes));
+            CV_CUDA(cudaEventCreateWithFlags(&ring_copied[b], cudaEventDisableTiming));
+            CV_CUDA(cudaEventCreateWithFlags(&ring_free[b], cudaEventDisableTiming));
+          }
+          for (size_t k = 0; k < hchunks.size(); k++) {
+            const size_t s = hchunks[k].seg;
+            CV_TRY(make_tmap(ctx, cfg, ring[k & 1], job.segs[s].n_sectors, &job.maps[s]));
+          }
+        }
+        CUtensorMap* maps_d;
+        Segment* segs_d;
+        uint4* hit_rec;
+        uint32_t *tile_nhit, *status;
+        uint64_t *tile_ntrip, *tile_off, *seg_off_d;
+        CV_TRY(tmp.alloc(&maps_d, nseg * sizeof(CUtensorMap)));
+        CV_TRY(tmp.alloc(&segs_d, nseg * sizeof(Segment)));
+        CV_TRY(tmp.alloc(&hit_rec, nt * cfg.T * sizeof(uint4)));
+        CV_TRY(tmp.alloc(&tile_nhit, nt * 4));
+        CV_TRY(tmp.alloc(&tile_ntrip, nt * 8));
+        CV_TRY(tmp.alloc(&tile_off, nt * 8));
+        CV_TRY(tmp.alloc(&seg_off_d, (nseg + 2) * 8));  // seg_off[nseg], total, status
+        status = (uint32_t*)(seg_off_d + nseg + 1);
+        status_keep = status;
+        CV_CUDA(cudaMemsetAsync(status, 0, 8, stream));
+        CV_CUDA(cudaMemcpyAsync(maps_d, job.maps.data(), nseg * sizeof(CUtensorMap), cudaMemcpyHostToDevice, stream));
+        CV_CUDA(cudaMemcpyAsync(segs_d, job.segs.data(), nseg * sizeof(Segment), cudaMemcpyHostToDevice, stream));
+        ScanParams p;
+        memset(&p, 0, sizeof p);
+        p.tab = m->tab;
+        p.hit_rec = hit_rec;
+        p.tile_nhit = tile_nhit;
+        p.tile_ntrip = tile_ntrip;
+        p.status = status;
+        CV_CUDA(cudaEventRecord(ev[1], stream));
+        // device segments: one launch per run of consecutive device segments
+        size_t hk = 0;
+        size_t s = 0;
+        while (s < nseg) {
+          if (hk < hchunks.size() && hchunks[hk].seg == s) {
+            const int b = (int)(hk & 1);
+            if (hk >= 2) CV_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ring_free[b], 0));
+            else CV_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ev[1], 0));
+            CV_CUDA(cudaMemcpyAsync(ring[b], hchunks[hk].src, hchunks[hk].bytes, cudaMemcpyHostToDevice,
+                                    ctx->copy_stream));
+            CV_CUDA(cudaEventRecord(ring_copied[b], ctx->copy_stream));
+            CV_CUDA(cudaStreamWaitEvent(stream, ring_copied[b], 0));
+            CV_TRY(launch_range(ctx, cfg_i, false, job, s, s + 1, maps_d, segs_d, p, stream));
+            CV_CUDA(cudaEventRecord(ring_free[b], stream));
+            hk++;
+            s++;
+          } else {
+            size_t e = s;
+            while (e < nseg && !(hk < hchunks.size() && hchunks[hk].seg == e)) e++;
+            CV_TRY(launch_range(ctx, cfg_i, false, job, s, e, maps_d, segs_d, p, stream));
+            s = e;
+          }
+        }
+        CV_CUDA(cudaEventRecord(ev[2], stream));
+        uint64_t* total_d = seg_off_d + nseg;
+        uint32_t nseg32 = (uint32_t)nseg;
+        uint64_t nt_arg = nt;
+        void* targs[] = {&tile_ntrip, &nt_arg, &tile_off, &segs_d, &nseg32, &seg_off_d, &total_d};
+        CV_CUDA(cudaLaunchKernel(tile_offsets_fn(), dim3(1), dim3(1024), targs, 0, stream));
+        CV_CUDA(cudaMemcpyAsync(seg_off.data(), seg_off_d, (nseg + 2) * 8, cudaMemcpyDeviceToHost, stream));
+        CV_CUDA(cudaStreamSynchronize(stream));
+        const uint32_t st = (uint32_t)seg_off[nseg + 1];
+        if (st & kStTimeout) return CV_ETIMEOUT;
+        if (st) return CV_ECORRUPT;
+        total = seg_off[nseg];
+        if (total) {
+          CV_CUDA(cudaMalloc(&r->dev_out, total * sizeof(MatchOut)));
+          const unsigned eg = grid_for(nt * 32, 256, ctx->sms);
+          uint64_t cap = total;
+          const uint2* postings = m->tab.postings;
+          MatchOut* outp = r->dev_out;
+          void* eargs[] = {&hit_rec, &tile_nhit, &tile_off, &nt_arg, &segs_d, &nseg32, &postings, &outp, &cap, &status};
+          CV_CUDA(cudaLaunchKernel(cfg.expand_fn, dim3(eg), dim3(256), eargs, 0, stream));
+        }
+      }
+      // per-image ranges; an image without sectors gets an empty range
+      r->off[n_images] = total;
+      for (int64_t i = (int64_t)n_images - 1; i >= 0; i--)
+        r->off[i] = (first_seg[i] < first_seg[i + 1]) ? seg_off[first_seg[i]] : r->off[i + 1];
+      r->st.matches = total;
+      if (total && !r->on_device) {
+        r->host = (MatchOut*)malloc(total * sizeof(MatchOut));
+        if (!r->host) return CV_ENOMEM;
+        CV_CUDA(cudaMemcpyAsync(r->host, r->dev_out, total * sizeof(MatchOut), cudaMemcpyDeviceToHost, stream));
+      }
+      CV_CUDA(cudaEventRecord(ev[3], stream));
+      CV_CUDA(cudaStreamSynchronize(stream));
+      if (nseg && total) {
+        uint32_t st2 = 0;
+        CV_CUDA(cudaMemcpy(&st2, (const uint8_t*)status_keep + 0, 4, cudaMemcpyDeviceToHost));
+        if (st2) return CV_ECORRUPT;
+      }
+      float ms = 0.f;
+      if (nseg) {
+        CV_CUDA(cudaEventElapsedTime(&ms, ev[1], ev[2]));
+        r->st.kernel_ms = ms;
+      }
+      CV_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[3]));
+      r->st.total_ms = ms;
+      if (total && !r->on_device) {
+        cudaFree(r->dev_out);
+        r->dev_out = nullptr;
+      }
+      return CV_OK;
+    };
+    rc = body();
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  for (int b = 0; b < 2; b++) {
+    if (ring_copied[b]) cudaEventDestroy(ring_copied[b]);
+    if (ring_free[b]) cudaEventDestroy(ring_free[b]);
+  }
+  if (rc != CV_OK) {
+    cudaStreamSynchronize(stream);
+    cudaStreamSynchronize(ctx->copy_stream);
+    cv_free(r);
+    return rc;
+  }
+  *out = r;
+  return CV_OK;
+}
+
+int cv_matches(const cv_result* r, uint32_t image_index, const cv_match** out, uint64_t* n_out) {
+  if (!r || r->magic != kMagicResult || !out || !n_out) return CV_EINVAL;
+  if (image_index >= r->n_images) return CV_ERANGE;
+  const uint64_t a = r->off[image_index], b = r->off[image_index + 1];
+  *n_out = b - a;
+  const MatchOut* base = r->on_device ? r->dev_out : r->host;
+  *out = (b > a && base) ? (const cv_match*)(base + a) : nullptr;
+  return CV_OK;
+}
+
+int cv_scan_get_stats(const cv_result* r, cv_scan_stats* st) {
+  if (!r || r->magic != kMagicResult || !st) return CV_EINVAL;
+  *st = r->st;
+  return CV_OK;
+}
+
+void cv_free(void* handle) {
+  if (!handle) return;
+  const uint32_t magic = *(const uint32_t*)handle;
+  if (magic == kMagicMaster) {
+    cv_master* m = (cv_master*)handle;
+    m->magic = 0;
+    if (m->slots) cudaFree(m->slots);
+    if (m->postings) cudaFree(m->postings);
+    if (m->bloom) cudaFree(m->bloom);
+    free(m);
+  } else if (magic == kMagicResult) {
+    cv_result* r = (cv_result*)handle;
+    r->magic = 0;
+    if (r->dev_out) cudaFree(r->dev_out);
+    free(r->host);
+    delete r;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+// Internal types shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cvk {
+
+constexpr uint32_t kSector = 512;
+
+// Device status word bits (set with atomicOr; read by the host after each launch).
+constexpr uint32_t kStTimeout = 1u;     // an mbarrier wait ran out of time
+constexpr uint32_t kStProbeBound = 2u;  // a lookup ran past the table's recorded probe bound
+constexpr uint32_t kStTableFull = 4u;   // an insert found no free slot
+constexpr uint32_t kStOverflow = 8u;    // an output buffer was too small
+
+// A contiguous run of whole sectors in device memory, scanned as one tensor map. An image
+// larger than kMaxSegmentSectors is split into several segments.
+constexpr uint64_t kMaxSegmentSectors = 1ull << 30;
+
+struct Segment {
+  uint64_t n_sectors;    // whole sectors in the segment
+  uint64_t tile_base;    // global index of the segment's first tile
+  uint64_t sector_base;  // index within its image of the segment's first sector
+  uint32_t image;        // index of the image the segment belongs to
+  uint32_t pad;
+};
+
+// Device view of a master table.
+//   slots: 2 x uint4 per slot: {d0, d1, d2, d3} and {post_off, post_cnt, 0, 0}; post_cnt == 0
+//          marks an empty slot. The home slot of digest d is d0 & slot_mask (Eq. 3).
+//   postings: (file_id, file_sector) per kept master sector, grouped by slot, ascending.
+//   bloom: 8 u32 words (32 bytes) per block; block d3 & bloom_mask; in word j the bit
+//          (d1 >> 5j) & 31 for j < 6, (d2 >> 5(j-6)) & 31 for j = 6, 7.
+struct TableView {
+  const uint4* slots;
+  const uint2* postings;
+  const uint4* bloom;
+  uint32_t slot_mask;
+  uint32_t bloom_mask;
+  uint32_t max_probe;  // no stored digest sits further than max_probe - 1 slots from home
+  uint32_t use_bloom;
+};
+
+struct ScanParams {
+  const CUtensorMap* tmaps;  // one per segment, 64-byte aligned device memory
+  const Segment* segs;
+  uint32_t n_segs;
+  uint32_t pad;
+  uint64_t tile_begin;  // global index of the first tile of this launch
+  uint64_t n_tiles;     // tiles of this launch
+  TableView tab;
+  // scan outputs
+  uint4* hit_rec;        // n_tiles * T records {sector_in_tile, post_off, post_cnt, 0}
+  uint32_t* tile_nhit;   // hit sectors per tile
+  uint64_t* tile_ntrip;  // triples per tile
+  uint32_t* status;
+  // digest outputs (digest mode): indexed by segment sector_base + row
+  uint4* digests;
+  uint8_t* trivial;
+};
+
+// One output triple (the layout of cv_match).
+struct MatchOut {
+  uint64_t disk_sector;
+  uint32_t file_id;
+  uint32_t file_sector;
+};
+
+// Index of the segment holding global tile `tile` (segments sorted by tile_base).
+__device__ __forceinline__ uint32_t find_segment(const Segment* segs, uint32_t n, uint64_t tile) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (segs[mid].tile_base <= tile) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+}  // namespace cvk

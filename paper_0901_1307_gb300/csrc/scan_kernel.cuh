@@ -1,0 +1,306 @@
+// The fused sector scan: TMA staging -> per-sector MD5 -> Bloom test -> linear probe ->
+// warp-ballot compaction of the hits of each tile.
+//
+// Paper Section 3.2 stages 16x16-word blocks of 16 sectors through shared memory with a
+// rotation skew so that a cohort of 16 threads loads coalesced and then hashes one sector per
+// thread without bank conflicts (Figures 8 and 9). The same idea on sm_103a: a tile of T
+// sectors is brought into shared memory by the Tensor Memory Accelerator as a 2-D box
+// (T rows of 512 bytes, BOXB bytes of each row per stage) with the hardware's 16-byte-chunk
+// XOR swizzle, which plays the role of Figure 9's skew; thread t then hashes sector t of the
+// tile (one sector per thread, Section 3.2), reading its words with conflict-free 16-byte
+// shared loads. A dedicated producer warp keeps NS stages in flight through an mbarrier ring,
+// so the hashing warps never issue a global load. Tiles are spread over a persistent grid.
+//
+// Every mbarrier wait is bounded in time: on expiry the kernel sets kStTimeout in the status
+// word, stops waiting (its results are then discarded by the host), lets the producer wait
+// for its own copies in flight, and returns.
+#pragma once
+#include <cuda.h>
+#include <stdint.h>
+
+#include "cv_internal.h"
+#include "md5_sector.cuh"
+
+namespace cvk {
+
+constexpr uint64_t kWaitTimeoutNs = 4000000000ull;  // 4 s per wait
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete; false on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
+                                          uint32_t* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
+      *abort_flag = 1u;
+      atomicOr(status, kStTimeout);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y, uint32_t bar,
+                                            uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+  return v;
+}
+
+__device__ __forceinline__ void consumer_bar_sync(uint32_t n_threads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(n_threads) : "memory");
+}
+
+// Blocked Bloom test: all eight bits of the digest's block set.
+__device__ __forceinline__ bool bloom_test(const TableView& tab, uint32_t d1, uint32_t d2, uint32_t d3) {
+  const uint4* blk = tab.bloom + 2ull * (d3 & tab.bloom_mask);
+  uint4 lo = __ldg(blk);
+  uint4 hi = __ldg(blk + 1);
+  uint32_t m = (lo.x >> (d1 & 31)) & (lo.y >> ((d1 >> 5) & 31)) & (lo.z >> ((d1 >> 10) & 31)) &
+               (lo.w >> ((d1 >> 15) & 31)) & (hi.x >> ((d1 >> 20) & 31)) & (hi.y >> ((d1 >> 25) & 31)) &
+               (hi.z >> (d2 & 31)) & (hi.w >> ((d2 >> 5) & 31));
+  return (m & 1u) != 0;
+}
+
+// Linear probing from the home slot (Eq. 3) until the digest or an empty slot is found, never
+// beyond the table's probe bound. Returns post_cnt (0: not present) and post_off.
+__device__ __forceinline__ uint32_t table_probe(const TableView& tab, uint32_t d0, uint32_t d1, uint32_t d2,
+                                                uint32_t d3, uint32_t& post_off) {
+  uint32_t idx = d0 & tab.slot_mask;
+  for (uint32_t c = 0; c < tab.max_probe; c++) {
+    const uint4* s = tab.slots + 2ull * idx;
+    uint4 key = __ldg(s);
+    uint4 val = __ldg(s + 1);
+    if (val.y == 0u) return 0u;
+    if (key.x == d0 && key.y == d1 && key.z == d2 && key.w == d3) {
+      post_off = val.x;
+      return val.y;
+    }
+    idx = (idx + 1u) & tab.slot_mask;
+  }
+  return 0u;
+}
+
+enum : int { kModeScan = 0, kModeDigest = 1 };
+
+template <int T, int NS, int BOXB>
+struct ScanSmem {
+  static constexpr uint32_t kStageBytes = T * BOXB;
+  static constexpr uint32_t kW = T / 32;
+  // stages first (1024-byte aligned), then barriers and the compaction scratch
+  static constexpr uint32_t kBarOff = NS * kStageBytes;
+  static constexpr uint32_t kMiscOff = kBarOff + 2 * NS * 8;
+  static constexpr uint32_t kBytes = kMiscOff + 4 * kW * 4 + 16;
+  static constexpr uint32_t kAlloc = kBytes + 1024;  // room to align the base
+};
+
+// T: sectors per tile (= hashing threads); NS: ring stages; BOXB: bytes of each sector row per
+// stage (64 or 128). Block size is T + 32 (the last warp is the producer).
+template <int T, int NS, int BOXB, int MODE>
+__global__ void __launch_bounds__(T + 32) scan_kernel(const ScanParams p) {
+  static_assert(T % 32 == 0 && T <= 256, "tile rows");
+  static_assert(BOXB == 64 || BOXB == 128, "box width");
+  using L = ScanSmem<T, NS, BOXB>;
+  constexpr int kChunks = 512 / BOXB;       // stages per sector
+  constexpr int kBlocksPerChunk = BOXB / 64;  // MD5 blocks per stage
+  constexpr uint32_t kW = L::kW;
+
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_addr(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* const gbase = smem_raw + (base - raw);
+  const uint32_t bar_full = base + L::kBarOff;  // NS x 8 bytes
+  const uint32_t bar_empty = bar_full + NS * 8;
+  uint32_t* const s_hits = reinterpret_cast<uint32_t*>(gbase + L::kMiscOff);  // [2][kW]
+  uint32_t* const s_trip = s_hits + 2 * kW;                                   // [2][kW]
+  volatile uint32_t* const s_abort = s_trip + 2 * kW;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+
+  if (tid == 0) {
+    for (int s = 0; s < NS; s++) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, T);
+    }
+    *s_abort = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == (int)kW) {
+    // ------------------------------------------------------------------ producer warp
+    if (lane != 0) return;
+    const uint64_t policy = l2_evict_first_policy();
+    uint32_t j = 0;
+    bool ok = true;
+    for (uint64_t lt = blockIdx.x; lt < p.n_tiles && ok; lt += gridDim.x) {
+      const uint64_t tile = p.tile_begin + lt;
+      const uint32_t sg = find_segment(p.segs, p.n_segs, tile);
+      const CUtensorMap* map = p.tmaps + sg;
+      // the maps were written to global memory by a copy: make them visible to the TMA unit
+      asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                   : "memory");
+      const int32_t row0 = (int32_t)((tile - p.segs[sg].tile_base) * T);
+      for (int c = 0; c < kChunks; c++, j++) {
+        const uint32_t s = j % NS;
+        if (j >= (uint32_t)NS && !mbar_wait(bar_empty + 8 * s, ((j / NS) - 1) & 1, s_abort, p.status)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(bar_full + 8 * s, L::kStageBytes);
+        tma_load_2d(base + s * L::kStageBytes, map, c * (BOXB / 4), row0, bar_full + 8 * s, policy);
+      }
+    }
+    // Wait (bounded) for the copies still in flight so none lands after the block exits.
+    const uint32_t issued = j;
+    const uint32_t first = issued > (uint32_t)NS ? issued - NS : 0u;
+    for (uint32_t q = first; q < issued; q++) {
+      const uint32_t s = q % NS;
+      const uint64_t t0 = globaltimer_ns();
+      while (!mbar_try_wait(bar_full + 8 * s, (q / NS) & 1)) {
+        if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
+          atomicOr(p.status, kStTimeout);
+          break;
+        }
+      }
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------------- hashing warps
+  // Row `tid` of each stage; the 16-byte chunk q of the row sits at chunk q ^ swz.
+  const uint32_t row_off = (uint32_t)tid * BOXB;
+  const uint32_t swz = (BOXB == 128) ? ((uint32_t)tid & 7u) : (((uint32_t)tid >> 1) & 3u);
+  const uint32_t lane_lt = (1u << lane) - 1u;
+  uint32_t j = 0;
+  uint32_t parity_buf = 0;
+  for (uint64_t lt = blockIdx.x; lt < p.n_tiles; lt += gridDim.x, parity_buf ^= 1u) {
+    const uint64_t tile = p.tile_begin + lt;
+    const uint32_t sg = find_segment(p.segs, p.n_segs, tile);
+    const uint64_t row0 = (tile - p.segs[sg].tile_base) * T;
+    const bool valid = row0 + (uint64_t)tid < p.segs[sg].n_sectors;
+
+    uint32_t st[4];
+    md5_init(st);
+    uint32_t diff = 0, ref = 0;
+#pragma unroll 1
+    for (int c = 0; c < kChunks; c++, j++) {
+      const uint32_t s = j % NS;
+      mbar_wait(bar_full + 8 * s, (j / NS) & 1, s_abort, p.status);
+      const uint32_t row = base + s * L::kStageBytes + row_off;
+#pragma unroll
+      for (int b = 0; b < kBlocksPerChunk; b++) {
+        uint32_t X[16];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const uint32_t chunk = (uint32_t)(4 * b + q) ^ swz;
+          const uint4 v = lds128(row + chunk * 16u);
+          X[4 * q + 0] = v.x;
+          X[4 * q + 1] = v.y;
+          X[4 * q + 2] = v.z;
+          X[4 * q + 3] = v.w;
+        }
+        if (b == kBlocksPerChunk - 1) mbar_arrive(bar_empty + 8 * s);
+        if constexpr (MODE == kModeDigest) {
+          if (c == 0 && b == 0) ref = (X[0] & 0xFFu) * 0x01010101u;
+#pragma unroll
+          for (int q = 0; q < 16; q++) diff |= X[q] ^ ref;
+        }
+        md5_compress(st, X);
+      }
+    }
+    md5_compress_sector_padding(st);
+
+    if constexpr (MODE == kModeDigest) {
+      if (valid) {
+        const uint64_t g = p.segs[sg].sector_base + row0 + (uint64_t)tid;
+        p.digests[g] = make_uint4(st[0], st[1], st[2], st[3]);
+        if (p.trivial) p.trivial[g] = diff == 0u ? 1 : 0;
+      }
+    } else {
+      uint32_t post_off = 0, post_cnt = 0;
+      if (valid && (!p.tab.use_bloom || bloom_test(p.tab, st[1], st[2], st[3])))
+        post_cnt = table_probe(p.tab, st[0], st[1], st[2], st[3], post_off);
+      const bool hit = post_cnt != 0u;
+      const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, hit);
+      const uint32_t wtrip = __reduce_add_sync(0xFFFFFFFFu, post_cnt);
+      uint32_t* hits_buf = s_hits + parity_buf * kW;
+      uint32_t* trip_buf = s_trip + parity_buf * kW;
+      if (lane == 0) {
+        hits_buf[warp] = __popc(ballot);
+        trip_buf[warp] = wtrip;
+      }
+      consumer_bar_sync(T);
+      uint32_t before = 0, total = 0;
+      uint64_t trips = 0;
+#pragma unroll
+      for (int w = 0; w < (int)kW; w++) {
+        const uint32_t h = hits_buf[w];
+        before += (w < warp) ? h : 0u;
+        total += h;
+        trips += trip_buf[w];
+      }
+      if (hit) {
+        const uint32_t slot = before + __popc(ballot & lane_lt);
+        p.hit_rec[tile * T + slot] = make_uint4((uint32_t)tid, post_off, post_cnt, 0u);
+      }
+      if (tid == 0) {
+        p.tile_nhit[tile] = total;
+        p.tile_ntrip[tile] = trips;
+      }
+    }
+  }
+}
+
+}  // namespace cvk

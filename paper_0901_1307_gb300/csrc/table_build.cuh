@@ -1,0 +1,201 @@
+// Device kernels that build the master signature table (paper Section 3.1: every master
+// sector's signature is inserted at the slot given by its low bits, collisions resolved by
+// linear probing, Eq. 3).
+//
+// Steps (one launch each):
+//   insert   one thread per master sector: claim the first free slot from the digest's home
+//            slot on (atomicCAS of an owner word), or join the slot that already holds an
+//            equal digest; record the slot, count its members, track the longest probe run.
+//   sort     stable LSD radix sort of (slot, master index) pairs by slot, so every slot's
+//            members end up contiguous and in master order, i.e. by (file_id, file_sector).
+//   fill     the sorted pairs become the postings; the first pair of each run writes its
+//            slot {digest, post_off, post_cnt}.
+//   bloom    every occupied slot sets its 8 bits in the blocked Bloom filter.
+// Which slot a digest lands in depends on thread timing; the lookup result does not.
+#pragma once
+#include <stdint.h>
+
+#include "cv_internal.h"
+
+namespace cvk {
+
+__global__ void insert_kernel(const uint4* dig, const uint8_t* trivial, uint64_t n, uint32_t* owner, uint32_t* cnt,
+                              uint32_t* slot_of, uint32_t mask, uint32_t* max_disp, uint32_t* n_kept,
+                              uint32_t* status) {
+  const uint32_t none = mask + 1u;
+  for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (uint64_t)gridDim.x * blockDim.x) {
+    if (trivial[m]) {
+      slot_of[m] = none;
+      continue;
+    }
+    const uint4 d = dig[m];
+    uint32_t idx = d.x & mask;
+    uint32_t c = 0;
+    bool placed = false;
+    for (; c <= mask; c++) {
+      const uint32_t prev = atomicCAS(owner + idx, 0u, (uint32_t)m + 1u);
+      if (prev == 0u) {
+        placed = true;
+        break;
+      }
+      const uint4 e = dig[prev - 1u];
+      if (e.x == d.x && e.y == d.y && e.z == d.z && e.w == d.w) {
+        placed = true;
+        break;
+      }
+      idx = (idx + 1u) & mask;
+    }
+    if (!placed) {
+      atomicOr(status, kStTableFull);
+      slot_of[m] = none;
+      continue;
+    }
+    slot_of[m] = idx;
+    atomicAdd(cnt + idx, 1u);
+    atomicMax(max_disp, c);
+    atomicAdd(n_kept, 1u);
+  }
+}
+
+__global__ void iota_kernel(uint32_t* v, uint64_t n) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    v[i] = (uint32_t)i;
+}
+
+// ------------------------------------------------------------------ stable radix sort pass
+constexpr int kRsThreads = 256;
+constexpr int kRsRounds = 16;
+constexpr int kRsChunk = kRsThreads * kRsRounds;
+
+// Digit histogram of each 4096-key chunk: hist[digit * n_blocks + block].
+__global__ void __launch_bounds__(kRsThreads) rs_hist_kernel(const uint32_t* keys, uint64_t n, int shift,
+                                                             uint32_t* hist, uint32_t n_blocks) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t base = (uint64_t)blockIdx.x * kRsChunk;
+  for (int r = 0; r < kRsRounds; r++) {
+    const uint64_t i = base + (uint64_t)r * kRsThreads + threadIdx.x;
+    if (i < n) atomicAdd(h + ((keys[i] >> shift) & 255u), 1u);
+  }
+  __syncthreads();
+  hist[(uint64_t)threadIdx.x * n_blocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// In-place exclusive scan of n u32 values whose total fits in 32 bits (one block).
+__global__ void __launch_bounds__(1024) exclusive_scan_u32_kernel(uint32_t* v, uint64_t n) {
+  __shared__ uint32_t warp_sum[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t per = (n + 1023) / 1024;
+  const uint64_t lo = per * tid < n ? per * tid : n;
+  const uint64_t hi = lo + per < n ? lo + per : n;
+  uint32_t sum = 0;
+  for (uint64_t i = lo; i < hi; i++) sum += v[i];
+  uint32_t incl = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t x = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if (lane >= d) incl += x;
+  }
+  if (lane == 31) warp_sum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = warp_sum[lane], wi = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      uint32_t x = __shfl_up_sync(0xFFFFFFFFu, wi, d);
+      if (lane >= d) wi += x;
+    }
+    warp_sum[lane] = wi - w;
+  }
+  __syncthreads();
+  uint32_t run = warp_sum[warp] + incl - sum;
+  for (uint64_t i = lo; i < hi; i++) {
+    const uint32_t x = v[i];
+    v[i] = run;
+    run += x;
+  }
+}
+
+// Scatter of one pass: the keys of a chunk go, in their original order within each digit, to
+// the chunk's offset for that digit (hist, after the scan).
+__global__ void __launch_bounds__(kRsThreads) rs_scatter_kernel(const uint32_t* kin, const uint32_t* vin,
+                                                                uint32_t* kout, uint32_t* vout, uint64_t n, int shift,
+                                                                const uint32_t* hist, uint32_t n_blocks) {
+  constexpr int kWarps = kRsThreads / 32;
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t wcnt[kWarps][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lane_lt = (1u << lane) - 1u;
+  run[tid] = hist[(uint64_t)tid * n_blocks + blockIdx.x];
+  const uint64_t base = (uint64_t)blockIdx.x * kRsChunk;
+  for (int r = 0; r < kRsRounds; r++) {
+#pragma unroll
+    for (int w = 0; w < kWarps; w++) wcnt[w][tid] = 0;
+    __syncthreads();
+    const uint64_t i = base + (uint64_t)r * kRsThreads + tid;
+    const bool valid = i < n;
+    const uint32_t key = valid ? kin[i] : 0u;
+    const uint32_t digit = valid ? ((key >> shift) & 255u) : 256u;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, digit);
+    const uint32_t rank = __popc(peers & lane_lt);
+    if (valid && rank == 0) wcnt[warp][digit] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = run[digit] + rank;
+      for (int w = 0; w < warp; w++) pos += wcnt[w][digit];
+      kout[pos] = key;
+      vout[pos] = vin[i];
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; w++) tot += wcnt[w][tid];
+    run[tid] += tot;
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------ fill
+// Sorted (slot, master index) pairs -> postings and slot records. file_base has n_files + 1
+// entries: the first master index of every file, then the total.
+__global__ void fill_kernel(const uint32_t* keys, const uint32_t* vals, uint64_t n, uint32_t n_slots,
+                            const uint32_t* owner, const uint32_t* cnt, const uint4* dig, const uint64_t* file_base,
+                            uint32_t n_files, uint4* slots, uint2* postings, uint32_t* n_unique) {
+  for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t key = keys[q];
+    if (key >= n_slots) continue;
+    const uint32_t m = vals[q];
+    uint32_t lo = 0, hi = n_files;  // largest f with file_base[f] <= m
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (file_base[mid] <= m) lo = mid; else hi = mid;
+    }
+    postings[q] = make_uint2(lo, (uint32_t)(m - file_base[lo]));
+    if (q == 0 || keys[q - 1] != key) {
+      slots[2ull * key] = dig[owner[key] - 1u];
+      slots[2ull * key + 1] = make_uint4((uint32_t)q, cnt[key], 0u, 0u);
+      atomicAdd(n_unique, 1u);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- Bloom
+__global__ void bloom_kernel(const uint4* slots, uint32_t n_slots, uint32_t* bloom, uint32_t bloom_mask) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += gridDim.x * blockDim.x) {
+    const uint4 val = slots[2ull * i + 1];
+    if (val.y == 0u) continue;
+    const uint4 d = slots[2ull * i];
+    uint32_t* blk = bloom + 8ull * (d.w & bloom_mask);
+    atomicOr(blk + 0, 1u << (d.y & 31));
+    atomicOr(blk + 1, 1u << ((d.y >> 5) & 31));
+    atomicOr(blk + 2, 1u << ((d.y >> 10) & 31));
+    atomicOr(blk + 3, 1u << ((d.y >> 15) & 31));
+    atomicOr(blk + 4, 1u << ((d.y >> 20) & 31));
+    atomicOr(blk + 5, 1u << ((d.y >> 25) & 31));
+    atomicOr(blk + 6, 1u << (d.z & 31));
+    atomicOr(blk + 7, 1u << ((d.z >> 5) & 31));
+  }
+}
+
+}  // namespace cvk

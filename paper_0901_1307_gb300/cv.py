@@ -1,0 +1,286 @@
+"""Python binding of libcv.so (include/cv.h): argument marshalling only.
+
+Every step of the scan runs in the library's CUDA kernels. There is no CPU path: if libcv.so is
+missing or no CUDA device is usable, the calls raise.
+
+Buffers can be given as torch tensors (CPU or CUDA), numpy arrays, bytes, or (pointer, n_bytes)
+tuples; streams as torch.cuda.Stream objects or raw cudaStream_t integers (None = default).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcv.so")
+
+CV_OK = 0
+CV_EINVAL = -1
+CV_ENOMEM = -2
+CV_ECUDA = -3
+CV_ETABLEFULL = -4
+CV_ECORRUPT = -5
+CV_ETIMEOUT = -6
+CV_ENODEV = -7
+CV_ERANGE = -8
+CV_BLOOM_AUTO = 0xFFFFFFFF
+CV_KEEP_ON_DEVICE = 1
+SECTOR = 512
+
+MATCH_DTYPE = np.dtype([("disk_sector", "<u8"), ("file_id", "<u4"), ("file_sector", "<u4")])
+
+EXPORTS = ("cv_master_build", "cv_master_get_info", "cv_scan", "cv_matches", "cv_scan_get_stats", "cv_free",
+           "cv_strerror", "cv_last_cuda_error", "cv_sector_digests", "cv_kernel_config_count",
+           "cv_kernel_config_name")
+
+
+class CVError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code}), last CUDA error {last_cuda_error()}")
+
+
+class cv_buf(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("n_bytes", ctypes.c_uint64)]
+
+
+class cv_master_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("max_load", ctypes.c_float),
+                ("bloom_bits_per_key", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("stream", ctypes.c_void_p)]
+
+
+class cv_scan_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("stream", ctypes.c_void_p),
+                ("chunk_bytes", ctypes.c_uint64), ("kernel_config", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class cv_master_info(ctypes.Structure):
+    _fields_ = [("n_files", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("n_sectors", ctypes.c_uint64),
+                ("n_kept", ctypes.c_uint64), ("n_unique", ctypes.c_uint64), ("n_slots", ctypes.c_uint64),
+                ("bloom_bytes", ctypes.c_uint64), ("max_probe", ctypes.c_uint32), ("reserved2", ctypes.c_uint32),
+                ("device_bytes", ctypes.c_uint64)]
+
+
+class cv_scan_stats(ctypes.Structure):
+    _fields_ = [("sectors", ctypes.c_uint64), ("matches", ctypes.c_uint64), ("hit_sectors", ctypes.c_uint64),
+                ("kernel_ms", ctypes.c_float), ("total_ms", ctypes.c_float)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcv.so and declare its signatures. Raises if the library was not built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with paper_0901_1307_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        lib.cv_master_build.argtypes = [ctypes.POINTER(cv_buf), u32, ctypes.POINTER(cv_master_opts), ctypes.POINTER(vp)]
+        lib.cv_master_build.restype = i32
+        lib.cv_master_get_info.argtypes = [vp, ctypes.POINTER(cv_master_info)]
+        lib.cv_master_get_info.restype = i32
+        lib.cv_scan.argtypes = [vp, ctypes.POINTER(cv_buf), u32, ctypes.POINTER(cv_scan_opts), ctypes.POINTER(vp)]
+        lib.cv_scan.restype = i32
+        lib.cv_matches.argtypes = [vp, u32, ctypes.POINTER(vp), ctypes.POINTER(u64)]
+        lib.cv_matches.restype = i32
+        lib.cv_scan_get_stats.argtypes = [vp, ctypes.POINTER(cv_scan_stats)]
+        lib.cv_scan_get_stats.restype = i32
+        lib.cv_free.argtypes = [vp]
+        lib.cv_free.restype = None
+        lib.cv_strerror.argtypes = [i32]
+        lib.cv_strerror.restype = ctypes.c_char_p
+        lib.cv_last_cuda_error.argtypes = []
+        lib.cv_last_cuda_error.restype = i32
+        lib.cv_sector_digests.argtypes = [vp, u64, vp, vp, vp]
+        lib.cv_sector_digests.restype = i32
+        lib.cv_kernel_config_count.argtypes = []
+        lib.cv_kernel_config_count.restype = i32
+        lib.cv_kernel_config_name.argtypes = [i32]
+        lib.cv_kernel_config_name.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    return load().cv_strerror(code).decode()
+
+
+def last_cuda_error() -> int:
+    return int(load().cv_last_cuda_error())
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != CV_OK:
+        raise CVError(rc, what)
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _buf(x):
+    """(pointer, n_bytes, keepalive) of a buffer-like object."""
+    if isinstance(x, tuple):
+        return int(x[0]), int(x[1]), None
+    if hasattr(x, "data_ptr") and hasattr(x, "element_size"):  # torch.Tensor
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return int(x.data_ptr()), int(x.numel() * x.element_size()), x
+    if isinstance(x, (bytes, bytearray, memoryview)):
+        x = np.frombuffer(bytes(x), np.uint8)
+    a = np.ascontiguousarray(x)
+    return (int(a.ctypes.data) if a.size else 0), int(a.nbytes), a
+
+
+def _bufs(xs):
+    keep = []
+    arr = (cv_buf * max(1, len(xs)))()
+    for i, x in enumerate(xs):
+        p, n, k = _buf(x)
+        arr[i].data = p
+        arr[i].n_bytes = n
+        keep.append(k)
+    return arr, keep
+
+
+class Master:
+    """A signature table of master files on the GPU (cv_master)."""
+
+    def __init__(self, handle: int):
+        self._h = handle
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def info(self) -> dict:
+        inf = cv_master_info()
+        _check(load().cv_master_get_info(self._h, ctypes.byref(inf)), "cv_master_get_info")
+        return {k: getattr(inf, k) for k, _ in cv_master_info._fields_ if not k.startswith("reserved")}
+
+    def close(self) -> None:
+        if self._h:
+            load().cv_free(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DeviceMatches:
+    """Matches of one image left in device memory; exposes __cuda_array_interface__ as an
+    (n, 2) uint64 array: column 0 = disk_sector, column 1 = file_id | file_sector << 32."""
+
+    def __init__(self, ptr: int, n: int, owner):
+        self.ptr, self.n, self._owner = ptr, n, owner
+
+    @property
+    def __cuda_array_interface__(self):
+        return {"shape": (self.n, 2), "typestr": "<u8", "data": (self.ptr or 0, False), "version": 3,
+                "strides": None}
+
+
+class Result:
+    """Sorted matches of every scanned image (cv_result)."""
+
+    def __init__(self, handle: int, n_images: int, on_device: bool):
+        self._h = handle
+        self.n_images = n_images
+        self.on_device = on_device
+
+    def _raw(self, i: int):
+        p = ctypes.c_void_p()
+        n = ctypes.c_uint64()
+        _check(load().cv_matches(self._h, i, ctypes.byref(p), ctypes.byref(n)), "cv_matches")
+        return p.value or 0, int(n.value)
+
+    def matches(self, i: int = 0):
+        """Image i's matches: a numpy structured array (host results) or DeviceMatches."""
+        p, n = self._raw(i)
+        if self.on_device:
+            return DeviceMatches(p, n, self)
+        if n == 0:
+            return np.zeros(0, MATCH_DTYPE)
+        buf = (ctypes.c_char * (n * 16)).from_address(p)
+        return np.frombuffer(buf, MATCH_DTYPE, count=n).copy()
+
+    def count(self, i: int = 0) -> int:
+        return self._raw(i)[1]
+
+    def stats(self) -> dict:
+        st = cv_scan_stats()
+        _check(load().cv_scan_get_stats(self._h, ctypes.byref(st)), "cv_scan_get_stats")
+        return {k: getattr(st, k) for k, _ in cv_scan_stats._fields_}
+
+    def close(self) -> None:
+        if self._h:
+            load().cv_free(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def master_build(files, max_load: float = 0.0, bloom_bits_per_key: int = CV_BLOOM_AUTO, stream=None) -> Master:
+    """cv_master_build: the signature table of a list of master files."""
+    arr, keep = _bufs(list(files))
+    o = cv_master_opts(ctypes.sizeof(cv_master_opts), max_load, bloom_bits_per_key, 0, _stream(stream))
+    h = ctypes.c_void_p()
+    _check(load().cv_master_build(arr, len(files), ctypes.byref(o), ctypes.byref(h)), "cv_master_build")
+    del keep
+    return Master(h.value)
+
+
+def kernel_configs() -> list:
+    """Names of the scan kernel configurations; index k is selected with kernel_config=k+1."""
+    lib = load()
+    return [lib.cv_kernel_config_name(k).decode() for k in range(lib.cv_kernel_config_count())]
+
+
+def scan(master: Master, images, keep_on_device: bool = False, stream=None, chunk_bytes: int = 0,
+         kernel_config: int = 0) -> Result:
+    """cv_scan: every match of every image against the master table."""
+    images = list(images)
+    arr, keep = _bufs(images)
+    o = cv_scan_opts(ctypes.sizeof(cv_scan_opts), CV_KEEP_ON_DEVICE if keep_on_device else 0, _stream(stream),
+                     chunk_bytes, kernel_config, 0)
+    h = ctypes.c_void_p()
+    _check(load().cv_scan(master.handle, arr, len(images), ctypes.byref(o), ctypes.byref(h)), "cv_scan")
+    del keep
+    return Result(h.value, len(images), keep_on_device)
+
+
+def sector_digests(in_ptr: int, n_sectors: int, out_ptr: int, trivial_ptr: int = 0, stream=None) -> None:
+    """cv_sector_digests: MD5 of n_sectors device sectors into device memory (asynchronous)."""
+    _check(load().cv_sector_digests(in_ptr, n_sectors, out_ptr, trivial_ptr or None, _stream(stream)),
+           "cv_sector_digests")
