@@ -225,25 +225,38 @@ struct Job {
   }
 };
 
-// Launch the scan (or digest) kernel over segments [s0, s1) of the job.
-int launch_range(DevCtx* ctx, int cfg_i, bool digest, const Job& job, size_t s0, size_t s1, const CUtensorMap* maps_d,
-                 const Segment* segs_d, ScanParams base_params, cudaStream_t stream) {
-  if (s1 <= s0) return CV_OK;
+// Launch the scan (or digest) kernel over segments [s0, s1) of the job, at most kSegsPerLaunch
+// segments per launch. `base` carries the table and the output pointers.
+int launch_range(DevCtx* ctx, int cfg_i, bool digest, const Job& job, size_t s0, size_t s1, const ScanParams& base,
+                 cudaStream_t stream) {
   int n;
   const ScanCfg& cfg = scan_configs(&n)[cfg_i];
-  ScanParams p = base_params;
-  p.tmaps = maps_d + s0;
-  p.segs = segs_d + s0;
-  p.n_segs = (uint32_t)(s1 - s0);
-  p.tile_begin = job.segs[s0].tile_base;
-  const uint64_t tile_end = (s1 < job.segs.size()) ? job.segs[s1].tile_base : job.n_tiles;
-  p.n_tiles = tile_end - p.tile_begin;
-  if (p.n_tiles == 0) return CV_OK;
   const int bps = digest ? ctx->blocks_per_sm_digest[cfg_i] : ctx->blocks_per_sm[cfg_i];
-  const uint64_t grid = std::min<uint64_t>(p.n_tiles, (uint64_t)ctx->sms * bps);
-  void* args[] = {&p};
-  CV_CUDA(cudaLaunchKernel(digest ? cfg.digest_fn : cfg.scan_fn, dim3((unsigned)grid), dim3(cfg.T + 32), args,
-                           cfg.smem, stream));
+  for (size_t a = s0; a < s1; a += kSegsPerLaunch) {
+    const size_t b = std::min(s1, a + (size_t)kSegsPerLaunch);
+    ScanParams p;
+    memset(&p, 0, sizeof p);
+    p.tab = base.tab;
+    p.hit_rec = base.hit_rec;
+    p.tile_nhit = base.tile_nhit;
+    p.tile_ntrip = base.tile_ntrip;
+    p.status = base.status;
+    p.digests = base.digests;
+    p.trivial = base.trivial;
+    for (size_t k = a; k < b; k++) {
+      p.maps[k - a] = job.maps[k];
+      p.segs[k - a] = job.segs[k];
+    }
+    p.n_segs = (uint32_t)(b - a);
+    p.tile_begin = job.segs[a].tile_base;
+    const uint64_t tile_end = (b < job.segs.size()) ? job.segs[b].tile_base : job.n_tiles;
+    p.n_tiles = tile_end - p.tile_begin;
+    if (p.n_tiles == 0) continue;
+    const uint64_t grid = std::min<uint64_t>(p.n_tiles, (uint64_t)ctx->sms * bps);
+    void* args[] = {&p};
+    CV_CUDA(cudaLaunchKernel(digest ? cfg.digest_fn : cfg.scan_fn, dim3((unsigned)grid), dim3(cfg.T + 32), args,
+                             cfg.smem, stream));
+  }
   return CV_OK;
 }
 
@@ -280,7 +293,8 @@ struct cv_result {
   uint32_t n_images;
   std::vector<uint64_t> off;  // n_images + 1
   MatchOut* host;
-  MatchOut* dev_out;
+  MatchOut* dev_out;     // from the library's pool, released on free_stream
+  cudaStream_t free_stream;
   cv_scan_stats st;
 };
 
@@ -318,20 +332,14 @@ const char* cv_kernel_config_name(int k) {
 
 static int digest_job(DevCtx* ctx, Job& job, uint4* digests, uint8_t* trivial, uint32_t* status, cudaStream_t stream,
                       Temps& tmp) {
+  (void)tmp;
   const int cfg_i = ctx->cfg_index;
-  CUtensorMap* maps_d;
-  Segment* segs_d;
-  CV_TRY(tmp.alloc(&maps_d, job.maps.size() * sizeof(CUtensorMap)));
-  CV_TRY(tmp.alloc(&segs_d, job.segs.size() * sizeof(Segment)));
-  CV_CUDA(cudaMemcpyAsync(maps_d, job.maps.data(), job.maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
-                          stream));
-  CV_CUDA(cudaMemcpyAsync(segs_d, job.segs.data(), job.segs.size() * sizeof(Segment), cudaMemcpyHostToDevice, stream));
   ScanParams p;
   memset(&p, 0, sizeof p);
   p.status = status;
   p.digests = digests;
   p.trivial = trivial;
-  CV_TRY(launch_range(ctx, cfg_i, true, job, 0, job.segs.size(), maps_d, segs_d, p, stream));
+  CV_TRY(launch_range(ctx, cfg_i, true, job, 0, job.segs.size(), p, stream));
   return CV_OK;
 }
 
@@ -496,6 +504,18 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
   return CV_OK;
 }
 
+}  // extern "C"
+
+// Device view of a master table for other translation units of the library.
+int cvk_master_view(const cv_master* m, TableView* tab, int* dev) {
+  if (!m || m->magic != kMagicMaster) return CV_EINVAL;
+  *tab = m->tab;
+  *dev = m->dev;
+  return CV_OK;
+}
+
+extern "C" {
+
 int cv_master_get_info(const cv_master* m, cv_master_info* info) {
   if (!m || !info || m->magic != kMagicMaster) return CV_EINVAL;
   *info = m->info;
@@ -562,6 +582,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
   r->off.assign(n_images + 1, 0);
   r->host = nullptr;
   r->dev_out = nullptr;
+  r->free_stream = stream;
   memset(&r->st, 0, sizeof r->st);
   r->st.sectors = job.n_sectors;
 
@@ -596,12 +617,10 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
             CV_TRY(make_tmap(ctx, cfg, ring[k & 1], job.segs[s].n_sectors, &job.maps[s]));
           }
         }
-        CUtensorMap* maps_d;
         Segment* segs_d;
         uint4* hit_rec;
         uint32_t *tile_nhit, *status;
         uint64_t *tile_ntrip, *tile_off, *seg_off_d;
-        CV_TRY(tmp.alloc(&maps_d, nseg * sizeof(CUtensorMap)));
         CV_TRY(tmp.alloc(&segs_d, nseg * sizeof(Segment)));
         CV_TRY(tmp.alloc(&hit_rec, nt * cfg.T * sizeof(uint4)));
         CV_TRY(tmp.alloc(&tile_nhit, nt * 4));
@@ -611,7 +630,6 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         status = (uint32_t*)(seg_off_d + nseg + 1);
         status_keep = status;
         CV_CUDA(cudaMemsetAsync(status, 0, 8, stream));
-        CV_CUDA(cudaMemcpyAsync(maps_d, job.maps.data(), nseg * sizeof(CUtensorMap), cudaMemcpyHostToDevice, stream));
         CV_CUDA(cudaMemcpyAsync(segs_d, job.segs.data(), nseg * sizeof(Segment), cudaMemcpyHostToDevice, stream));
         ScanParams p;
         memset(&p, 0, sizeof p);
@@ -633,14 +651,14 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
                                     ctx->copy_stream));
             CV_CUDA(cudaEventRecord(ring_copied[b], ctx->copy_stream));
             CV_CUDA(cudaStreamWaitEvent(stream, ring_copied[b], 0));
-            CV_TRY(launch_range(ctx, cfg_i, false, job, s, s + 1, maps_d, segs_d, p, stream));
+            CV_TRY(launch_range(ctx, cfg_i, false, job, s, s + 1, p, stream));
             CV_CUDA(cudaEventRecord(ring_free[b], stream));
             hk++;
             s++;
           } else {
             size_t e = s;
             while (e < nseg && !(hk < hchunks.size() && hchunks[hk].seg == e)) e++;
-            CV_TRY(launch_range(ctx, cfg_i, false, job, s, e, maps_d, segs_d, p, stream));
+            CV_TRY(launch_range(ctx, cfg_i, false, job, s, e, p, stream));
             s = e;
           }
         }
@@ -648,8 +666,10 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         uint64_t* total_d = seg_off_d + nseg;
         uint32_t nseg32 = (uint32_t)nseg;
         uint64_t nt_arg = nt;
-        void* targs[] = {&tile_ntrip, &nt_arg, &tile_off, &segs_d, &nseg32, &seg_off_d, &total_d};
-        CV_CUDA(cudaLaunchKernel(tile_offsets_fn(), dim3(1), dim3(1024), targs, 0, stream));
+        uint64_t* off_scratch;
+        CV_TRY(tmp.alloc(&off_scratch, tile_offsets_scratch_words(nt) * 8));
+        CV_CUDA((cudaError_t)launch_tile_offsets(tile_ntrip, nt, tile_off, segs_d, nseg32, seg_off_d, total_d,
+                                                 off_scratch, stream));
         CV_CUDA(cudaMemcpyAsync(seg_off.data(), seg_off_d, (nseg + 2) * 8, cudaMemcpyDeviceToHost, stream));
         CV_CUDA(cudaStreamSynchronize(stream));
         const uint32_t st = (uint32_t)seg_off[nseg + 1];
@@ -657,7 +677,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         if (st) return CV_ECORRUPT;
         total = seg_off[nseg];
         if (total) {
-          CV_CUDA(cudaMalloc(&r->dev_out, total * sizeof(MatchOut)));
+          CV_CUDA(cudaMallocFromPoolAsync((void**)&r->dev_out, total * sizeof(MatchOut), ctx->pool, stream));
           const unsigned eg = grid_for(nt * 32, 256, ctx->sms);
           uint64_t cap = total;
           const uint2* postings = m->tab.postings;
@@ -676,13 +696,11 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         if (!r->host) return CV_ENOMEM;
         CV_CUDA(cudaMemcpyAsync(r->host, r->dev_out, total * sizeof(MatchOut), cudaMemcpyDeviceToHost, stream));
       }
+      uint32_t st2 = 0;
+      if (nseg && total) CV_CUDA(cudaMemcpyAsync(&st2, status_keep, 4, cudaMemcpyDeviceToHost, stream));
       CV_CUDA(cudaEventRecord(ev[3], stream));
       CV_CUDA(cudaStreamSynchronize(stream));
-      if (nseg && total) {
-        uint32_t st2 = 0;
-        CV_CUDA(cudaMemcpy(&st2, (const uint8_t*)status_keep + 0, 4, cudaMemcpyDeviceToHost));
-        if (st2) return CV_ECORRUPT;
-      }
+      if (st2) return CV_ECORRUPT;
       float ms = 0.f;
       if (nseg) {
         CV_CUDA(cudaEventElapsedTime(&ms, ev[1], ev[2]));
@@ -691,7 +709,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
       CV_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[3]));
       r->st.total_ms = ms;
       if (total && !r->on_device) {
-        cudaFree(r->dev_out);
+        CV_CUDA(cudaFreeAsync(r->dev_out, stream));
         r->dev_out = nullptr;
       }
       return CV_OK;
@@ -743,7 +761,10 @@ void cv_free(void* handle) {
   } else if (magic == kMagicResult) {
     cv_result* r = (cv_result*)handle;
     r->magic = 0;
-    if (r->dev_out) cudaFree(r->dev_out);
+    if (r->dev_out) {
+      cudaFreeAsync(r->dev_out, r->free_stream);
+      cudaStreamSynchronize(r->free_stream);
+    }
     free(r->host);
     delete r;
   }

@@ -12,51 +12,91 @@
 
 namespace cvk {
 
-constexpr int kScanThreads = 1024;
+// Exclusive scan of the per-tile triple counts in three coalesced passes: chunk sums, a scan
+// of the chunk sums (one block), and the scan within each chunk plus its chunk offset. A fourth
+// small pass reads off each segment's first offset. No block waits on another.
+constexpr int kOffThreads = 1024;
+constexpr int kOffItems = 4;
+constexpr uint64_t kOffChunk = (uint64_t)kOffThreads * kOffItems;
 
-// Exclusive scan of tile_ntrip[0..n) into tile_off, the grand total into *total, and the
-// offset of every segment's first tile into seg_off[0..n_segs) (one block of 1024 threads).
-__global__ void __launch_bounds__(kScanThreads) tile_offsets_kernel(const uint64_t* tile_ntrip, uint64_t n,
-                                                                    uint64_t* tile_off, const Segment* segs,
-                                                                    uint32_t n_segs, uint64_t* seg_off,
-                                                                    uint64_t* total) {
-  __shared__ uint64_t warp_sum[kScanThreads / 32];
-  __shared__ uint64_t carry;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint64_t per = (n + kScanThreads - 1) / kScanThreads;
-  const uint64_t lo = per * tid < n ? per * tid : n;
-  const uint64_t hi = lo + per < n ? lo + per : n;
-  uint64_t sum = 0;
-  for (uint64_t i = lo; i < hi; i++) sum += tile_ntrip[i];
-  // block-wide exclusive scan of the per-thread sums
-  uint64_t incl = sum;
+// Block-wide inclusive scan of one u64 per thread (1024 threads).
+__device__ __forceinline__ uint64_t block_inclusive_scan(uint64_t x, uint64_t* warp_buf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    uint64_t v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-    if (lane >= d) incl += v;
+    const uint64_t v = __shfl_up_sync(0xFFFFFFFFu, x, d);
+    if (lane >= d) x += v;
   }
-  if (lane == 31) warp_sum[warp] = incl;
+  if (lane == 31) warp_buf[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    uint64_t w = warp_sum[lane];
-    uint64_t wi = w;
+    uint64_t w = warp_buf[lane];
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      uint64_t v = __shfl_up_sync(0xFFFFFFFFu, wi, d);
-      if (lane >= d) wi += v;
+      const uint64_t v = __shfl_up_sync(0xFFFFFFFFu, w, d);
+      if (lane >= d) w += v;
     }
-    warp_sum[lane] = wi - w;
-    if (lane == 31) carry = wi;
+    warp_buf[lane] = w;  // inclusive over warps
   }
   __syncthreads();
-  uint64_t run = warp_sum[warp] + incl - sum;
-  for (uint64_t i = lo; i < hi; i++) {
-    tile_off[i] = run;
-    run += tile_ntrip[i];
+  return x + (warp ? warp_buf[warp - 1] : 0ull);
+}
+
+__global__ void __launch_bounds__(kOffThreads) chunk_sums_kernel(const uint64_t* v, uint64_t n, uint64_t* sums) {
+  __shared__ uint64_t wb[32];
+  const uint64_t base = (uint64_t)blockIdx.x * kOffChunk;
+  uint64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kOffItems; k++) {
+    const uint64_t i = base + (uint64_t)k * kOffThreads + threadIdx.x;
+    if (i < n) s += v[i];
   }
+  const uint64_t incl = block_inclusive_scan(s, wb);
+  if (threadIdx.x == kOffThreads - 1) sums[blockIdx.x] = incl;
+}
+
+// In place: sums[0..m) -> exclusive offsets; *total = the sum of all.
+__global__ void __launch_bounds__(kOffThreads) scan_sums_kernel(uint64_t* sums, uint64_t m, uint64_t* total) {
+  __shared__ uint64_t wb[32];
+  __shared__ uint64_t carry;
+  if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  if (tid == 0) *total = carry;
-  for (uint32_t s = tid; s < n_segs; s += kScanThreads) seg_off[s] = segs[s].tile_base < n ? tile_off[segs[s].tile_base] : carry;
+  for (uint64_t base = 0; base < m; base += kOffThreads) {
+    const uint64_t i = base + threadIdx.x;
+    const uint64_t x = i < m ? sums[i] : 0ull;
+    const uint64_t incl = block_inclusive_scan(x, wb);
+    const uint64_t c = carry;
+    if (i < m) sums[i] = c + incl - x;
+    __syncthreads();
+    if (threadIdx.x == kOffThreads - 1) carry = c + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kOffThreads) chunk_scan_kernel(const uint64_t* v, uint64_t n, const uint64_t* offs,
+                                                                 uint64_t* out) {
+  __shared__ uint64_t wb[32];
+  const uint64_t first = (uint64_t)blockIdx.x * kOffChunk + (uint64_t)threadIdx.x * kOffItems;
+  uint64_t x[kOffItems];
+  uint64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kOffItems; k++) {
+    x[k] = (first + k < n) ? v[first + k] : 0ull;
+    s += x[k];
+  }
+  uint64_t run = block_inclusive_scan(s, wb) - s + offs[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kOffItems; k++) {
+    if (first + k < n) out[first + k] = run;
+    run += x[k];
+  }
+}
+
+__global__ void segment_offsets_kernel(const uint64_t* tile_off, uint64_t n, const Segment* segs, uint32_t n_segs,
+                                       const uint64_t* total, uint64_t* seg_off) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_segs; s += gridDim.x * blockDim.x)
+    seg_off[s] = segs[s].tile_base < n ? tile_off[segs[s].tile_base] : *total;
 }
 
 // One warp per tile with hits. out_cap bounds the writes (kStOverflow when exceeded).

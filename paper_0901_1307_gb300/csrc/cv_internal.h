@@ -42,15 +42,21 @@ struct TableView {
   uint32_t use_bloom;
 };
 
+// Segments (and their tensor maps) one launch of the scan kernel can cover.
+constexpr int kSegsPerLaunch = 128;
+
+// Parameters of one scan-kernel launch, passed by value as a __grid_constant__ kernel
+// parameter: the TMA unit reads the tensor maps straight from the parameter space, so no
+// descriptor ever lives in (reused) global memory.
 struct ScanParams {
-  const CUtensorMap* tmaps;  // one per segment, 64-byte aligned device memory
-  const Segment* segs;
+  CUtensorMap maps[kSegsPerLaunch];  // one per segment of this launch (64-byte aligned)
+  Segment segs[kSegsPerLaunch];      // tile_base values are global tile indices
   uint32_t n_segs;
   uint32_t pad;
   uint64_t tile_begin;  // global index of the first tile of this launch
   uint64_t n_tiles;     // tiles of this launch
   TableView tab;
-  // scan outputs
+  // scan outputs, indexed by global tile
   uint4* hit_rec;        // n_tiles * T records {sector_in_tile, post_off, post_cnt, 0}
   uint32_t* tile_nhit;   // hit sectors per tile
   uint64_t* tile_ntrip;  // triples per tile

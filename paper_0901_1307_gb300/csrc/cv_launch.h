@@ -16,6 +16,15 @@ struct ScanCfg {
 };
 
 const ScanCfg* scan_configs(int* n);
-const void* tile_offsets_fn();
+
+struct Segment;
+
+// Scratch (u64 words) the offset pass needs for n tiles.
+uint64_t tile_offsets_scratch_words(uint64_t n_tiles);
+
+// tile_off[i] = sum of tile_ntrip[0..i); *total = sum of all; seg_off[s] = offset of segment
+// s's first tile. scratch: tile_offsets_scratch_words(n_tiles) u64 words. Returns a CUDA error.
+int launch_tile_offsets(const uint64_t* tile_ntrip, uint64_t n_tiles, uint64_t* tile_off, const Segment* segs,
+                        uint32_t n_segs, uint64_t* seg_off, uint64_t* total, uint64_t* scratch, void* stream);
 
 }  // namespace cvk

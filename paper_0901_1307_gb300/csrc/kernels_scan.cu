@@ -26,6 +26,18 @@ const ScanCfg* scan_configs(int* n) {
   return kConfigs;
 }
 
-const void* tile_offsets_fn() { return (const void*)tile_offsets_kernel; }
+uint64_t tile_offsets_scratch_words(uint64_t n_tiles) { return (n_tiles + kOffChunk - 1) / kOffChunk + 1; }
+
+int launch_tile_offsets(const uint64_t* tile_ntrip, uint64_t n_tiles, uint64_t* tile_off, const Segment* segs,
+                        uint32_t n_segs, uint64_t* seg_off, uint64_t* total, uint64_t* scratch, void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  const uint64_t chunks = (n_tiles + kOffChunk - 1) / kOffChunk;
+  if (chunks) chunk_sums_kernel<<<(unsigned)chunks, kOffThreads, 0, stream>>>(tile_ntrip, n_tiles, scratch);
+  scan_sums_kernel<<<1, kOffThreads, 0, stream>>>(scratch, chunks, total);
+  if (chunks) chunk_scan_kernel<<<(unsigned)chunks, kOffThreads, 0, stream>>>(tile_ntrip, n_tiles, scratch, tile_off);
+  if (n_segs) segment_offsets_kernel<<<(n_segs + 255) / 256, 256, 0, stream>>>(tile_off, n_tiles, segs, n_segs, total,
+                                                                               seg_off);
+  return (int)cudaGetLastError();
+}
 
 }  // namespace cvk

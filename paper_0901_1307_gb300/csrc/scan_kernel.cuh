@@ -146,7 +146,7 @@ struct ScanSmem {
 // T: sectors per tile (= hashing threads); NS: ring stages; BOXB: bytes of each sector row per
 // stage (64 or 128). Block size is T + 32 (the last warp is the producer).
 template <int T, int NS, int BOXB, int MODE>
-__global__ void __launch_bounds__(T + 32) scan_kernel(const ScanParams p) {
+__global__ void __launch_bounds__(T + 32) scan_kernel(const __grid_constant__ ScanParams p) {
   static_assert(T % 32 == 0 && T <= 256, "tile rows");
   static_assert(BOXB == 64 || BOXB == 128, "box width");
   using L = ScanSmem<T, NS, BOXB>;
@@ -187,10 +187,7 @@ __global__ void __launch_bounds__(T + 32) scan_kernel(const ScanParams p) {
     for (uint64_t lt = blockIdx.x; lt < p.n_tiles && ok; lt += gridDim.x) {
       const uint64_t tile = p.tile_begin + lt;
       const uint32_t sg = find_segment(p.segs, p.n_segs, tile);
-      const CUtensorMap* map = p.tmaps + sg;
-      // the maps were written to global memory by a copy: make them visible to the TMA unit
-      asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
-                   : "memory");
+      const CUtensorMap* map = &p.maps[sg];
       const int32_t row0 = (int32_t)((tile - p.segs[sg].tile_base) * T);
       for (int c = 0; c < kChunks; c++, j++) {
         const uint32_t s = j % NS;
@@ -251,7 +248,12 @@ __global__ void __launch_bounds__(T + 32) scan_kernel(const ScanParams p) {
           X[4 * q + 2] = v.z;
           X[4 * q + 3] = v.w;
         }
-        if (b == kBlocksPerChunk - 1) mbar_arrive(bar_empty + 8 * s);
+        if (b == kBlocksPerChunk - 1) {
+          // The stage is handed back to the copy engine: order this thread's shared-memory
+          // reads (generic proxy) before the next TMA write into the stage (async proxy).
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(bar_empty + 8 * s);
+        }
         if constexpr (MODE == kModeDigest) {
           if (c == 0 && b == 0) ref = (X[0] & 0xFFu) * 0x01010101u;
 #pragma unroll

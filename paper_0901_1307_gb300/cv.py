@@ -284,3 +284,4 @@ def sector_digests(in_ptr: int, n_sectors: int, out_ptr: int, trivial_ptr: int =
     """cv_sector_digests: MD5 of n_sectors device sectors into device memory (asynchronous)."""
     _check(load().cv_sector_digests(in_ptr, n_sectors, out_ptr, trivial_ptr or None, _stream(stream)),
            "cv_sector_digests")
+

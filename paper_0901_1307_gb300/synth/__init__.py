@@ -286,6 +286,7 @@ def config_plan(name: str) -> Plan:
             (32-512 sectors); 40% of each file's clusters planted, 10% of those partly overwritten.
     scale : 32 GiB image (67,108,864 sectors), seed 1; 20,000 master files with log-uniform
             8 KiB-1 MiB sizes scaled to 4,194,304 sectors in total (minimum 16); 25% planted.
+    mid   : 4 GiB image (8,388,608 sectors), seed 6; 1,250 such files scaled to 262,144 sectors.
     """
     if name == "tiny":
         rng = np.random.default_rng(0)
@@ -296,6 +297,13 @@ def config_plan(name: str) -> Plan:
         raw = log_uniform_sizes(rng, 20000, 8 << 10, 1 << 20) / SECTOR
         nsect = scale_to_total(raw, 4194304, 16)
         return make_plan(1, 67108864, nsect, 0.25)
+    if name == "mid":
+        # a 4 GiB image against 262,144 master sectors: the scale workload's mix at 1/8 of the
+        # image and 1/16 of the masters, for profiling runs
+        rng = np.random.default_rng(6)
+        raw = log_uniform_sizes(rng, 1250, 8 << 10, 1 << 20) / SECTOR
+        nsect = scale_to_total(raw, 262144, 16)
+        return make_plan(6, 8388608, nsect, 0.25)
     if name.startswith("small:"):
         # small:<sectors>:<files>:<seed> -- a scaled-down image for fast tests
         _, ns, nf, seed = name.split(":")

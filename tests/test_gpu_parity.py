@@ -29,6 +29,17 @@ def dev(a: np.ndarray):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+def assert_same(got, want, what=""):
+    """Bit-exact comparison of two sorted triple arrays, naming the differences on failure."""
+    if np.array_equal(got, want):
+        return
+    g = set(map(tuple, np.stack([got["disk_sector"], got["file_id"], got["file_sector"]], 1).tolist()))
+    w = set(map(tuple, np.stack([want["disk_sector"], want["file_id"], want["file_sector"]], 1).tolist()))
+    miss, extra = sorted(w - g), sorted(g - w)
+    raise AssertionError(f"{what}: got {got.size} want {want.size}; missing {len(miss)} {miss[:16]}; "
+                         f"extra {len(extra)} {extra[:16]}; order ok={sorted(g) == [tuple(x) for x in got.tolist()]}")
+
+
 def gpu_digests(cv, img_t, n):
     out = torch.empty(max(n, 1) * 16, dtype=torch.uint8, device="cuda")
     triv = torch.empty(max(n, 1), dtype=torch.uint8, device="cuda")
@@ -113,9 +124,9 @@ def test_scan_tricky_cases(cv, seed):
     want = oracle.match_brute(image, files)
     with cv.master_build(files) as m:
         with cv.scan(m, [dev(image)]) as r:
-            assert np.array_equal(r.matches(0), want)
+            assert_same(r.matches(0), want)
         with cv.scan(m, [image]) as r:  # host image, streamed
-            assert np.array_equal(r.matches(0), want)
+            assert_same(r.matches(0), want)
 
 
 def test_scan_tiny_workload_full(cv):
@@ -129,9 +140,9 @@ def test_scan_tiny_workload_full(cv):
         info = m.info()
         assert info["n_kept"] == plan.n_master_sectors and info["n_unique"] == plan.n_master_sectors
         with cv.scan(m, [dev(img)]) as r:
-            assert np.array_equal(r.matches(0), want)
+            assert_same(r.matches(0), want)
         with cv.scan(m, [img], chunk_bytes=3 * 1024 * 1024 + 512) as r:  # 22 ragged chunks
-            assert np.array_equal(r.matches(0), want)
+            assert_same(r.matches(0), want)
 
 
 @pytest.mark.parametrize("cfg_k", range(5))
@@ -144,7 +155,7 @@ def test_every_kernel_config_same_result(cv, cfg_k):
     files = plan.masters_host()
     want = oracle.match_hash(img, files)
     with cv.master_build(files) as m, cv.scan(m, [dev(img)], kernel_config=cfg_k + 1) as r:
-        assert np.array_equal(r.matches(0), want), names[cfg_k]
+        assert_same(r.matches(0), want, names[cfg_k])
 
 
 @pytest.mark.parametrize("max_load,bloom", [(0.5, 0), (0.9, 0xFFFFFFFF), (0.25, 8), (0.9, 0)])
@@ -157,7 +168,7 @@ def test_table_options_do_not_change_result(cv, max_load, bloom):
     want = oracle.match_hash(img, files)
     with cv.master_build(files, max_load=max_load, bloom_bits_per_key=bloom) as m:
         with cv.scan(m, [dev(img)]) as r:
-            assert np.array_equal(r.matches(0), want)
+            assert_same(r.matches(0), want)
 
 
 def test_many_images_uneven_sizes(cv):
@@ -176,7 +187,7 @@ def test_many_images_uneven_sizes(cv):
             images.append(piece)  # host buffers, also the misaligned one
     with cv.master_build(files) as m, cv.scan(m, images) as r:
         for k in range(len(cuts)):
-            assert np.array_equal(r.matches(k), wants[k]), k
+            assert_same(r.matches(k), wants[k], str(k))
 
 
 def test_empty_master_set_and_trivial_only(cv):
