@@ -163,6 +163,30 @@ int cv_last_cuda_error(void);
  */
 int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t* trivial, void* stream);
 
+/*
+ * Scan one device-resident image without allocating any memory. The paper has no counterpart:
+ * this is for callers that cannot allocate while they work, such as a real-time ingest loop
+ * handing over fixed buffers, or a process whose device memory is fully reserved by another
+ * allocator at start-up, where cudaMalloc could block, fail or synchronize the device.
+ *
+ * Instead of a memory pool it uses one fixed scratch array built into the library (a little
+ * over 8 MiB, resident on every GPU that loads the library until the process exits).
+ *   image        device pointer, 16-byte aligned; n_bytes / 512 whole sectors are scanned, at
+ *                most CV_NOALLOC_MAX_SECTORS (256 MiB of image), else CV_EINVAL.
+ *   out          device pointer, 16-byte aligned, room for out_capacity cv_match entries; the
+ *                sorted matches are written there.
+ *   *n_out       (host) the number of matches. If it exceeds out_capacity, only out_capacity
+ *                entries are written and CV_ERANGE is returned: call again with more room.
+ * Runs on stream and returns after the work has finished. Every call shares the one scratch
+ * array and finds the previous call's contents there; calls whose work could overlap on the
+ * GPU must be serialized by the caller. The first call on a device performs a one-time set-up
+ * (the array's device address, kernel attributes); make it before any stream capture.
+ * Errors: CV_EINVAL, CV_ERANGE, CV_ECUDA, CV_ETIMEOUT, CV_ECORRUPT, CV_ENODEV.
+ */
+#define CV_NOALLOC_MAX_SECTORS (1u << 19)
+int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n_bytes, cv_match* out, uint64_t out_capacity,
+                    uint64_t* n_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

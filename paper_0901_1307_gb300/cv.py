@@ -34,7 +34,8 @@ MATCH_DTYPE = np.dtype([("disk_sector", "<u8"), ("file_id", "<u4"), ("file_secto
 
 EXPORTS = ("cv_master_build", "cv_master_get_info", "cv_scan", "cv_matches", "cv_scan_get_stats", "cv_free",
            "cv_strerror", "cv_last_cuda_error", "cv_sector_digests", "cv_kernel_config_count",
-           "cv_kernel_config_name")
+           "cv_kernel_config_name", "cv_scan_noalloc")
+CV_NOALLOC_MAX_SECTORS = 1 << 19
 
 
 class CVError(RuntimeError):
@@ -105,6 +106,8 @@ def load(path: str = LIB_PATH):
         lib.cv_kernel_config_count.restype = i32
         lib.cv_kernel_config_name.argtypes = [i32]
         lib.cv_kernel_config_name.restype = ctypes.c_char_p
+        lib.cv_scan_noalloc.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(u64), vp]
+        lib.cv_scan_noalloc.restype = i32
         _lib = lib
         return lib
 
@@ -285,3 +288,15 @@ def sector_digests(in_ptr: int, n_sectors: int, out_ptr: int, trivial_ptr: int =
     _check(load().cv_sector_digests(in_ptr, n_sectors, out_ptr, trivial_ptr or None, _stream(stream)),
            "cv_sector_digests")
 
+
+def scan_noalloc(master: Master, image, out, out_capacity: int, stream=None, check: bool = True):
+    """cv_scan_noalloc: scan one device image into a caller-owned device buffer of
+    out_capacity matches, without any allocation. Returns (return code, match count); raises
+    on any code other than CV_OK and CV_ERANGE when check is set."""
+    ip, nb, _k1 = _buf(image)
+    op, _, _k2 = _buf(out)
+    n = ctypes.c_uint64()
+    rc = load().cv_scan_noalloc(master.handle, ip, nb, op, out_capacity, ctypes.byref(n), _stream(stream))
+    if check and rc not in (CV_OK, CV_ERANGE):
+        raise CVError(rc, "cv_scan_noalloc")
+    return rc, int(n.value)
