@@ -126,21 +126,26 @@ def setup_workload(torch, cv, synth, name: str, seed_offset: int):
     return plan, image, master, build_s
 
 
-def cpu_baseline(plan, sample_sectors: int, first: int = 0):
+def cpu_baseline(plan, pieces: int):
+    """The oracle's lookup timed on `pieces` 1 GiB windows of the image at seeded offsets."""
     import oracle
 
     files = plan.masters_host()
     db = oracle.OracleDB(files)
-    img = plan.image_host(first, sample_sectors)
-    t0 = time.perf_counter()
-    got = db.lookup(img, first)
-    dt = time.perf_counter() - t0
+    n = min(1 << 21, plan.n_sectors)
+    rng = np.random.default_rng(12345)
+    starts = sorted(rng.integers(0, plan.n_sectors - n + 1, size=pieces).tolist())
+    secs, found = 0.0, 0
+    for s in starts:
+        img = plan.image_host(int(s), n)
+        t0 = time.perf_counter()
+        found += db.lookup(img, int(s)).size
+        secs += time.perf_counter() - t0
     db.close()
-    return {"value": sample_sectors * SECTOR / dt / 1e9, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"sectors [{first}, {first + sample_sectors}) of the image "
-                      f"({sample_sectors * SECTOR / 2**30:.2f} GiB), lookup only (signature database of "
-                      f"{plan.n_master_sectors} master sectors built untimed)",
-            "matches_in_sample": int(got.size), "seconds": dt}
+    return {"value": pieces * n * SECTOR / secs / 1e9, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{pieces} windows of {n} sectors ({n * SECTOR / 2**30:.0f} GiB each) at seeded offsets of "
+                      f"the image; lookup only, signature database of {plan.n_master_sectors} master sectors "
+                      f"built untimed", "matches_in_sample": found, "seconds": secs}
 
 
 def run_reference(args):
@@ -180,19 +185,192 @@ def run_reference(args):
     return 0
 
 
+def device_plan(torch, synth, plan):
+    """Device copies of a plan's arrays (the generator reads them); keep the list alive."""
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    keep = [dev(plan.plant_file.view(np.uint8)), dev(plan.plant_fcluster.view(np.uint8)), dev(plan.plant_over),
+            dev(plan.file_nsect.view(np.uint8)), dev(synth.vocab(plan.image_seed))]
+    return tuple(k.data_ptr() for k in keep), keep
+
+
+def build_master_set(torch, cv, synth, name):
+    """The named master set generated on the device and built into a table."""
+    file_nsect, mseed = synth.master_set(name)
+    mplan = synth.Plan(0, mseed, 0, file_nsect, np.zeros(0, np.int32), np.zeros(0, np.uint32), np.zeros(0, np.uint8))
+    base = mplan.file_base()
+    base_d = torch.from_numpy(base.view(np.uint8).copy()).cuda()
+    masters = torch.empty(mplan.n_master_sectors * SECTOR, dtype=torch.uint8, device="cuda")
+    mplan.masters_device(masters.data_ptr(), base_d.data_ptr())
+    torch.cuda.synchronize()
+    files = [(masters.data_ptr() + int(base[f]) * SECTOR, int(file_nsect[f]) * SECTOR) for f in range(file_nsect.size)]
+    t0 = time.perf_counter()
+    m = cv.master_build(files)
+    build_s = time.perf_counter() - t0
+    del masters
+    torch.cuda.synchronize()
+    return m, file_nsect, mseed, build_s
+
+
+def expected_window(expect: np.ndarray, a: int, n: int) -> np.ndarray:
+    """The triples of disk sectors [a, a + n) renumbered from 0."""
+    lo = np.searchsorted(expect["disk_sector"], a, side="left")
+    hi = np.searchsorted(expect["disk_sector"], a + n, side="left")
+    out = expect[lo:hi].copy()
+    out["disk_sector"] -= a
+    return out
+
+
+def run_batched(torch, cv, synth, args, stream):
+    """512 device images of uneven sizes (one device arena) against one 8M-sector table: one CUDA
+    graph launch per run, autotuned, against 512 sequential cv_scan calls on the same images."""
+    m, file_nsect, mseed, build_s = build_master_set(torch, cv, synth, "m8m")
+    sizes = synth.batch_sizes(4, args.batch_images, 1 << 20, 2 << 30, args.batch_total_gib << 30)
+    total = int(sizes.sum())
+    arena = torch.empty(total * SECTOR, dtype=torch.uint8, device="cuda")
+    images, expects, off = [], [], 0
+    for i, n in enumerate(sizes.tolist()):
+        plan = synth.make_plan_density(1000 + i, n, file_nsect, args.batch_density, mseed)
+        ptrs, keep = device_plan(torch, synth, plan)
+        plan.image_device(arena.data_ptr() + off * SECTOR, dev_plan=ptrs)
+        if i % 64 == 0:
+            torch.cuda.synchronize()
+        expects.append(plan.expected_intact())
+        images.append((arena.data_ptr() + off * SECTOR, n * SECTOR))
+        off += n
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = cv.batch_create(m, images, autotune=True, stream=stream)
+    tune_s = time.perf_counter() - t0
+    info = b.info()
+    for _ in range(3):
+        b.run(stream)
+        b.wait()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.batch_runs):
+        b.run(stream)
+    e1.record(stream)
+    n_match = b.wait()
+    graph_ms = e0.elapsed_time(e1) / args.batch_runs
+    exact = n_match == sum(e.size for e in expects)
+    for i in range(0, len(images), max(1, len(images) // 16)):
+        exact = exact and np.array_equal(cv.device_matches_to_numpy(b.matches(i)), expects[i])
+    # the same images as 512 sequential plain scans
+    seq = []
+    for rep in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for im in images:
+            cv.scan(m, [im], keep_on_device=True, stream=stream).close()
+        torch.cuda.synchronize()
+        seq.append(time.perf_counter() - t0)
+    seq_s = min(seq)
+    b.close()
+    m.close()
+    del arena
+    torch.cuda.synchronize()
+    return {"workload": f"{len(images)} images, {total * SECTOR / 2**30:.0f} GiB, log-uniform 1 MiB-2 GiB scaled, "
+                        f"{args.batch_density:.0%} of clusters planted from a {int(file_nsect.sum())}-sector table",
+            "graph_GBps": total * SECTOR / (graph_ms * 1e-3) / 1e9, "graph_ms_per_run": graph_ms,
+            "sequential_GBps": total * SECTOR / seq_s / 1e9, "sequential_ms": seq_s * 1e3,
+            "speedup_vs_sequential": (seq_s * 1e3) / graph_ms, "kernel_config": info["config_name"],
+            "bloom": info["bloom"], "tuned": info["tuned"], "tune_s": tune_s, "kernel_nodes": info["kernel_launches"],
+            "tensor_maps": info["tensor_maps"], "matches": n_match, "bit_exact_vs_plant_log": bool(exact),
+            "table_build_s": build_s}
+
+
+def run_served(torch, cv, synth, args, host):
+    """Poisson arrivals of host-resident requests (80% 64 KiB-4 MiB stream chunks, 20%
+    256 MiB-16 GiB drive images, windows of one pinned pool) against one 8M-sector table."""
+    import threading
+
+    m, file_nsect, mseed, build_s = build_master_set(torch, cv, synth, "m8m")
+    pool_sectors = host.numel() // SECTOR
+    plan = synth.make_plan_density(5, pool_sectors, file_nsect, args.serve_density, mseed)
+    ptrs, keep = device_plan(torch, synth, plan)
+    pool = torch.empty(pool_sectors * SECTOR, dtype=torch.uint8, device="cuda")
+    plan.image_device(pool.data_ptr(), dev_plan=ptrs)
+    host.copy_(pool)
+    del pool, keep
+    torch.cuda.synchronize()
+    expect = plan.expected_intact()
+    rng = np.random.default_rng(5)
+    n = args.serve_requests
+    gaps = rng.exponential(1.0 / args.serve_rate, size=n)
+    drive = rng.random(n) < 0.2
+    size_b = np.where(drive, np.exp(rng.uniform(np.log(256 << 20), np.log(16 << 30), n)),
+                      np.exp(rng.uniform(np.log(64 << 10), np.log(4 << 20), n)))
+    size_s = np.maximum((size_b // 4096).astype(np.int64), 1) * 8
+    size_s = np.minimum(size_s, pool_sectors // 8 * 8)
+    start = (rng.integers(0, (pool_sectors - size_s) // 8 + 1) * 8).astype(np.int64)
+    srv = cv.server_create(m, hbm_budget_bytes=args.serve_budget_gb * 10**9, work_unit_bytes=64 << 20, max_live=64,
+                           copy_streams=4)
+    base = host.data_ptr()
+    tickets = [None] * n
+    arrivals = np.cumsum(gaps)
+
+    def submitter():
+        t0 = time.perf_counter()
+        for k in range(n):
+            wait = arrivals[k] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            tickets[k] = srv.submit((base + int(start[k]) * SECTOR, int(size_s[k]) * SECTOR), tag=k)
+
+    th = threading.Thread(target=submitter)
+    t0 = time.perf_counter()
+    th.start()
+    exact = True
+    for k in range(n):
+        while tickets[k] is None:
+            time.sleep(0.0005)
+        r = srv.poll(tickets[k], timeout_ms=-1)
+        got = r.matches(0)
+        r.close()
+        if not np.array_equal(got, expected_window(expect, int(start[k]), int(size_s[k]))):
+            exact = False
+    th.join()
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    m.close()
+    total_b = int(size_s.sum()) * SECTOR
+    return {"workload": f"{n} requests, Poisson {args.serve_rate:g}/s, 80% 64 KiB-4 MiB / 20% 256 MiB-16 GiB, "
+                        f"windows of a {pool_sectors * SECTOR / 2**30:.0f} GiB pinned pool, "
+                        f"{int(file_nsect.sum())}-sector table, HBM budget {args.serve_budget_gb} GB",
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
+            "throughput_GBps": total_b / st["wall_s"] / 1e9 if st["wall_s"] else None, "wall_s": wall,
+            "bytes": total_b, "iterations": st["iterations"], "units": st["units"],
+            "mean_live_per_iteration": st["mean_live_per_iteration"],
+            "peak_bytes_in_flight": st["peak_bytes_in_flight"], "completed": st["completed"], "failed": st["failed"],
+            "bit_exact_vs_plant_log": bool(exact)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="scale")
     ap.add_argument("--kernel-config", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample-sectors", type=int, default=1 << 21)
+    ap.add_argument("--cpu-sample-pieces", type=int, default=24, help="1 GiB pieces timed on the oracle")
     ap.add_argument("--ref-sample-sectors", type=int, default=1 << 19)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-images", type=int, default=512)
+    ap.add_argument("--batch-total-gib", type=int, default=64)
+    ap.add_argument("--batch-density", type=float, default=0.01)
+    ap.add_argument("--batch-runs", type=int, default=10)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-density", type=float, default=0.02)
+    ap.add_argument("--serve-budget-gb", type=int, default=120)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -228,7 +406,7 @@ def main():
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    kernel_ms, matches = [], 0
+    kernel_ms, matches, launches = [], 0, 0
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -239,6 +417,7 @@ def main():
             st = r.stats()
             kernel_ms.append(st["kernel_ms"])
             matches = st["matches"]
+            launches += st["kernel_launches"]
             r.close()
         e1.record(stream)
         torch.cuda.synchronize()
@@ -253,11 +432,13 @@ def main():
 
     # end to end through the C ABI from pinned host memory
     e2e = None
-    if not args.no_e2e:
+    host = None
+    if not args.no_e2e or not args.no_serve:
         host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
         host.copy_(image)
-        del image
-        torch.cuda.synchronize()
+    del image
+    torch.cuda.synchronize()
+    if not args.no_e2e:
         step(host, keep_on_device=False).close()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -270,7 +451,6 @@ def main():
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
         e2e = {"value": world * nbytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
-        del host
 
     kms = statistics.mean(kernel_ms)
     sectors = plan.n_sectors
@@ -302,13 +482,19 @@ def main():
                      "hbm_peak_GBps_measured": hbm},
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": launches,
     }
+    master.close()
+    if not args.no_batch:
+        line["batched"] = run_batched(torch, cv, synth, args, stream)
+    if not args.no_serve:
+        line["served"] = run_served(torch, cv, synth, args, host)
+        line["p99_served_ms"] = line["served"]["p99_ms"]
+    del host
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(plan, args.cpu_sample_sectors)
+        line["cpu_baseline"] = cpu_baseline(plan, args.cpu_sample_pieces)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    master.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()

@@ -50,6 +50,7 @@ extern "C" {
 #define CV_ETIMEOUT -6   /* a device-side wait ran out of time; the results were discarded */
 #define CV_ENODEV -7     /* no usable CUDA device (the library has no CPU path) */
 #define CV_ERANGE -8     /* image_index out of range, or an output buffer too small */
+#define CV_EAGAIN -9     /* not ready yet (cv_poll) */
 
 /* One match: disk sector i of image k equals sector file_sector of master file file_id. */
 typedef struct {
@@ -138,14 +139,17 @@ int cv_matches(const cv_result* r, uint32_t image_index, const cv_match** out, u
 typedef struct {
   uint64_t sectors;        /* whole sectors scanned */
   uint64_t matches;        /* triples over all images */
-  uint64_t hit_sectors;    /* disk sectors with at least one match */
+  uint64_t hit_sectors;    /* reserved (0) */
   float kernel_ms;         /* device time of the hashing/probe launches */
   float total_ms;          /* device time from the first copy to the last result copy */
+  uint32_t kernel_launches; /* kernels the call launched (scan, offsets, expand) */
+  uint32_t reserved;
 } cv_scan_stats;
 
 int cv_scan_get_stats(const cv_result* r, cv_scan_stats* st);
 
-/* Free a cv_master or cv_result handle (NULL is ignored). */
+/* Free a cv_master, cv_result, cv_batch or cv_server handle (NULL is ignored). A server first
+ * finishes its admitted requests and stops its engine thread. */
 void cv_free(void* handle);
 
 /* Text for a return code. */
@@ -162,6 +166,102 @@ int cv_last_cuda_error(void);
  * stream and returns without waiting. Errors: CV_EINVAL, CV_ECUDA, CV_ENODEV.
  */
 int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t* trivial, void* stream);
+
+/*
+ * Batched scans (a CUDA graph over many device images). The paper scans several drives at once
+ * by multiplexing them onto one GPU (Section 3); a batch makes all of its images one work list
+ * for one persistent scan launch (images in one device allocation share a tensor map), then
+ * one offset pass and one expand pass, captured once as a CUDA graph and replayed per run.
+ *
+ * Images must be device buffers (16-byte aligned), borrowed for the life of the batch: each run
+ * reads their current contents. Matches of the last run stay in device memory owned by the
+ * batch. With autotune set, cv_batch_create times every kernel configuration, with and without
+ * the Bloom prefilter, on the batch itself and keeps the fastest; the choice is cached per
+ * process and, when tune_cache names a file, in that file (one line per workload key).
+ */
+typedef struct cv_batch cv_batch;
+
+#define CV_BATCH_BLOOM_AUTO 0u /* use the table's Bloom filter when it has one */
+#define CV_BATCH_BLOOM_OFF 1u  /* probe the table directly */
+
+typedef struct {
+  uint32_t struct_size;     /* sizeof(cv_batch_opts) */
+  uint32_t autotune;        /* 1: tune the kernel configuration and Bloom use on this batch */
+  void* stream;             /* cudaStream_t for set-up and tuning */
+  uint64_t match_capacity;  /* output room in matches; 0 = size it from one scan at set-up */
+  uint32_t kernel_config;   /* 0 = default (or tuned); k + 1 = configuration k */
+  uint32_t bloom;           /* CV_BATCH_BLOOM_AUTO / CV_BATCH_BLOOM_OFF (ignored when tuning) */
+  const char* tune_cache;   /* file for tuned choices, or NULL */
+} cv_batch_opts;
+
+typedef struct {
+  int kernel_config;          /* index of the configuration in use */
+  const char* config_name;
+  uint32_t bloom;             /* 1 when the Bloom prefilter is used */
+  uint32_t tuned;             /* 1 when this batch ran the tuner (0: default or cached) */
+  uint32_t kernel_launches;   /* kernel nodes per run */
+  uint32_t tensor_maps;
+  uint32_t segments;
+  uint32_t reserved;
+  uint64_t sectors;
+  uint64_t match_capacity;
+  float scan_ms;              /* device time of the scan launch(es) of the last finished run */
+} cv_batch_info;
+
+/* Errors: CV_EINVAL (host or misaligned image, bad options), CV_ENOMEM, CV_ECUDA, CV_ENODEV. */
+int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images, const cv_batch_opts* opts,
+                    cv_batch** out);
+/* One graph launch on stream; returns without waiting. */
+int cv_batch_run(cv_batch* b, void* stream);
+/* Wait for the last run. *n_matches = matches over all images. CV_ERANGE when they exceed the
+ * batch's capacity (create the batch again with a larger match_capacity). */
+int cv_batch_wait(cv_batch* b, uint64_t* n_matches);
+/* Device pointer and count of image image_index's sorted matches from the last run. */
+int cv_batch_matches(const cv_batch* b, uint32_t image_index, const cv_match** out, uint64_t* n_out);
+int cv_batch_get_info(const cv_batch* b, cv_batch_info* info);
+
+/*
+ * Serving: a request loop that scans images as they arrive (drives at a checkpoint, chunks of
+ * a network stream) against one resident master table. Requests are cut into work units; the
+ * units are copied host-to-device on side streams into a device arena whose size is the HBM
+ * budget, and every engine iteration scans the units of all live requests that have arrived
+ * on the device in one launch (continuous batching). Each request's matches are identical to
+ * a solo cv_scan of the same image. One engine thread per server.
+ */
+typedef struct cv_server cv_server;
+
+typedef struct {
+  uint32_t struct_size;      /* sizeof(cv_server_opts) */
+  uint32_t max_live;         /* requests admitted at once; 0 = 64 */
+  uint64_t hbm_budget_bytes; /* device arena for request data in flight; 0 = 8 GiB */
+  uint64_t work_unit_bytes;  /* request data per work unit (multiple of 512); 0 = 64 MiB */
+  uint32_t kernel_config;    /* 0 = default; k + 1 = configuration k */
+  uint32_t copy_streams;     /* host-to-device copy streams; 0 = 2 */
+} cv_server_opts;
+
+typedef struct {
+  uint64_t submitted;
+  uint64_t completed;
+  uint64_t failed;
+  uint64_t bytes_scanned;
+  uint64_t iterations;          /* engine iterations (scan launches over ready units) */
+  uint64_t units;               /* work units scanned */
+  uint64_t peak_bytes_in_flight;
+  double mean_live_per_iteration; /* requests with units in an iteration, averaged */
+  double p50_ms, p99_ms, mean_ms, max_ms; /* submit-to-result latency of completed requests */
+  double wall_s;                /* first submit to last completion */
+} cv_server_stats;
+
+/* Errors: CV_EINVAL, CV_ENOMEM, CV_ECUDA, CV_ENODEV. The master must outlive the server. */
+int cv_server_create(const cv_master* m, const cv_server_opts* opts, cv_server** out);
+/* Queue one image (host memory, or device memory of the server's device), borrowed until its
+ * result is polled. Never blocks on the GPU. *ticket identifies the request. */
+int cv_submit(cv_server* s, cv_buf image, uint64_t tag, uint64_t* ticket);
+/* Wait up to timeout_ms (0: do not wait, < 0: forever) for a request. On success *out is its
+ * result (one image, host matches; free with cv_free) and the ticket is retired. CV_EAGAIN:
+ * not done yet. Other codes: the request failed. */
+int cv_poll(cv_server* s, uint64_t ticket, int timeout_ms, cv_result** out);
+int cv_server_get_stats(cv_server* s, cv_server_stats* st);
 
 /*
  * Scan one device-resident image without allocating any memory. The paper has no counterpart:

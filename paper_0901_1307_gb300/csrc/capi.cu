@@ -22,257 +22,17 @@
 #include "cv.h"
 #include "cv_internal.h"
 #include "cv_launch.h"
+#include "runtime.h"
 #include "table_build.cuh"
 
 using namespace cvk;
 
+void cvk_batch_free(void* h);
+void cvk_server_free(void* h);
+
 namespace {
-
-thread_local int g_last_cuda = 0;
-
-int cuda_fail(cudaError_t e) {
-  g_last_cuda = (int)e;
-  cudaGetLastError();
-  return e == cudaErrorMemoryAllocation ? CV_ENOMEM : CV_ECUDA;
-}
-
-#define CV_CUDA(expr)                           \
-  do {                                          \
-    cudaError_t e_ = (expr);                    \
-    if (e_ != cudaSuccess) return cuda_fail(e_); \
-  } while (0)
-
-#define CV_TRY(expr)           \
-  do {                         \
-    int r_ = (expr);           \
-    if (r_ != CV_OK) return r_; \
-  } while (0)
-
 constexpr uint32_t kMagicMaster = 0xC7A57E01u;
 constexpr uint32_t kMagicResult = 0xC7A57E02u;
-
-// ------------------------------------------------------------------ per-device state
-struct DevCtx {
-  bool ready = false;
-  int dev = -1;
-  int sms = 0;
-  cudaMemPool_t pool = nullptr;
-  cudaStream_t copy_stream = nullptr;
-  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  std::vector<int> blocks_per_sm;  // per scan configuration (scan mode)
-  std::vector<int> blocks_per_sm_digest;
-  int cfg_index = 0;               // default scan configuration
-};
-
-constexpr int kMaxDevices = 64;
-std::mutex g_ctx_mutex;
-DevCtx g_ctx[kMaxDevices];
-
-int find_cfg(const char* name) {
-  int n;
-  const ScanCfg* c = scan_configs(&n);
-  for (int i = 0; i < n; i++)
-    if (strcmp(c[i].name, name) == 0) return i;
-  return -1;
-}
-
-int get_ctx(DevCtx** out) {
-  int dev;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) {
-    g_last_cuda = (int)e;
-    cudaGetLastError();
-    return CV_ENODEV;
-  }
-  if (dev < 0 || dev >= kMaxDevices) return CV_ENODEV;
-  std::lock_guard<std::mutex> lk(g_ctx_mutex);
-  DevCtx& c = g_ctx[dev];
-  if (!c.ready) {
-    cudaDeviceProp prop;
-    CV_CUDA(cudaGetDeviceProperties(&prop, dev));
-    if (prop.major < 10) return CV_ENODEV;
-    c.dev = dev;
-    c.sms = prop.multiProcessorCount;
-    cudaMemPoolProps pp;
-    memset(&pp, 0, sizeof pp);
-    pp.allocType = cudaMemAllocationTypePinned;
-    pp.handleTypes = cudaMemHandleTypeNone;
-    pp.location.type = cudaMemLocationTypeDevice;
-    pp.location.id = dev;
-    CV_CUDA(cudaMemPoolCreate(&c.pool, &pp));
-    uint64_t thr = UINT64_MAX;
-    CV_CUDA(cudaMemPoolSetAttribute(c.pool, cudaMemPoolAttrReleaseThreshold, &thr));
-    CV_CUDA(cudaStreamCreateWithFlags(&c.copy_stream, cudaStreamNonBlocking));
-    cudaDriverEntryPointQueryResult q;
-    void* fn = nullptr;
-    CV_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !fn) return CV_ENODEV;
-    c.encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    int n;
-    const ScanCfg* cfgs = scan_configs(&n);
-    c.blocks_per_sm.assign(n, 0);
-    c.blocks_per_sm_digest.assign(n, 0);
-    for (int i = 0; i < n; i++) {
-      CV_CUDA(cudaFuncSetAttribute(cfgs[i].scan_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfgs[i].smem));
-      CV_CUDA(cudaFuncSetAttribute(cfgs[i].digest_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfgs[i].smem));
-      CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.blocks_per_sm[i], cfgs[i].scan_fn, cfgs[i].T + 32,
-                                                            cfgs[i].smem));
-      CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.blocks_per_sm_digest[i], cfgs[i].digest_fn,
-                                                            cfgs[i].T + 32, cfgs[i].smem));
-      if (c.blocks_per_sm[i] < 1 || c.blocks_per_sm_digest[i] < 1) return CV_ECUDA;
-    }
-    c.cfg_index = 0;
-    const char* env = getenv("CV_SCAN_CONFIG");
-    if (env && *env) {
-      int k = find_cfg(env);
-      if (k < 0) return CV_EINVAL;
-      c.cfg_index = k;
-    }
-    c.ready = true;
-  }
-  *out = &c;
-  return CV_OK;
-}
-
-// Stream-ordered temporaries, returned to the pool when the scope ends.
-struct Temps {
-  DevCtx* ctx;
-  cudaStream_t stream;
-  std::vector<void*> ptrs;
-  Temps(DevCtx* c, cudaStream_t s) : ctx(c), stream(s) {}
-  ~Temps() {
-    for (void* p : ptrs) cudaFreeAsync(p, stream);
-  }
-  template <typename P>
-  int alloc(P** out, size_t bytes) {
-    void* p = nullptr;
-    cudaError_t e = cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, ctx->pool, stream);
-    if (e != cudaSuccess) return cuda_fail(e);
-    ptrs.push_back(p);
-    *out = (P*)p;
-    return CV_OK;
-  }
-};
-
-enum BufKind { kHost = 0, kDevice = 1 };
-
-int classify(DevCtx* ctx, const void* p, BufKind* kind) {
-  cudaPointerAttributes a;
-  cudaError_t e = cudaPointerGetAttributes(&a, p);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    *kind = kHost;
-    return CV_OK;
-  }
-  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
-    if (a.device != ctx->dev) return CV_EINVAL;
-    *kind = kDevice;
-  } else {
-    *kind = kHost;
-  }
-  return CV_OK;
-}
-
-int make_tmap(DevCtx* ctx, const ScanCfg& cfg, const void* base, uint64_t n_sectors, CUtensorMap* out) {
-  cuuint64_t dims[2] = {128, (cuuint64_t)n_sectors};
-  cuuint64_t strides[1] = {512};
-  cuuint32_t box[2] = {(cuuint32_t)(cfg.BOXB / 4), (cuuint32_t)cfg.T};
-  cuuint32_t es[2] = {1, 1};
-  CUtensorMapSwizzle sw = cfg.BOXB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-  CUresult r = ctx->encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(base), dims, strides, box, es,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    g_last_cuda = (int)r;
-    return CV_ECUDA;
-  }
-  return CV_OK;
-}
-
-// A list of segments, each a contiguous device range of whole sectors with its tensor map.
-struct Job {
-  std::vector<Segment> segs;
-  std::vector<CUtensorMap> maps;
-  std::vector<const void*> bases;
-  uint64_t n_tiles = 0;
-  uint64_t n_sectors = 0;
-
-  // Append one device range (split at kMaxSegmentSectors). `base` may be null for ranges whose
-  // tensor map is made later (streamed chunks).
-  int add(DevCtx* ctx, const ScanCfg& cfg, const void* base, uint64_t n_sectors_in, uint64_t sector_base,
-          uint32_t image) {
-    uint64_t done = 0;
-    while (done < n_sectors_in) {
-      uint64_t n = std::min<uint64_t>(n_sectors_in - done, kMaxSegmentSectors);
-      Segment s;
-      s.n_sectors = n;
-      s.tile_base = n_tiles;
-      s.sector_base = sector_base + done;
-      s.image = image;
-      s.pad = 0;
-      CUtensorMap m;
-      memset(&m, 0, sizeof m);
-      const void* b = base ? (const uint8_t*)base + done * kSector : nullptr;
-      if (b) CV_TRY(make_tmap(ctx, cfg, b, n, &m));
-      segs.push_back(s);
-      maps.push_back(m);
-      bases.push_back(b);
-      n_tiles += (n + cfg.T - 1) / cfg.T;
-      n_sectors += n;
-      done += n;
-    }
-    return CV_OK;
-  }
-};
-
-// Launch the scan (or digest) kernel over segments [s0, s1) of the job, at most kSegsPerLaunch
-// segments per launch. `base` carries the table and the output pointers.
-int launch_range(DevCtx* ctx, int cfg_i, bool digest, const Job& job, size_t s0, size_t s1, const ScanParams& base,
-                 cudaStream_t stream) {
-  int n;
-  const ScanCfg& cfg = scan_configs(&n)[cfg_i];
-  const int bps = digest ? ctx->blocks_per_sm_digest[cfg_i] : ctx->blocks_per_sm[cfg_i];
-  for (size_t a = s0; a < s1; a += kSegsPerLaunch) {
-    const size_t b = std::min(s1, a + (size_t)kSegsPerLaunch);
-    ScanParams p;
-    memset(&p, 0, sizeof p);
-    p.tab = base.tab;
-    p.hit_rec = base.hit_rec;
-    p.tile_nhit = base.tile_nhit;
-    p.tile_ntrip = base.tile_ntrip;
-    p.status = base.status;
-    p.digests = base.digests;
-    p.trivial = base.trivial;
-    for (size_t k = a; k < b; k++) {
-      p.maps[k - a] = job.maps[k];
-      p.segs[k - a] = job.segs[k];
-    }
-    p.n_segs = (uint32_t)(b - a);
-    p.tile_begin = job.segs[a].tile_base;
-    const uint64_t tile_end = (b < job.segs.size()) ? job.segs[b].tile_base : job.n_tiles;
-    p.n_tiles = tile_end - p.tile_begin;
-    if (p.n_tiles == 0) continue;
-    const uint64_t grid = std::min<uint64_t>(p.n_tiles, (uint64_t)ctx->sms * bps);
-    void* args[] = {&p};
-    CV_CUDA(cudaLaunchKernel(digest ? cfg.digest_fn : cfg.scan_fn, dim3((unsigned)grid), dim3(cfg.T + 32), args,
-                             cfg.smem, stream));
-  }
-  return CV_OK;
-}
-
-uint64_t next_pow2(uint64_t x) {
-  uint64_t p = 1;
-  while (p < x) p <<= 1;
-  return p;
-}
-
-unsigned grid_for(uint64_t n, int threads, int sms) {
-  uint64_t g = (n + threads - 1) / threads;
-  uint64_t cap = (uint64_t)sms * 16;
-  if (g > cap) g = cap;
-  return (unsigned)(g ? g : 1);
-}
-
 }  // namespace
 
 // ======================================================================== handles
@@ -296,6 +56,7 @@ struct cv_result {
   MatchOut* dev_out;     // from the library's pool, released on free_stream
   cudaStream_t free_stream;
   cv_scan_stats st;
+  int launches;          // kernel launches of the scan
 };
 
 // ======================================================================= C ABI
@@ -312,11 +73,12 @@ const char* cv_strerror(int code) {
     case CV_ETIMEOUT: return "device wait timed out";
     case CV_ENODEV: return "no usable CUDA device";
     case CV_ERANGE: return "index or size out of range";
+    case CV_EAGAIN: return "not ready yet";
     default: return "unknown error";
   }
 }
 
-int cv_last_cuda_error(void) { return g_last_cuda; }
+int cv_last_cuda_error(void) { return last_cuda(); }
 
 int cv_kernel_config_count(void) {
   int n;
@@ -332,14 +94,16 @@ const char* cv_kernel_config_name(int k) {
 
 static int digest_job(DevCtx* ctx, Job& job, uint4* digests, uint8_t* trivial, uint32_t* status, cudaStream_t stream,
                       Temps& tmp) {
-  (void)tmp;
   const int cfg_i = ctx->cfg_index;
+  Segment* segs_d;
+  CV_TRY(tmp.alloc(&segs_d, job.segs.size() * sizeof(Segment)));
+  CV_CUDA(cudaMemcpyAsync(segs_d, job.segs.data(), job.segs.size() * sizeof(Segment), cudaMemcpyHostToDevice, stream));
   ScanParams p;
   memset(&p, 0, sizeof p);
   p.status = status;
   p.digests = digests;
   p.trivial = trivial;
-  CV_TRY(launch_range(ctx, cfg_i, true, job, 0, job.segs.size(), p, stream));
+  CV_TRY(launch_range(ctx, cfg_i, true, job, segs_d, 0, job.segs.size(), p, stream));
   return CV_OK;
 }
 
@@ -354,7 +118,7 @@ int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t
   const ScanCfg& cfg = scan_configs(&n)[ctx->cfg_index];
   Temps tmp(ctx, stream);
   Job job;
-  CV_TRY(job.add(ctx, cfg, in, n_sectors, 0, 0));
+  CV_TRY(job.add(ctx, cfg, in, n_sectors, 0, 0, false));
   uint32_t* status;
   CV_TRY(tmp.alloc(&status, 4));
   CV_CUDA(cudaMemsetAsync(status, 0, 4, stream));
@@ -434,7 +198,7 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       }
       if (M) {
         Job job;
-        CV_TRY(job.add(ctx, cfg, arena, M, 0, 0));
+        CV_TRY(job.add(ctx, cfg, arena, M, 0, 0, false));
         CV_TRY(digest_job(ctx, job, dig, trivial, counters + 3, stream, tmp));
         const unsigned g = grid_for(M, 256, ctx->sms);
         insert_kernel<<<g, 256, 0, stream>>>(dig, trivial, M, owner, cnt, slot_of, mask, counters, counters + 1,
@@ -507,12 +271,43 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
 }  // extern "C"
 
 // Device view of a master table for other translation units of the library.
-int cvk_master_view(const cv_master* m, TableView* tab, int* dev) {
+namespace cvk {
+// A one-image result holding a copy of n host triples (used by the serving loop).
+cv_result* make_host_result(int dev, const MatchOut* data, uint64_t n, uint64_t sectors, float total_ms) {
+  cv_result* r = new (std::nothrow) cv_result();
+  if (!r) return nullptr;
+  r->magic = kMagicResult;
+  r->dev = dev;
+  r->on_device = false;
+  r->n_images = 1;
+  r->off.assign(2, 0);
+  r->off[1] = n;
+  r->host = nullptr;
+  r->dev_out = nullptr;
+  r->free_stream = nullptr;
+  memset(&r->st, 0, sizeof r->st);
+  r->st.sectors = sectors;
+  r->st.matches = n;
+  r->st.total_ms = total_ms;
+  r->launches = 0;
+  if (n) {
+    r->host = (MatchOut*)malloc(n * sizeof(MatchOut));
+    if (!r->host) {
+      delete r;
+      return nullptr;
+    }
+    memcpy(r->host, data, n * sizeof(MatchOut));
+  }
+  return r;
+}
+
+int master_view(const cv_master* m, TableView* tab, int* dev) {
   if (!m || m->magic != kMagicMaster) return CV_EINVAL;
   *tab = m->tab;
   *dev = m->dev;
   return CV_OK;
 }
+}  // namespace cvk
 
 extern "C" {
 
@@ -561,13 +356,13 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
     CV_TRY(classify(ctx, images[i].data, &kind[i]));
     if (kind[i] == kDevice) {
       if ((uintptr_t)images[i].data & 15u) return CV_EINVAL;
-      CV_TRY(job.add(ctx, cfg, images[i].data, ns, 0, i));
+      CV_TRY(job.add(ctx, cfg, images[i].data, ns, 0, i, true));
     } else {
       const uint64_t per = chunk / kSector;
       for (uint64_t s0 = 0; s0 < ns; s0 += per) {
         const uint64_t n = std::min(per, ns - s0);
         hchunks.push_back(HostChunk{job.segs.size(), (const uint8_t*)images[i].data + s0 * kSector, n * kSector});
-        CV_TRY(job.add(ctx, cfg, nullptr, n, s0, i));
+        CV_TRY(job.add(ctx, cfg, nullptr, n, s0, i, false));
       }
     }
   }
@@ -584,6 +379,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
   r->dev_out = nullptr;
   r->free_stream = stream;
   memset(&r->st, 0, sizeof r->st);
+  r->launches = 0;
   r->st.sectors = job.n_sectors;
 
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -614,7 +410,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
           }
           for (size_t k = 0; k < hchunks.size(); k++) {
             const size_t s = hchunks[k].seg;
-            CV_TRY(make_tmap(ctx, cfg, ring[k & 1], job.segs[s].n_sectors, &job.maps[s]));
+            CV_TRY(job.set_map(ctx, cfg, s, ring[k & 1]));
           }
         }
         Segment* segs_d;
@@ -622,10 +418,12 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         uint32_t *tile_nhit, *status;
         uint64_t *tile_ntrip, *tile_off, *seg_off_d;
         CV_TRY(tmp.alloc(&segs_d, nseg * sizeof(Segment)));
-        CV_TRY(tmp.alloc(&hit_rec, nt * cfg.T * sizeof(uint4)));
-        CV_TRY(tmp.alloc(&tile_nhit, nt * 4));
-        CV_TRY(tmp.alloc(&tile_ntrip, nt * 8));
-        CV_TRY(tmp.alloc(&tile_off, nt * 8));
+        // compaction works on output tiles of 32 sectors, T / 32 per scan tile
+        const uint64_t n_out = nt * (uint64_t)(cfg.T / 32);
+        CV_TRY(tmp.alloc(&hit_rec, n_out * 32 * sizeof(uint4)));
+        CV_TRY(tmp.alloc(&tile_nhit, n_out * 4));
+        CV_TRY(tmp.alloc(&tile_ntrip, n_out * 8));
+        CV_TRY(tmp.alloc(&tile_off, n_out * 8));
         CV_TRY(tmp.alloc(&seg_off_d, (nseg + 2) * 8));  // seg_off[nseg], total, status
         status = (uint32_t*)(seg_off_d + nseg + 1);
         status_keep = status;
@@ -651,25 +449,25 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
                                     ctx->copy_stream));
             CV_CUDA(cudaEventRecord(ring_copied[b], ctx->copy_stream));
             CV_CUDA(cudaStreamWaitEvent(stream, ring_copied[b], 0));
-            CV_TRY(launch_range(ctx, cfg_i, false, job, s, s + 1, p, stream));
+            CV_TRY(launch_range(ctx, cfg_i, false, job, segs_d, s, s + 1, p, stream, &r->launches));
             CV_CUDA(cudaEventRecord(ring_free[b], stream));
             hk++;
             s++;
           } else {
             size_t e = s;
             while (e < nseg && !(hk < hchunks.size() && hchunks[hk].seg == e)) e++;
-            CV_TRY(launch_range(ctx, cfg_i, false, job, s, e, p, stream));
+            CV_TRY(launch_range(ctx, cfg_i, false, job, segs_d, s, e, p, stream, &r->launches));
             s = e;
           }
         }
         CV_CUDA(cudaEventRecord(ev[2], stream));
         uint64_t* total_d = seg_off_d + nseg;
         uint32_t nseg32 = (uint32_t)nseg;
-        uint64_t nt_arg = nt;
+        uint64_t nt_arg = n_out;
         uint64_t* off_scratch;
-        CV_TRY(tmp.alloc(&off_scratch, tile_offsets_scratch_words(nt) * 8));
-        CV_CUDA((cudaError_t)launch_tile_offsets(tile_ntrip, nt, tile_off, segs_d, nseg32, seg_off_d, total_d,
-                                                 off_scratch, stream));
+        CV_TRY(tmp.alloc(&off_scratch, tile_offsets_scratch_words(n_out) * 8));
+        CV_CUDA((cudaError_t)launch_tile_offsets(tile_ntrip, n_out, tile_off, segs_d, nseg32, (uint32_t)(cfg.T / 32),
+                                                 seg_off_d, total_d, off_scratch, stream));
         CV_CUDA(cudaMemcpyAsync(seg_off.data(), seg_off_d, (nseg + 2) * 8, cudaMemcpyDeviceToHost, stream));
         CV_CUDA(cudaStreamSynchronize(stream));
         const uint32_t st = (uint32_t)seg_off[nseg + 1];
@@ -678,13 +476,15 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         total = seg_off[nseg];
         if (total) {
           CV_CUDA(cudaMallocFromPoolAsync((void**)&r->dev_out, total * sizeof(MatchOut), ctx->pool, stream));
-          const unsigned eg = grid_for(nt * 32, 256, ctx->sms);
+          const unsigned eg = grid_for(n_out * 32, 256, ctx->sms);
           uint64_t cap = total;
           const uint2* postings = m->tab.postings;
           MatchOut* outp = r->dev_out;
           void* eargs[] = {&hit_rec, &tile_nhit, &tile_off, &nt_arg, &segs_d, &nseg32, &postings, &outp, &cap, &status};
           CV_CUDA(cudaLaunchKernel(cfg.expand_fn, dim3(eg), dim3(256), eargs, 0, stream));
+          r->launches += 1;
         }
+        r->launches += 4;  // the offset pass
       }
       // per-image ranges; an image without sectors gets an empty range
       r->off[n_images] = total;
@@ -708,6 +508,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
       }
       CV_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[3]));
       r->st.total_ms = ms;
+      r->st.kernel_launches = (uint32_t)r->launches;
       if (total && !r->on_device) {
         CV_CUDA(cudaFreeAsync(r->dev_out, stream));
         r->dev_out = nullptr;
@@ -751,6 +552,14 @@ int cv_scan_get_stats(const cv_result* r, cv_scan_stats* st) {
 void cv_free(void* handle) {
   if (!handle) return;
   const uint32_t magic = *(const uint32_t*)handle;
+  if (magic == 0xC7A57E03u) {
+    cvk_batch_free(handle);
+    return;
+  }
+  if (magic == 0xC7A57E04u) {
+    cvk_server_free(handle);
+    return;
+  }
   if (magic == kMagicMaster) {
     cv_master* m = (cv_master*)handle;
     m->magic = 0;

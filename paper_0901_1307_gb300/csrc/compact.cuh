@@ -93,47 +93,47 @@ __global__ void __launch_bounds__(kOffThreads) chunk_scan_kernel(const uint64_t*
   }
 }
 
+// seg_off[s] = offset of the first output tile of segment s (output tiles per scan tile: scale).
 __global__ void segment_offsets_kernel(const uint64_t* tile_off, uint64_t n, const Segment* segs, uint32_t n_segs,
-                                       const uint64_t* total, uint64_t* seg_off) {
-  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_segs; s += gridDim.x * blockDim.x)
-    seg_off[s] = segs[s].tile_base < n ? tile_off[segs[s].tile_base] : *total;
+                                       uint32_t scale, const uint64_t* total, uint64_t* seg_off) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_segs; s += gridDim.x * blockDim.x) {
+    const uint64_t u = segs[s].tile_base * scale;
+    seg_off[s] = u < n ? tile_off[u] : *total;
+  }
 }
 
-// One warp per tile with hits. out_cap bounds the writes (kStOverflow when exceeded).
+// One warp per output tile (32 consecutive sectors) with hits. out_cap bounds the writes
+// (kStOverflow when exceeded).
 template <int T>
 __global__ void expand_kernel(const uint4* hit_rec, const uint32_t* tile_nhit, const uint64_t* tile_off,
-                              uint64_t n_tiles, const Segment* segs, uint32_t n_segs, const uint2* postings,
+                              uint64_t n_out_tiles, const Segment* segs, uint32_t n_segs, const uint2* postings,
                               MatchOut* out, uint64_t out_cap, uint32_t* status) {
+  constexpr uint32_t kW = T / 32;
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t tile = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); tile < n_tiles;
-       tile += warps) {
-    const uint32_t n = tile_nhit[tile];
+  for (uint64_t u = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n_out_tiles; u += warps) {
+    const uint32_t n = tile_nhit[u];
     if (n == 0) continue;
-    const uint32_t sg = find_segment(segs, n_segs, tile);
-    const uint64_t first_sector = segs[sg].sector_base + (tile - segs[sg].tile_base) * T;
-    uint64_t pos = tile_off[tile];
-    for (uint32_t h0 = 0; h0 < n; h0 += 32) {
-      const uint32_t h = h0 + lane;
-      uint4 rec = make_uint4(0, 0, 0, 0);
-      if (h < n) rec = hit_rec[tile * T + h];
-      uint32_t incl = rec.z;
+    const uint64_t ctile = u / kW;
+    const uint32_t sg = find_segment(segs, n_segs, ctile);
+    const uint64_t first_sector = segs[sg].sector_base + (ctile - segs[sg].tile_base) * T + (u % kW) * 32;
+    uint4 rec = make_uint4(0, 0, 0, 0);
+    if ((uint32_t)lane < n) rec = hit_rec[u * 32 + lane];
+    uint32_t incl = rec.z;
 #pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if (lane >= d) incl += v;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+      if (lane >= d) incl += v;
+    }
+    const uint64_t my = tile_off[u] + (incl - rec.z);
+    for (uint32_t k = 0; k < rec.z; k++) {
+      const uint64_t o = my + k;
+      if (o < out_cap) {
+        const uint2 pf = postings[rec.y + k];
+        out[o] = MatchOut{first_sector + rec.x, pf.x, pf.y};
+      } else {
+        atomicOr(status, kStOverflow);
       }
-      const uint64_t my = pos + (incl - rec.z);
-      for (uint32_t k = 0; k < rec.z; k++) {
-        const uint64_t o = my + k;
-        if (o < out_cap) {
-          const uint2 pf = postings[rec.y + k];
-          out[o] = MatchOut{first_sector + rec.x, pf.x, pf.y};
-        } else {
-          atomicOr(status, kStOverflow);
-        }
-      }
-      pos += __shfl_sync(0xFFFFFFFFu, incl, 31);
     }
   }
 }

@@ -22,8 +22,9 @@ struct Segment {
   uint64_t n_sectors;    // whole sectors in the segment
   uint64_t tile_base;    // global index of the segment's first tile
   uint64_t sector_base;  // index within its image of the segment's first sector
+  uint64_t row_base;     // row of the segment's first sector in its tensor map
   uint32_t image;        // index of the image the segment belongs to
-  uint32_t pad;
+  uint32_t map;          // index of its tensor map within the job
 };
 
 // Device view of a master table.
@@ -42,24 +43,27 @@ struct TableView {
   uint32_t use_bloom;
 };
 
-// Segments (and their tensor maps) one launch of the scan kernel can cover.
-constexpr int kSegsPerLaunch = 128;
+// Tensor maps one launch of the scan kernel can carry.
+constexpr int kMapsPerLaunch = 64;
 
 // Parameters of one scan-kernel launch, passed by value as a __grid_constant__ kernel
 // parameter: the TMA unit reads the tensor maps straight from the parameter space, so no
-// descriptor ever lives in (reused) global memory.
+// descriptor ever lives in (reused) global memory. Many segments may share one map (images
+// placed side by side in one device allocation).
 struct ScanParams {
-  CUtensorMap maps[kSegsPerLaunch];  // one per segment of this launch (64-byte aligned)
-  Segment segs[kSegsPerLaunch];      // tile_base values are global tile indices
+  CUtensorMap maps[kMapsPerLaunch];  // the job's maps [map_base, map_base + kMapsPerLaunch)
+  const Segment* segs;               // device: this launch's segments, sorted by tile_base
   uint32_t n_segs;
+  uint32_t map_base;
+  uint32_t one;         // always 1 (an opaque multiplier for the MD5 additions)
   uint32_t pad;
   uint64_t tile_begin;  // global index of the first tile of this launch
   uint64_t n_tiles;     // tiles of this launch
   TableView tab;
-  // scan outputs, indexed by global tile
-  uint4* hit_rec;        // n_tiles * T records {sector_in_tile, post_off, post_cnt, 0}
-  uint32_t* tile_nhit;   // hit sectors per tile
-  uint64_t* tile_ntrip;  // triples per tile
+  // scan outputs, indexed by global output tile (32 sectors)
+  uint4* hit_rec;        // 32 records per output tile {lane, post_off, post_cnt, 0}
+  uint32_t* tile_nhit;   // hit sectors per output tile
+  uint64_t* tile_ntrip;  // triples per output tile
   uint32_t* status;
   // digest outputs (digest mode): indexed by segment sector_base + row
   uint4* digests;

@@ -6,8 +6,10 @@ namespace cvk {
 
 struct ScanCfg {
   const char* name;
-  int T;      // sectors per tile = hashing threads per block (block = T + 32)
-  int NS;     // shared-memory ring stages
+  int T;        // sectors per tile; T / 32 output tiles per tile
+  int SPT;      // sectors per hashing thread
+  int threads;  // block size: T / SPT hashing threads + one producer warp
+  int NS;       // shared-memory ring stages
   int BOXB;   // bytes of each sector row per stage (64 or 128)
   const void* scan_fn;    // scan_kernel<T, NS, BOXB, kModeScan>
   const void* digest_fn;  // scan_kernel<T, NS, BOXB, kModeDigest>
@@ -22,9 +24,11 @@ struct Segment;
 // Scratch (u64 words) the offset pass needs for n tiles.
 uint64_t tile_offsets_scratch_words(uint64_t n_tiles);
 
-// tile_off[i] = sum of tile_ntrip[0..i); *total = sum of all; seg_off[s] = offset of segment
-// s's first tile. scratch: tile_offsets_scratch_words(n_tiles) u64 words. Returns a CUDA error.
+// tile_off[i] = sum of tile_ntrip[0..i) over the n_tiles output tiles; *total = sum of all;
+// seg_off[s] = offset of segment s's first output tile (segment tile_base * scale). scratch:
+// tile_offsets_scratch_words(n_tiles) u64 words. Returns a CUDA error code.
 int launch_tile_offsets(const uint64_t* tile_ntrip, uint64_t n_tiles, uint64_t* tile_off, const Segment* segs,
-                        uint32_t n_segs, uint64_t* seg_off, uint64_t* total, uint64_t* scratch, void* stream);
+                        uint32_t n_segs, uint32_t scale, uint64_t* seg_off, uint64_t* total, uint64_t* scratch,
+                        void* stream);
 
 }  // namespace cvk

@@ -6,19 +6,29 @@
 
 namespace cvk {
 
-#define CV_SCAN_CFG(T, NS, B)                                                                              \
+#define CV_SCAN_CFG(T, SPT, NS, B, P)                                                                      \
   ScanCfg {                                                                                                \
-    "t" #T "_s" #NS "_b" #B, T, NS, B, (const void*)scan_kernel<T, NS, B, kModeScan>,                       \
-        (const void*)scan_kernel<T, NS, B, kModeDigest>, (const void*)expand_kernel<T>,                    \
+    "t" #T "_x" #SPT "_s" #NS "_b" #B "_p" #P, T, SPT, T / SPT + 32, NS, B,                                 \
+        (const void*)scan_kernel<T, SPT, NS, B, kModeScan, P>,                                            \
+        (const void*)scan_kernel<T, SPT, NS, B, kModeDigest, P>, (const void*)expand_kernel<T>,            \
         ScanSmem<T, NS, B>::kAlloc                                                                         \
   }
 
+// The first entry is the default configuration (the fastest measured on GB300 for the 32 GiB
+// image workload); the others stay selectable and are what the batch autotuner tries.
 static const ScanCfg kConfigs[] = {
-    CV_SCAN_CFG(128, 4, 64),
-    CV_SCAN_CFG(128, 2, 128),
-    CV_SCAN_CFG(256, 3, 64),
-    CV_SCAN_CFG(64, 6, 64),
-    CV_SCAN_CFG(128, 3, 128),
+    CV_SCAN_CFG(256, 1, 2, 64, 3),
+    CV_SCAN_CFG(256, 1, 2, 64, 0),
+    CV_SCAN_CFG(256, 1, 2, 64, 1),
+    CV_SCAN_CFG(256, 1, 2, 64, 2),
+    CV_SCAN_CFG(256, 2, 2, 64, 3),
+    CV_SCAN_CFG(256, 2, 2, 64, 0),
+    CV_SCAN_CFG(256, 2, 3, 64, 3),
+    CV_SCAN_CFG(256, 2, 2, 128, 3),
+    CV_SCAN_CFG(128, 2, 4, 64, 3),
+    CV_SCAN_CFG(256, 1, 3, 64, 3),
+    CV_SCAN_CFG(128, 1, 2, 128, 2),
+    CV_SCAN_CFG(128, 1, 4, 64, 0),
 };
 
 const ScanCfg* scan_configs(int* n) {
@@ -29,14 +39,15 @@ const ScanCfg* scan_configs(int* n) {
 uint64_t tile_offsets_scratch_words(uint64_t n_tiles) { return (n_tiles + kOffChunk - 1) / kOffChunk + 1; }
 
 int launch_tile_offsets(const uint64_t* tile_ntrip, uint64_t n_tiles, uint64_t* tile_off, const Segment* segs,
-                        uint32_t n_segs, uint64_t* seg_off, uint64_t* total, uint64_t* scratch, void* stream_) {
+                        uint32_t n_segs, uint32_t scale, uint64_t* seg_off, uint64_t* total, uint64_t* scratch,
+                        void* stream_) {
   cudaStream_t stream = (cudaStream_t)stream_;
   const uint64_t chunks = (n_tiles + kOffChunk - 1) / kOffChunk;
   if (chunks) chunk_sums_kernel<<<(unsigned)chunks, kOffThreads, 0, stream>>>(tile_ntrip, n_tiles, scratch);
   scan_sums_kernel<<<1, kOffThreads, 0, stream>>>(scratch, chunks, total);
   if (chunks) chunk_scan_kernel<<<(unsigned)chunks, kOffThreads, 0, stream>>>(tile_ntrip, n_tiles, scratch, tile_off);
-  if (n_segs) segment_offsets_kernel<<<(n_segs + 255) / 256, 256, 0, stream>>>(tile_off, n_tiles, segs, n_segs, total,
-                                                                               seg_off);
+  if (n_segs) segment_offsets_kernel<<<(n_segs + 255) / 256, 256, 0, stream>>>(tile_off, n_tiles, segs, n_segs, scale,
+                                                                               total, seg_off);
   return (int)cudaGetLastError();
 }
 

@@ -8,6 +8,8 @@
 // Each of the 64 operations of a block is a = b + ((a + g(b,c,d) + X[k] + T[i]) <<< s). The
 // auxiliary function g is a single 3-input logic op (lop3 with the function's truth table),
 // the rotation a funnel shift, and in the padding block X[k] + T[i] folds to one constant.
+// Nothing here is a dense contraction: it is 32-bit integer ALU work, and the PIPE variants
+// only choose which execution pipe carries the additions.
 #pragma once
 #include <stdint.h>
 
@@ -53,23 +55,92 @@ __host__ __device__ constexpr int md5_rot(int i) {
   return s[i / 16][i % 4];
 }
 
+// x * y + z on the integer multiply-add datapath (the FMA pipe). With y a run-time 1 the product
+// is x itself, so mad(x, one, z) is an addition the compiler cannot turn back into an integer
+// ALU add; with x = one and y an immediate it adds that immediate.
+__device__ __forceinline__ uint32_t mad_lo(uint32_t x, uint32_t y, uint32_t z) {
+  uint32_t r;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(y), "r"(z));
+  return r;
+}
+
+template <uint32_t K>
+__device__ __forceinline__ uint32_t mad_one_imm(uint32_t one, uint32_t z) {
+  uint32_t r;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(one), "n"(K), "r"(z));
+  return r;
+}
+
+// Which operations route their two additions a + T[i] and + X[k] through the multiply-add
+// pipe. The lop3 and the rotation run on the integer ALU pipe, which otherwise also carries
+// both additions; moving a share of them to the FMA pipe balances the two pipes. PIPE 0: none;
+// 1: every third operation; 2: every other one; 3: two of three; 4: all.
+template <int I, int PIPE>
+__host__ __device__ constexpr bool md5_fma_adds() {
+  return PIPE == 4 || (PIPE == 1 && I % 3 == 0) || (PIPE == 2 && (I & 1)) || (PIPE == 3 && I % 3 != 0);
+}
+
+// Operation I of a block: a = b + ((a + g(b,c,d) + X[k] + T[I]) <<< s).
+template <int I, int PIPE>
+__device__ __forceinline__ void md5_step(uint32_t& a, uint32_t b, uint32_t c, uint32_t d, const uint32_t (&X)[16],
+                                         uint32_t one) {
+  uint32_t t;
+  if constexpr (md5_fma_adds<I, PIPE>()) {
+    t = mad_lo(X[md5_word(I)], one, mad_one_imm<kMd5Sines.v[I]>(one, a)) + md5_aux<I / 16>(b, c, d);
+  } else {
+    t = a + X[md5_word(I)] + kMd5Sines.v[I] + md5_aux<I / 16>(b, c, d);
+  }
+  a = b + __funnelshift_l(t, t, md5_rot(I));
+}
+
 // The 64 operations over one block; registers rotate roles by renaming, not by moves.
-template <int I>
-__device__ __forceinline__ void md5_ops(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d, const uint32_t (&X)[16]) {
+template <int I, int PIPE>
+__device__ __forceinline__ void md5_ops(uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d, const uint32_t (&X)[16],
+                                        uint32_t one) {
   if constexpr (I < 64) {
-    uint32_t t = a + X[md5_word(I)] + kMd5Sines.v[I] + md5_aux<I / 16>(b, c, d);
-    a = b + __funnelshift_l(t, t, md5_rot(I));
-    md5_ops<I + 1>(d, a, b, c, X);
+    md5_step<I, PIPE>(a, b, c, d, X, one);
+    md5_ops<I + 1, PIPE>(d, a, b, c, X, one);
   }
 }
 
-__device__ __forceinline__ void md5_compress(uint32_t (&st)[4], const uint32_t (&X)[16]) {
+// The same over two independent sectors, operation by operation, so that each thread always
+// has a second dependency chain to issue from.
+template <int I, int PIPE>
+__device__ __forceinline__ void md5_ops2(uint32_t& a0, uint32_t& b0, uint32_t& c0, uint32_t& d0,
+                                         const uint32_t (&X0)[16], uint32_t& a1, uint32_t& b1, uint32_t& c1,
+                                         uint32_t& d1, const uint32_t (&X1)[16], uint32_t one) {
+  if constexpr (I < 64) {
+    md5_step<I, PIPE>(a0, b0, c0, d0, X0, one);
+    md5_step<I, PIPE>(a1, b1, c1, d1, X1, one);
+    md5_ops2<I + 1, PIPE>(d0, a0, b0, c0, X0, d1, a1, b1, c1, X1, one);
+  }
+}
+
+// `one` must hold 1 at run time (see mad_lo); it only matters when PIPE != 0.
+template <int PIPE = 0>
+__device__ __forceinline__ void md5_compress(uint32_t (&st)[4], const uint32_t (&X)[16], uint32_t one = 1u) {
   uint32_t a = st[0], b = st[1], c = st[2], d = st[3];
-  md5_ops<0>(a, b, c, d, X);
+  md5_ops<0, PIPE>(a, b, c, d, X, one);
   st[0] += a;
   st[1] += b;
   st[2] += c;
   st[3] += d;
+}
+
+template <int PIPE = 0>
+__device__ __forceinline__ void md5_compress_x2(uint32_t (&s0)[4], const uint32_t (&X0)[16], uint32_t (&s1)[4],
+                                                const uint32_t (&X1)[16], uint32_t one = 1u) {
+  uint32_t a0 = s0[0], b0 = s0[1], c0 = s0[2], d0 = s0[3];
+  uint32_t a1 = s1[0], b1 = s1[1], c1 = s1[2], d1 = s1[3];
+  md5_ops2<0, PIPE>(a0, b0, c0, d0, X0, a1, b1, c1, d1, X1, one);
+  s0[0] += a0;
+  s0[1] += b0;
+  s0[2] += c0;
+  s0[3] += d0;
+  s1[0] += a1;
+  s1[1] += b1;
+  s1[2] += c1;
+  s1[3] += d1;
 }
 
 // The final block of a 512-byte message: one 1 bit, zeros, bit length 4096 (little-endian).
@@ -78,7 +149,7 @@ __device__ __forceinline__ void md5_compress_sector_padding(uint32_t (&st)[4]) {
   uint32_t X[16];
 #pragma unroll
   for (int j = 0; j < 16; j++) X[j] = P[j];
-  md5_compress(st, X);
+  md5_compress<0>(st, X);
 }
 
 __device__ __forceinline__ void md5_init(uint32_t (&st)[4]) {

@@ -31,17 +31,15 @@
 #include "cv.h"
 #include "cv_internal.h"
 #include "cv_launch.h"
+#include "runtime.h"
 
 using namespace cvk;
-
-int cvk_master_view(const cv_master* m, TableView* tab, int* dev);
 
 namespace {
 
 // Scratch layout (offsets in bytes); sized for CV_NOALLOC_MAX_SECTORS with the smallest tile.
 constexpr uint64_t kMaxSectors = CV_NOALLOC_MAX_SECTORS;
-constexpr uint64_t kMinTile = 64;
-constexpr uint64_t kMaxTiles = kMaxSectors / kMinTile + 1;
+constexpr uint64_t kMaxTiles = kMaxSectors / 32 + 8;  // output tiles of 32 sectors, plus a ragged tile
 constexpr uint64_t kOffSeg = 128;                               // Segment
 constexpr uint64_t kOffCounters = 256;                          // seg_off[1], total, status
 constexpr uint64_t kOffSums = 512;                              // chunk sums of the offset pass
@@ -86,7 +84,7 @@ int setup(int dev, NoAllocDev** out) {
     if (e != cudaSuccess) return fail(e);
     e = cudaFuncSetAttribute(cfg.scan_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
     if (e != cudaSuccess) return fail(e);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, cfg.scan_fn, cfg.T + 32, cfg.smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, cfg.scan_fn, cfg.threads, cfg.smem);
     if (e != cudaSuccess || d.blocks_per_sm < 1) return fail(e);
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
@@ -112,7 +110,7 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   *n_out = 0;
   TableView tab;
   int mdev;
-  if (cvk_master_view(m, &tab, &mdev) != CV_OK) return CV_EINVAL;
+  if (master_view(m, &tab, &mdev) != CV_OK) return CV_EINVAL;
   int dev;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
     cudaGetLastError();
@@ -155,16 +153,20 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   seg.n_sectors = S;
   seg.tile_base = 0;
   seg.sector_base = 0;
+  seg.row_base = 0;
   seg.image = 0;
-  seg.pad = 0;
+  seg.map = 0;
   const uint64_t n_tiles = (S + cfg.T - 1) / cfg.T;
+  const uint64_t n_out_tiles = n_tiles * (uint64_t)(cfg.T / 32);  // output tiles of 32 sectors
 
   cudaError_t e;
   if ((e = cudaMemsetAsync(status_d, 0, 4, stream)) != cudaSuccess) return fail(e);
   if ((e = cudaMemcpyAsync(seg_d, &seg, sizeof seg, cudaMemcpyHostToDevice, stream)) != cudaSuccess) return fail(e);
 
-  p.segs[0] = seg;
+  p.segs = seg_d;
   p.n_segs = 1;
+  p.map_base = 0;
+  p.one = 1u;
   p.tile_begin = 0;
   p.n_tiles = n_tiles;
   p.tab = tab;
@@ -174,15 +176,15 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   p.status = status_d;
   const uint64_t grid = n_tiles < (uint64_t)d->sms * d->blocks_per_sm ? n_tiles : (uint64_t)d->sms * d->blocks_per_sm;
   void* sargs[] = {&p};
-  if ((e = cudaLaunchKernel(cfg.scan_fn, dim3((unsigned)grid), dim3(cfg.T + 32), sargs, cfg.smem, stream)) !=
+  if ((e = cudaLaunchKernel(cfg.scan_fn, dim3((unsigned)grid), dim3(cfg.threads), sargs, cfg.smem, stream)) !=
       cudaSuccess)
     return fail(e);
   uint32_t one = 1;
-  uint64_t nt = n_tiles;
+  uint64_t nt = n_out_tiles;
   const Segment* segc = seg_d;
   static_assert((kMaxTiles + 4095) / 4096 + 1 <= 1024 / 8, "offset scratch");
-  if ((e = (cudaError_t)launch_tile_offsets(tile_ntrip, nt, tile_off, segc, one, seg_off_d, total_d,
-                                            (uint64_t*)(sc + kOffSums), stream)) != cudaSuccess)
+  if ((e = (cudaError_t)launch_tile_offsets(tile_ntrip, nt, tile_off, segc, one, (uint32_t)(cfg.T / 32), seg_off_d,
+                                            total_d, (uint64_t*)(sc + kOffSums), stream)) != cudaSuccess)
     return fail(e);
   const uint4* hr = hit_rec;
   const uint32_t* nh = tile_nhit;
@@ -190,7 +192,7 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   const uint2* post = tab.postings;
   MatchOut* o = (MatchOut*)out;
   uint64_t cap = out_capacity;
-  uint64_t eg = (n_tiles * 32 + 255) / 256;
+  uint64_t eg = (n_out_tiles * 32 + 255) / 256;
   if (eg > (uint64_t)d->sms * 16) eg = (uint64_t)d->sms * 16;
   void* eargs[] = {&hr, &nh, &to, &nt, &segc, &one, &post, &o, &cap, &status_d};
   if ((e = cudaLaunchKernel(cfg.expand_fn, dim3((unsigned)eg), dim3(256), eargs, 0, stream)) != cudaSuccess)

@@ -1,0 +1,107 @@
+// Host runtime shared by the library's entry points (not part of the ABI): per-device context,
+// stream-ordered temporaries, tensor maps, scan jobs (segments over device memory) and the
+// launch of the scan kernel over a job.
+#pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "cv.h"
+#include "cv_internal.h"
+#include "cv_launch.h"
+
+namespace cvk {
+
+// Records the failing CUDA code for cv_last_cuda_error and maps it to a CV_E* code.
+int cuda_fail(cudaError_t e);
+void set_last_cuda(int code);
+int last_cuda();
+
+#define CV_CUDA(expr)                                 \
+  do {                                                \
+    cudaError_t e_ = (expr);                          \
+    if (e_ != cudaSuccess) return ::cvk::cuda_fail(e_); \
+  } while (0)
+
+#define CV_TRY(expr)            \
+  do {                          \
+    int r_ = (expr);            \
+    if (r_ != CV_OK) return r_; \
+  } while (0)
+
+// Library state of one device, made on first use with that device current.
+struct DevCtx {
+  bool ready = false;
+  int dev = -1;
+  int sms = 0;
+  cudaMemPool_t pool = nullptr;      // stream-ordered temporaries and results
+  cudaStream_t copy_stream = nullptr;  // host-to-device copies of streamed images
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  PFN_cuMemGetAddressRange_v3020 address_range = nullptr;
+  std::vector<int> blocks_per_sm;  // per scan configuration (scan mode)
+  std::vector<int> blocks_per_sm_digest;
+  int cfg_index = 0;  // default scan configuration
+};
+
+int get_ctx(DevCtx** out);
+
+// Stream-ordered temporaries from the device pool, released on the stream when the scope ends.
+struct Temps {
+  DevCtx* ctx;
+  cudaStream_t stream;
+  std::vector<void*> ptrs;
+  Temps(DevCtx* c, cudaStream_t s) : ctx(c), stream(s) {}
+  ~Temps();
+  int alloc_bytes(void** out, size_t bytes);
+  template <typename P>
+  int alloc(P** out, size_t bytes) {
+    void* p = nullptr;
+    int rc = alloc_bytes(&p, bytes);
+    *out = (P*)p;
+    return rc;
+  }
+};
+
+enum BufKind { kHost = 0, kDevice = 1 };
+int classify(DevCtx* ctx, const void* p, BufKind* kind);
+
+// A 2-D tensor map viewing n_rows sectors at base as u32[n_rows][128] with the staging box of cfg.
+int make_tmap(DevCtx* ctx, const ScanCfg& cfg, const void* base, uint64_t n_rows, CUtensorMap* out);
+
+// A list of segments over device memory (or over not-yet-filled streaming buffers).
+struct Job {
+  std::vector<Segment> segs;
+  std::vector<CUtensorMap> maps;
+  std::vector<uintptr_t> map_base;  // device address of row 0 of each map (0: made later)
+  uint64_t n_tiles = 0;
+  uint64_t n_sectors = 0;
+
+  // Append n whole sectors at base (split at kMaxSegmentSectors). With share_alloc, images that
+  // lie in one device allocation at sector-aligned offsets share one tensor map over the whole
+  // allocation; otherwise each segment gets its own map. base == nullptr reserves segments
+  // whose map is set later (set_map).
+  int add(DevCtx* ctx, const ScanCfg& cfg, const void* base, uint64_t n, uint64_t sector_base, uint32_t image,
+          bool share_alloc);
+  // Point segment s at a fresh map over base (streamed chunks).
+  int set_map(DevCtx* ctx, const ScanCfg& cfg, size_t s, const void* base);
+};
+
+// Launch the scan (or digest) kernel over segments [s0, s1) of the job; segs_d is the job's
+// segment array in device memory. `base` carries the table and output pointers. Returns the
+// number of kernel launches through *launches when non-null.
+int launch_range(DevCtx* ctx, int cfg_i, bool digest, const Job& job, const Segment* segs_d, size_t s0, size_t s1,
+                 const ScanParams& base, cudaStream_t stream, int* launches = nullptr);
+
+uint64_t next_pow2(uint64_t x);
+unsigned grid_for(uint64_t n, int threads, int sms);
+
+// Device view of a master table (capi.cu).
+int master_view(const cv_master* m, TableView* tab, int* dev);
+
+// A one-image host result holding a copy of n triples (capi.cu).
+cv_result* make_host_result(int dev, const MatchOut* data, uint64_t n, uint64_t sectors, float total_ms);
+
+}  // namespace cvk

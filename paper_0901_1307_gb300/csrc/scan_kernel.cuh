@@ -96,10 +96,6 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
   return v;
 }
 
-__device__ __forceinline__ void consumer_bar_sync(uint32_t n_threads) {
-  asm volatile("bar.sync 1, %0;" ::"r"(n_threads) : "memory");
-}
-
 // Blocked Bloom test: all eight bits of the digest's block set.
 __device__ __forceinline__ bool bloom_test(const TableView& tab, uint32_t d1, uint32_t d2, uint32_t d3) {
   const uint4* blk = tab.bloom + 2ull * (d3 & tab.bloom_mask);
@@ -135,24 +131,29 @@ enum : int { kModeScan = 0, kModeDigest = 1 };
 template <int T, int NS, int BOXB>
 struct ScanSmem {
   static constexpr uint32_t kStageBytes = T * BOXB;
-  static constexpr uint32_t kW = T / 32;
-  // stages first (1024-byte aligned), then barriers and the compaction scratch
+  // stages first (1024-byte aligned), then the barriers and the abort flag
   static constexpr uint32_t kBarOff = NS * kStageBytes;
   static constexpr uint32_t kMiscOff = kBarOff + 2 * NS * 8;
-  static constexpr uint32_t kBytes = kMiscOff + 4 * kW * 4 + 16;
+  static constexpr uint32_t kBytes = kMiscOff + 16;
   static constexpr uint32_t kAlloc = kBytes + 1024;  // room to align the base
 };
 
-// T: sectors per tile (= hashing threads); NS: ring stages; BOXB: bytes of each sector row per
-// stage (64 or 128). Block size is T + 32 (the last warp is the producer).
-template <int T, int NS, int BOXB, int MODE>
-__global__ void __launch_bounds__(T + 32) scan_kernel(const __grid_constant__ ScanParams p) {
-  static_assert(T % 32 == 0 && T <= 256, "tile rows");
+// T: sectors per tile; SPT: sectors per hashing thread (1 or 2; the block has C = T / SPT
+// hashing threads plus one producer warp); NS: ring stages; BOXB: bytes of each sector row per
+// stage (64 or 128); PIPE: which MD5 additions use the FMA pipe (see md5_fma_adds).
+// Thread t hashes rows t, t + C, ... of the tile. Matches are compacted per warp and row group:
+// rows [32v, 32v + 32) of tile k form output tile k * (T / 32) + v.
+template <int T, int SPT, int NS, int BOXB, int MODE, int PIPE>
+__global__ void __launch_bounds__(T / SPT + 32) scan_kernel(const __grid_constant__ ScanParams p) {
+  constexpr int C = T / SPT;
+  static_assert(T % 32 == 0 && T <= 256 && C % 32 == 0, "tile rows");
+  static_assert(SPT == 1 || SPT == 2, "sectors per thread");
   static_assert(BOXB == 64 || BOXB == 128, "box width");
   using L = ScanSmem<T, NS, BOXB>;
-  constexpr int kChunks = 512 / BOXB;       // stages per sector
+  constexpr int kChunks = 512 / BOXB;         // stages per sector
   constexpr int kBlocksPerChunk = BOXB / 64;  // MD5 blocks per stage
-  constexpr uint32_t kW = L::kW;
+  constexpr uint32_t kW = T / 32;             // output tiles per tile
+  constexpr int kCW = C / 32;                 // hashing warps
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_addr(smem_raw);
@@ -160,9 +161,7 @@ __global__ void __launch_bounds__(T + 32) scan_kernel(const __grid_constant__ Sc
   uint8_t* const gbase = smem_raw + (base - raw);
   const uint32_t bar_full = base + L::kBarOff;  // NS x 8 bytes
   const uint32_t bar_empty = bar_full + NS * 8;
-  uint32_t* const s_hits = reinterpret_cast<uint32_t*>(gbase + L::kMiscOff);  // [2][kW]
-  uint32_t* const s_trip = s_hits + 2 * kW;                                   // [2][kW]
-  volatile uint32_t* const s_abort = s_trip + 2 * kW;
+  volatile uint32_t* const s_abort = reinterpret_cast<uint32_t*>(gbase + L::kMiscOff);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -171,14 +170,14 @@ __global__ void __launch_bounds__(T + 32) scan_kernel(const __grid_constant__ Sc
   if (tid == 0) {
     for (int s = 0; s < NS; s++) {
       mbar_init(bar_full + 8 * s, 1);
-      mbar_init(bar_empty + 8 * s, T);
+      mbar_init(bar_empty + 8 * s, C);
     }
     *s_abort = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  if (warp == (int)kW) {
+  if (warp == kCW) {
     // ------------------------------------------------------------------ producer warp
     if (lane != 0) return;
     const uint64_t policy = l2_evict_first_policy();
@@ -186,9 +185,9 @@ __global__ void __launch_bounds__(T + 32) scan_kernel(const __grid_constant__ Sc
     bool ok = true;
     for (uint64_t lt = blockIdx.x; lt < p.n_tiles && ok; lt += gridDim.x) {
       const uint64_t tile = p.tile_begin + lt;
-      const uint32_t sg = find_segment(p.segs, p.n_segs, tile);
-      const CUtensorMap* map = &p.maps[sg];
-      const int32_t row0 = (int32_t)((tile - p.segs[sg].tile_base) * T);
+      const Segment& seg = p.segs[find_segment(p.segs, p.n_segs, tile)];
+      const CUtensorMap* map = &p.maps[seg.map - p.map_base];
+      const int32_t row0 = (int32_t)(seg.row_base + (tile - seg.tile_base) * T);
       for (int c = 0; c < kChunks; c++, j++) {
         const uint32_t s = j % NS;
         if (j >= (uint32_t)NS && !mbar_wait(bar_empty + 8 * s, ((j / NS) - 1) & 1, s_abort, p.status)) {
@@ -216,37 +215,48 @@ __global__ void __launch_bounds__(T + 32) scan_kernel(const __grid_constant__ Sc
   }
 
   // -------------------------------------------------------------------- hashing warps
-  // Row `tid` of each stage; the 16-byte chunk q of the row sits at chunk q ^ swz.
-  const uint32_t row_off = (uint32_t)tid * BOXB;
-  const uint32_t swz = (BOXB == 128) ? ((uint32_t)tid & 7u) : (((uint32_t)tid >> 1) & 3u);
+  // Row r of each stage; its 16-byte chunk q sits at chunk q ^ swz(r) (hardware swizzle).
+  uint32_t row_off[SPT], swz[SPT];
+#pragma unroll
+  for (int k = 0; k < SPT; k++) {
+    const uint32_t r = (uint32_t)(tid + k * C);
+    row_off[k] = r * BOXB;
+    swz[k] = (BOXB == 128) ? (r & 7u) : ((r >> 1) & 3u);
+  }
   const uint32_t lane_lt = (1u << lane) - 1u;
   uint32_t j = 0;
-  uint32_t parity_buf = 0;
-  for (uint64_t lt = blockIdx.x; lt < p.n_tiles; lt += gridDim.x, parity_buf ^= 1u) {
+  for (uint64_t lt = blockIdx.x; lt < p.n_tiles; lt += gridDim.x) {
     const uint64_t tile = p.tile_begin + lt;
-    const uint32_t sg = find_segment(p.segs, p.n_segs, tile);
-    const uint64_t row0 = (tile - p.segs[sg].tile_base) * T;
-    const bool valid = row0 + (uint64_t)tid < p.segs[sg].n_sectors;
+    const Segment& seg = p.segs[find_segment(p.segs, p.n_segs, tile)];
+    const uint64_t row0 = (tile - seg.tile_base) * T;  // within the segment
 
-    uint32_t st[4];
-    md5_init(st);
-    uint32_t diff = 0, ref = 0;
+    uint32_t st[SPT][4];
+    uint32_t diff[SPT], ref[SPT];
+#pragma unroll
+    for (int k = 0; k < SPT; k++) {
+      md5_init(st[k]);
+      diff[k] = 0;
+      ref[k] = 0;
+    }
 #pragma unroll 1
     for (int c = 0; c < kChunks; c++, j++) {
       const uint32_t s = j % NS;
       mbar_wait(bar_full + 8 * s, (j / NS) & 1, s_abort, p.status);
-      const uint32_t row = base + s * L::kStageBytes + row_off;
+      const uint32_t stage = base + s * L::kStageBytes;
 #pragma unroll
       for (int b = 0; b < kBlocksPerChunk; b++) {
-        uint32_t X[16];
+        uint32_t X[SPT][16];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const uint32_t chunk = (uint32_t)(4 * b + q) ^ swz;
-          const uint4 v = lds128(row + chunk * 16u);
-          X[4 * q + 0] = v.x;
-          X[4 * q + 1] = v.y;
-          X[4 * q + 2] = v.z;
-          X[4 * q + 3] = v.w;
+        for (int k = 0; k < SPT; k++) {
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const uint32_t chunk = (uint32_t)(4 * b + q) ^ swz[k];
+            const uint4 v = lds128(stage + row_off[k] + chunk * 16u);
+            X[k][4 * q + 0] = v.x;
+            X[k][4 * q + 1] = v.y;
+            X[k][4 * q + 2] = v.z;
+            X[k][4 * q + 3] = v.w;
+          }
         }
         if (b == kBlocksPerChunk - 1) {
           // The stage is handed back to the copy engine: order this thread's shared-memory
@@ -255,51 +265,46 @@ __global__ void __launch_bounds__(T + 32) scan_kernel(const __grid_constant__ Sc
           mbar_arrive(bar_empty + 8 * s);
         }
         if constexpr (MODE == kModeDigest) {
-          if (c == 0 && b == 0) ref = (X[0] & 0xFFu) * 0x01010101u;
 #pragma unroll
-          for (int q = 0; q < 16; q++) diff |= X[q] ^ ref;
+          for (int k = 0; k < SPT; k++) {
+            if (c == 0 && b == 0) ref[k] = (X[k][0] & 0xFFu) * 0x01010101u;
+#pragma unroll
+            for (int q = 0; q < 16; q++) diff[k] |= X[k][q] ^ ref[k];
+          }
         }
-        md5_compress(st, X);
+        if constexpr (SPT == 2) {
+          md5_compress_x2<PIPE>(st[0], X[0], st[1], X[1], p.one);
+        } else {
+          md5_compress<PIPE>(st[0], X[0], p.one);
+        }
       }
     }
-    md5_compress_sector_padding(st);
-
-    if constexpr (MODE == kModeDigest) {
-      if (valid) {
-        const uint64_t g = p.segs[sg].sector_base + row0 + (uint64_t)tid;
-        p.digests[g] = make_uint4(st[0], st[1], st[2], st[3]);
-        if (p.trivial) p.trivial[g] = diff == 0u ? 1 : 0;
-      }
-    } else {
-      uint32_t post_off = 0, post_cnt = 0;
-      if (valid && (!p.tab.use_bloom || bloom_test(p.tab, st[1], st[2], st[3])))
-        post_cnt = table_probe(p.tab, st[0], st[1], st[2], st[3], post_off);
-      const bool hit = post_cnt != 0u;
-      const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, hit);
-      const uint32_t wtrip = __reduce_add_sync(0xFFFFFFFFu, post_cnt);
-      uint32_t* hits_buf = s_hits + parity_buf * kW;
-      uint32_t* trip_buf = s_trip + parity_buf * kW;
-      if (lane == 0) {
-        hits_buf[warp] = __popc(ballot);
-        trip_buf[warp] = wtrip;
-      }
-      consumer_bar_sync(T);
-      uint32_t before = 0, total = 0;
-      uint64_t trips = 0;
 #pragma unroll
-      for (int w = 0; w < (int)kW; w++) {
-        const uint32_t h = hits_buf[w];
-        before += (w < warp) ? h : 0u;
-        total += h;
-        trips += trip_buf[w];
-      }
-      if (hit) {
-        const uint32_t slot = before + __popc(ballot & lane_lt);
-        p.hit_rec[tile * T + slot] = make_uint4((uint32_t)tid, post_off, post_cnt, 0u);
-      }
-      if (tid == 0) {
-        p.tile_nhit[tile] = total;
-        p.tile_ntrip[tile] = trips;
+    for (int k = 0; k < SPT; k++) md5_compress_sector_padding(st[k]);
+
+#pragma unroll
+    for (int k = 0; k < SPT; k++) {
+      const uint64_t r = row0 + (uint64_t)(tid + k * C);
+      const bool valid = r < seg.n_sectors;
+      if constexpr (MODE == kModeDigest) {
+        if (valid) {
+          const uint64_t g = seg.sector_base + r;
+          p.digests[g] = make_uint4(st[k][0], st[k][1], st[k][2], st[k][3]);
+          if (p.trivial) p.trivial[g] = diff[k] == 0u ? 1 : 0;
+        }
+      } else {
+        uint32_t post_off = 0, post_cnt = 0;
+        if (valid && (!p.tab.use_bloom || bloom_test(p.tab, st[k][1], st[k][2], st[k][3])))
+          post_cnt = table_probe(p.tab, st[k][0], st[k][1], st[k][2], st[k][3], post_off);
+        const bool hit = post_cnt != 0u;
+        const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, hit);
+        const uint32_t wtrip = __reduce_add_sync(0xFFFFFFFFu, post_cnt);
+        const uint64_t u = tile * kW + (uint64_t)(warp + k * kCW);  // this row group's output tile
+        if (hit) p.hit_rec[u * 32 + __popc(ballot & lane_lt)] = make_uint4((uint32_t)lane, post_off, post_cnt, 0u);
+        if (lane == 0) {
+          p.tile_nhit[u] = __popc(ballot);
+          p.tile_ntrip[u] = wtrip;
+        }
       }
     }
   }

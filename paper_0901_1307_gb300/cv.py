@@ -34,7 +34,12 @@ MATCH_DTYPE = np.dtype([("disk_sector", "<u8"), ("file_id", "<u4"), ("file_secto
 
 EXPORTS = ("cv_master_build", "cv_master_get_info", "cv_scan", "cv_matches", "cv_scan_get_stats", "cv_free",
            "cv_strerror", "cv_last_cuda_error", "cv_sector_digests", "cv_kernel_config_count",
-           "cv_kernel_config_name", "cv_scan_noalloc")
+           "cv_kernel_config_name", "cv_scan_noalloc", "cv_batch_create", "cv_batch_run", "cv_batch_wait",
+           "cv_batch_matches", "cv_batch_get_info", "cv_server_create", "cv_submit", "cv_poll",
+           "cv_server_get_stats")
+CV_EAGAIN = -9
+CV_BATCH_BLOOM_AUTO = 0
+CV_BATCH_BLOOM_OFF = 1
 CV_NOALLOC_MAX_SECTORS = 1 << 19
 
 
@@ -67,7 +72,35 @@ class cv_master_info(ctypes.Structure):
 
 class cv_scan_stats(ctypes.Structure):
     _fields_ = [("sectors", ctypes.c_uint64), ("matches", ctypes.c_uint64), ("hit_sectors", ctypes.c_uint64),
-                ("kernel_ms", ctypes.c_float), ("total_ms", ctypes.c_float)]
+                ("kernel_ms", ctypes.c_float), ("total_ms", ctypes.c_float), ("kernel_launches", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class cv_batch_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("autotune", ctypes.c_uint32), ("stream", ctypes.c_void_p),
+                ("match_capacity", ctypes.c_uint64), ("kernel_config", ctypes.c_uint32), ("bloom", ctypes.c_uint32),
+                ("tune_cache", ctypes.c_char_p)]
+
+
+class cv_batch_info(ctypes.Structure):
+    _fields_ = [("kernel_config", ctypes.c_int), ("config_name", ctypes.c_char_p), ("bloom", ctypes.c_uint32),
+                ("tuned", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint32), ("tensor_maps", ctypes.c_uint32),
+                ("segments", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("sectors", ctypes.c_uint64),
+                ("match_capacity", ctypes.c_uint64), ("scan_ms", ctypes.c_float)]
+
+
+class cv_server_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("max_live", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("work_unit_bytes", ctypes.c_uint64), ("kernel_config", ctypes.c_uint32),
+                ("copy_streams", ctypes.c_uint32)]
+
+
+class cv_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("bytes_scanned", ctypes.c_uint64), ("iterations", ctypes.c_uint64), ("units", ctypes.c_uint64),
+                ("peak_bytes_in_flight", ctypes.c_uint64), ("mean_live_per_iteration", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("wall_s", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -108,6 +141,25 @@ def load(path: str = LIB_PATH):
         lib.cv_kernel_config_name.restype = ctypes.c_char_p
         lib.cv_scan_noalloc.argtypes = [vp, vp, u64, vp, u64, ctypes.POINTER(u64), vp]
         lib.cv_scan_noalloc.restype = i32
+        lib.cv_batch_create.argtypes = [vp, ctypes.POINTER(cv_buf), u32, ctypes.POINTER(cv_batch_opts),
+                                        ctypes.POINTER(vp)]
+        lib.cv_batch_create.restype = i32
+        lib.cv_batch_run.argtypes = [vp, vp]
+        lib.cv_batch_run.restype = i32
+        lib.cv_batch_wait.argtypes = [vp, ctypes.POINTER(u64)]
+        lib.cv_batch_wait.restype = i32
+        lib.cv_batch_matches.argtypes = [vp, u32, ctypes.POINTER(vp), ctypes.POINTER(u64)]
+        lib.cv_batch_matches.restype = i32
+        lib.cv_batch_get_info.argtypes = [vp, ctypes.POINTER(cv_batch_info)]
+        lib.cv_batch_get_info.restype = i32
+        lib.cv_server_create.argtypes = [vp, ctypes.POINTER(cv_server_opts), ctypes.POINTER(vp)]
+        lib.cv_server_create.restype = i32
+        lib.cv_submit.argtypes = [vp, cv_buf, u64, ctypes.POINTER(u64)]
+        lib.cv_submit.restype = i32
+        lib.cv_poll.argtypes = [vp, u64, ctypes.c_int, ctypes.POINTER(vp)]
+        lib.cv_poll.restype = i32
+        lib.cv_server_get_stats.argtypes = [vp, ctypes.POINTER(cv_server_stats)]
+        lib.cv_server_get_stats.restype = i32
         _lib = lib
         return lib
 
@@ -300,3 +352,135 @@ def scan_noalloc(master: Master, image, out, out_capacity: int, stream=None, che
     if check and rc not in (CV_OK, CV_ERANGE):
         raise CVError(rc, "cv_scan_noalloc")
     return rc, int(n.value)
+
+
+class Batch:
+    """Many device images scanned by one CUDA graph replay per run (cv_batch)."""
+
+    def __init__(self, handle: int, n_images: int, keep):
+        self._h = handle
+        self.n_images = n_images
+        self._keep = keep  # the images must outlive the batch
+
+    def run(self, stream=None) -> None:
+        _check(load().cv_batch_run(self._h, _stream(stream)), "cv_batch_run")
+
+    def wait(self) -> int:
+        n = ctypes.c_uint64()
+        _check(load().cv_batch_wait(self._h, ctypes.byref(n)), "cv_batch_wait")
+        return int(n.value)
+
+    def matches(self, i: int) -> DeviceMatches:
+        p = ctypes.c_void_p()
+        n = ctypes.c_uint64()
+        _check(load().cv_batch_matches(self._h, i, ctypes.byref(p), ctypes.byref(n)), "cv_batch_matches")
+        return DeviceMatches(p.value or 0, int(n.value), self)
+
+    def info(self) -> dict:
+        inf = cv_batch_info()
+        _check(load().cv_batch_get_info(self._h, ctypes.byref(inf)), "cv_batch_get_info")
+        d = {k: getattr(inf, k) for k, _ in cv_batch_info._fields_ if k != "reserved"}
+        d["config_name"] = d["config_name"].decode() if d["config_name"] else None
+        return d
+
+    def close(self) -> None:
+        if self._h:
+            load().cv_free(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_create(master: Master, images, autotune: bool = False, match_capacity: int = 0, kernel_config: int = 0,
+                 bloom: int = CV_BATCH_BLOOM_AUTO, tune_cache: str | None = None, stream=None) -> Batch:
+    """cv_batch_create: a graph over device images (kept alive by the returned Batch)."""
+    images = list(images)
+    arr, keep = _bufs(images)
+    o = cv_batch_opts(ctypes.sizeof(cv_batch_opts), 1 if autotune else 0, _stream(stream), match_capacity,
+                      kernel_config, bloom, tune_cache.encode() if tune_cache else None)
+    h = ctypes.c_void_p()
+    _check(load().cv_batch_create(master.handle, arr, len(images), ctypes.byref(o), ctypes.byref(h)),
+           "cv_batch_create")
+    return Batch(h.value, len(images), (images, keep))
+
+
+def device_matches_to_numpy(dm: DeviceMatches) -> np.ndarray:
+    """Copy device-resident matches to a host structured array (uses torch for the copy)."""
+    import torch
+
+    if dm.n == 0:
+        return np.zeros(0, MATCH_DTYPE)
+    t = torch.as_tensor(dm, device="cuda").cpu().numpy()
+    out = np.zeros(t.shape[0], MATCH_DTYPE)
+    out["disk_sector"] = t[:, 0]
+    out["file_id"] = t[:, 1] & 0xFFFFFFFF
+    out["file_sector"] = t[:, 1] >> 32
+    return out
+
+
+class Server:
+    """A serving loop (cv_server): submit images as they arrive, poll their results."""
+
+    def __init__(self, handle: int):
+        self._h = handle
+        self._keep = {}
+
+    def submit(self, image, tag: int = 0) -> int:
+        p, n, k = _buf(image)
+        t = ctypes.c_uint64()
+        _check(load().cv_submit(self._h, cv_buf(p, n), tag, ctypes.byref(t)), "cv_submit")
+        self._keep[int(t.value)] = (image, k)
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """The request's Result, or None if it is not done within timeout_ms."""
+        h = ctypes.c_void_p()
+        rc = load().cv_poll(self._h, ticket, timeout_ms, ctypes.byref(h))
+        if rc == CV_EAGAIN:
+            return None
+        self._keep.pop(ticket, None)
+        _check(rc, "cv_poll")
+        return Result(h.value, 1, False)
+
+    def stats(self) -> dict:
+        st = cv_server_stats()
+        _check(load().cv_server_get_stats(self._h, ctypes.byref(st)), "cv_server_get_stats")
+        return {k: getattr(st, k) for k, _ in cv_server_stats._fields_}
+
+    def close(self) -> None:
+        if self._h:
+            load().cv_free(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def server_create(master: Master, max_live: int = 0, hbm_budget_bytes: int = 0, work_unit_bytes: int = 0,
+                  kernel_config: int = 0, copy_streams: int = 0) -> Server:
+    """cv_server_create: a serving loop over one resident master table."""
+    o = cv_server_opts(ctypes.sizeof(cv_server_opts), max_live, hbm_budget_bytes, work_unit_bytes, kernel_config,
+                       copy_streams)
+    h = ctypes.c_void_p()
+    _check(load().cv_server_create(master.handle, ctypes.byref(o), ctypes.byref(h)), "cv_server_create")
+    return Server(h.value)

@@ -259,6 +259,66 @@ def make_plan(image_seed: int, n_sectors: int, file_nsect, plant_frac: float, ov
     return Plan(image_seed, master_seed, n_sectors, file_nsect, plant_file, plant_fcluster, plant_over)
 
 
+def make_plan_density(image_seed: int, n_sectors: int, file_nsect, density: float, master_seed: int,
+                      overwrite_frac: float = 0.10) -> Plan:
+    """Plant round(density * image clusters) distinct image clusters, each with a master cluster
+    drawn uniformly over every cluster of every master file (repeats allowed), and overwrite the
+    first 1-4 sectors of round(overwrite_frac * planted) of them."""
+    file_nsect = np.asarray(file_nsect, dtype=np.uint32)
+    rng = np.random.default_rng([image_seed, 0xD3])
+    n_clusters = (n_sectors + CLUSTER - 1) // CLUSTER
+    plant_file = np.full(n_clusters, -1, np.int32)
+    plant_fcluster = np.zeros(n_clusters, np.uint32)
+    plant_over = np.zeros(n_clusters, np.uint8)
+    P = int(round(density * n_clusters))
+    if P and file_nsect.size:
+        slots = rng.choice(n_clusters, size=P, replace=False)
+        ncl = (file_nsect.astype(np.int64) + CLUSTER - 1) // CLUSTER
+        cum = np.cumsum(ncl)
+        g = rng.integers(0, int(cum[-1]), size=P)
+        f = np.searchsorted(cum, g, side="right")
+        c = g - (cum[f] - ncl[f])
+        plant_file[slots] = f.astype(np.int32)
+        plant_fcluster[slots] = c.astype(np.uint32)
+        n_over = int(round(overwrite_frac * P))
+        if n_over:
+            which = rng.choice(P, size=n_over, replace=False)
+            plant_over[slots[which]] = rng.integers(1, 5, size=n_over).astype(np.uint8)
+    return Plan(image_seed, master_seed, n_sectors, file_nsect, plant_file, plant_fcluster, plant_over)
+
+
+def master_set(name: str):
+    """(file_nsect, master_seed) of a named master set.
+
+    m8m: 40,000 files with log-uniform 8 KiB-1 MiB sizes scaled to 8,388,608 sectors, seed 4
+         (the shared table of the batched and served workloads)."""
+    if name == "m8m":
+        rng = np.random.default_rng(4)
+        raw = log_uniform_sizes(rng, 40000, 8 << 10, 1 << 20) / SECTOR
+        return scale_to_total(raw, 8388608, 16), 4 + 0x5EED
+    raise KeyError(name)
+
+
+def batch_sizes(seed: int, n: int, lo_bytes: int, hi_bytes: int, total_bytes: int) -> np.ndarray:
+    """Image sizes in sectors: log-uniform lo..hi, scaled to total_bytes, each at least lo_bytes
+    and a whole number of 4 KiB clusters."""
+    rng = np.random.default_rng(seed)
+    raw = log_uniform_sizes(rng, n, lo_bytes, hi_bytes)
+    raw = raw * (total_bytes / raw.sum())
+    clusters = np.maximum(np.round(raw / (CLUSTER * SECTOR)), lo_bytes // (CLUSTER * SECTOR)).astype(np.int64)
+    diff = total_bytes // (CLUSTER * SECTOR) - int(clusters.sum())
+    order = np.argsort(-clusters)
+    i = 0
+    while diff != 0:
+        j = order[i % n]
+        step = 1 if diff > 0 else -1
+        if clusters[j] + step >= lo_bytes // (CLUSTER * SECTOR):
+            clusters[j] += step
+            diff -= step
+        i += 1
+    return clusters * CLUSTER
+
+
 def log_uniform_sizes(rng, n: int, lo_bytes: int, hi_bytes: int) -> np.ndarray:
     return np.exp(rng.uniform(np.log(lo_bytes), np.log(hi_bytes), size=n))
 

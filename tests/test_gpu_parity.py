@@ -224,3 +224,131 @@ def test_keep_on_device(cv):
         got["file_id"] = t[:, 1] & 0xFFFFFFFF
         got["file_sector"] = t[:, 1] >> 32
         assert np.array_equal(got, want)
+
+
+def test_images_sharing_one_allocation(cv):
+    """Images carved out of one device buffer: sector-aligned ones share a tensor map over the
+    whole allocation, a 16-byte-aligned one gets its own; results equal separate scans."""
+    plan = synth.config_plan("small:60000:50:23")
+    files = plan.masters_host()
+    full = plan.image_host()
+    whole = dev(full)
+    cuts = [(0, 7000), (7000, 7003), (7003, 31000), (31000, 31000), (40000, 60000)]
+    images, wants = [], []
+    for a, b in cuts:
+        images.append((whole.data_ptr() + a * SECTOR, (b - a) * SECTOR))
+        wants.append(oracle.match_hash(full[a * SECTOR:b * SECTOR], files))
+    off = 12345 * SECTOR + 16  # 16-byte aligned, not sector-aligned within the allocation
+    images.append((whole.data_ptr() + off, 9000 * SECTOR))
+    wants.append(oracle.match_hash(full[off:off + 9000 * SECTOR], files))
+    with cv.master_build(files) as m, cv.scan(m, images) as r:
+        for k in range(len(images)):
+            assert_same(r.matches(k), wants[k], str(k))
+
+
+def _batch_images(n_images, seed):
+    """Images of uneven sizes carved out of one device buffer, plus their oracle results."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(0, 4000, size=n_images)
+    sizes[3] = 0
+    sizes[5] = 1
+    plan = synth.config_plan(f"small:{int(sizes.sum()) + 64}:60:{seed}")
+    full = plan.image_host()
+    files = plan.masters_host()
+    whole = dev(full)
+    images, wants, a = [], [], 0
+    for n in sizes.tolist():
+        images.append((whole.data_ptr() + a * SECTOR, n * SECTOR))
+        wants.append(oracle.match_hash(full[a * SECTOR:(a + n) * SECTOR], files))
+        a += n
+    return files, whole, images, wants
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batch_graph_equals_oracle_per_image(cv, autotune, tmp_path):
+    files, whole, images, wants = _batch_images(40, 31)
+    with cv.master_build(files) as m:
+        cache = str(tmp_path / "tune.txt") if autotune else None
+        with cv.batch_create(m, images, autotune=autotune, tune_cache=cache) as b:
+            info = b.info()
+            assert info["tensor_maps"] == 1 and info["segments"] == sum(1 for w in images if w[1] >= SECTOR)
+            for run in range(2):  # replays give the same result
+                b.run()
+                total = b.wait()
+                assert total == sum(w.size for w in wants)
+                for k in range(len(images)):
+                    assert_same(cv.device_matches_to_numpy(b.matches(k)), wants[k], f"run {run} image {k}")
+        if autotune:
+            assert open(cache).read().strip()
+            with cv.batch_create(m, images, autotune=True, tune_cache=cache) as b2:
+                assert b2.info()["tuned"] == 0  # served from the cache
+
+
+def test_batch_capacity_overflow_reported(cv):
+    files, whole, images, wants = _batch_images(12, 33)
+    total = sum(w.size for w in wants)
+    assert total > 10
+    with cv.master_build(files) as m, cv.batch_create(m, images, match_capacity=10) as b:
+        b.run()
+        with pytest.raises(cv.CVError) as e:
+            b.wait()
+        assert e.value.code == cv.CV_ERANGE
+
+
+def test_server_results_equal_solo_scans(cv):
+    """Requests of mixed sizes arriving together: each result equals the oracle and the solo
+    scan of the same image, while work units of many requests share launches."""
+    plan = synth.config_plan("small:120000:80:51")
+    files = plan.masters_host()
+    full = plan.image_host()
+    rng = np.random.default_rng(9)
+    cuts = []
+    for k in range(30):
+        n = int(rng.integers(1, 40)) if k % 5 else int(rng.integers(3000, 20000))
+        a = int(rng.integers(0, 120000 - n))
+        cuts.append((a, n))
+    cuts.append((0, 0))
+    pinned = torch.from_numpy(full).pin_memory()
+    with cv.master_build(files) as m:
+        # work units of 1 MiB and a 6 MiB budget force units of big requests to take turns
+        with cv.server_create(m, work_unit_bytes=1 << 20, hbm_budget_bytes=6 << 20, max_live=8) as srv:
+            tickets = []
+            for k, (a, n) in enumerate(cuts):
+                img = pinned[a * SECTOR:(a + n) * SECTOR] if k % 2 else np.ascontiguousarray(
+                    full[a * SECTOR:(a + n) * SECTOR])
+                tickets.append(srv.submit(img, tag=k))
+            dimg = dev(full[5000 * SECTOR:9000 * SECTOR])
+            tdev = srv.submit(dimg, tag=99)
+            for k, t in enumerate(tickets):
+                r = srv.poll(t, timeout_ms=60000)
+                assert r is not None
+                a, n = cuts[k]
+                want = oracle.match_hash(full[a * SECTOR:(a + n) * SECTOR], files)
+                assert_same(r.matches(0), want, f"request {k}")
+                r.close()
+            r = srv.poll(tdev, timeout_ms=60000)
+            assert_same(r.matches(0), oracle.match_hash(full[5000 * SECTOR:9000 * SECTOR], files), "device request")
+            r.close()
+            st = srv.stats()
+            assert st["completed"] == len(cuts) + 1 and st["failed"] == 0
+            assert st["peak_bytes_in_flight"] <= 6 << 20
+            assert st["p99_ms"] >= st["p50_ms"] > 0
+        # the solo scan of one of the big requests gives the same list
+        a, n = cuts[0]
+        with cv.scan(m, [np.ascontiguousarray(full[a * SECTOR:(a + n) * SECTOR])]) as r:
+            assert_same(r.matches(0), oracle.match_hash(full[a * SECTOR:(a + n) * SECTOR], files), "solo")
+
+
+def test_server_poll_nonblocking_and_unknown_ticket(cv):
+    files = [synth.random_sectors(3, 64)]
+    with cv.master_build(files) as m, cv.server_create(m) as srv:
+        with pytest.raises(cv.CVError):
+            srv.poll(12345, timeout_ms=0)
+        t = srv.submit(np.ascontiguousarray(files[0]))
+        r = None
+        for _ in range(2000):
+            r = srv.poll(t, timeout_ms=10)
+            if r is not None:
+                break
+        assert r is not None and r.count(0) == 64
+        r.close()
