@@ -452,6 +452,11 @@ def main():
         e2e = {"value": world * nbytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
 
+    ip = cv.int_peak()
+    int_peak = {k: ip[k] / 1e12 for k in ("alu_ops_per_s", "fma_ops_per_s", "mixed_ops_per_s")}
+    int_peak.update({"unit": "Top/s", "sm_clock_mhz": ip["sm_clock_mhz"],
+                     "mixed_ops_per_clk_per_sm": ip["mixed_ops_per_s"] / (ip["sms"] * ip["sm_clock_mhz"] * 1e6),
+                     "how": "cv_int_peak: independent lop3 / mad.lo chains, 8 blocks of 256 threads per SM"})
     kms = statistics.mean(kernel_ms)
     sectors = plan.n_sectors
     achieved_ops = sectors * MD5_OPS_PER_SECTOR / (kms * 1e-3)
@@ -479,7 +484,7 @@ def main():
                                   f"{MD5_OPS_PER_SECTOR} algorithmic ops per sector",
                      "hash_hbm_roofline_GBps": roof_gbs,
                      "frac_of_hash_hbm_roofline": (nbytes / (kms * 1e-3) / 1e9) / roof_gbs,
-                     "hbm_peak_GBps_measured": hbm},
+                     "hbm_peak_GBps_measured": hbm, "int_peak_measured": int_peak},
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": launches,

@@ -167,6 +167,25 @@ int cv_last_cuda_error(void);
  */
 int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t* trivial, void* stream);
 
+/* Integer throughput of this GPU: independent lop3 chains (ALU pipe), mad.lo chains (FMA pipe)
+ * and the two interleaved, in operations per second, with the SM clock seen during the run.
+ * The paper has no counterpart; it is the denominator of the scan's roofline. */
+typedef struct {
+  double alu_ops_per_s;
+  double fma_ops_per_s;
+  double mixed_ops_per_s;
+  double sm_clock_mhz;
+  int sms;
+  int reserved;
+} cv_int_peak_info;
+int cv_int_peak(cv_int_peak_info* info);
+
+/* Failure-path self-test: a kernel waits on a barrier that nothing completes, using the same
+ * bounded wait as the scan kernel with a limit of timeout_us microseconds (1..10^7); the wait
+ * gives up, sets the device status word and the kernel returns. Expected result: CV_ETIMEOUT,
+ * with the device still usable afterwards. The paper has no counterpart. */
+int cv_selftest_wait_timeout(uint32_t timeout_us, void* stream);
+
 /*
  * Batched scans (a CUDA graph over many device images). The paper scans several drives at once
  * by multiplexing them onto one GPU (Section 3); a batch makes all of its images one work list

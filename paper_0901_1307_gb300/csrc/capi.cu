@@ -80,6 +80,23 @@ const char* cv_strerror(int code) {
 
 int cv_last_cuda_error(void) { return last_cuda(); }
 
+int cv_selftest_wait_timeout(uint32_t timeout_us, void* stream_) {
+  if (timeout_us == 0 || timeout_us > 10000000u) return CV_EINVAL;
+  DevCtx* ctx;
+  CV_TRY(get_ctx(&ctx));
+  cudaStream_t stream = (cudaStream_t)stream_;
+  Temps tmp(ctx, stream);
+  uint32_t* status;
+  CV_TRY(tmp.alloc(&status, 4));
+  CV_CUDA(cudaMemsetAsync(status, 0, 4, stream));
+  CV_CUDA((cudaError_t)launch_wait_selftest(status, (uint64_t)timeout_us * 1000u, stream));
+  uint32_t st = 0;
+  CV_CUDA(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, stream));
+  CV_CUDA(cudaStreamSynchronize(stream));
+  if (st & kStTimeout) return CV_ETIMEOUT;
+  return st ? CV_ECORRUPT : CV_OK;
+}
+
 int cv_kernel_config_count(void) {
   int n;
   scan_configs(&n);

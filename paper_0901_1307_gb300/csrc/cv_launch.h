@@ -31,4 +31,8 @@ int launch_tile_offsets(const uint64_t* tile_ntrip, uint64_t n_tiles, uint64_t* 
                         uint32_t n_segs, uint32_t scale, uint64_t* seg_off, uint64_t* total, uint64_t* scratch,
                         void* stream);
 
+// One block whose single waiting thread waits on an mbarrier nothing completes (bounded by
+// timeout_ns): the status word gets the timeout bit. Returns a CUDA error code.
+int launch_wait_selftest(uint32_t* status, uint64_t timeout_ns, void* stream);
+
 }  // namespace cvk

@@ -6,34 +6,39 @@
 
 namespace cvk {
 
-#define CV_SCAN_CFG(T, SPT, NS, B, P)                                                                      \
+#define CV_SCAN_CFG(T, SPT, NS, B, P, MB)                                                                  \
   ScanCfg {                                                                                                \
     "t" #T "_x" #SPT "_s" #NS "_b" #B "_p" #P, T, SPT, T / SPT + 32, NS, B,                                 \
-        (const void*)scan_kernel<T, SPT, NS, B, kModeScan, P>,                                            \
-        (const void*)scan_kernel<T, SPT, NS, B, kModeDigest, P>, (const void*)expand_kernel<T>,            \
+        (const void*)scan_kernel<T, SPT, NS, B, kModeScan, P, MB>,                                        \
+        (const void*)scan_kernel<T, SPT, NS, B, kModeDigest, P, MB>, (const void*)expand_kernel<T>,        \
         ScanSmem<T, NS, B>::kAlloc                                                                         \
   }
 
 // The first entry is the default configuration (the fastest measured on GB300 for the 32 GiB
 // image workload); the others stay selectable and are what the batch autotuner tries.
 static const ScanCfg kConfigs[] = {
-    CV_SCAN_CFG(256, 1, 2, 64, 3),
-    CV_SCAN_CFG(256, 1, 2, 64, 0),
-    CV_SCAN_CFG(256, 1, 2, 64, 1),
-    CV_SCAN_CFG(256, 1, 2, 64, 2),
-    CV_SCAN_CFG(256, 2, 2, 64, 3),
-    CV_SCAN_CFG(256, 2, 2, 64, 0),
-    CV_SCAN_CFG(256, 2, 3, 64, 3),
-    CV_SCAN_CFG(256, 2, 2, 128, 3),
-    CV_SCAN_CFG(128, 2, 4, 64, 3),
-    CV_SCAN_CFG(256, 1, 3, 64, 3),
-    CV_SCAN_CFG(128, 1, 2, 128, 2),
-    CV_SCAN_CFG(128, 1, 4, 64, 0),
+    CV_SCAN_CFG(256, 1, 2, 64, 3, 0),
+    CV_SCAN_CFG(480, 1, 2, 64, 3, 3),
+    CV_SCAN_CFG(352, 1, 2, 64, 3, 4),
+    CV_SCAN_CFG(224, 1, 2, 64, 3, 6),
+    CV_SCAN_CFG(480, 1, 3, 64, 3, 3),
+    CV_SCAN_CFG(256, 1, 2, 64, 0, 0),
+    CV_SCAN_CFG(256, 1, 2, 64, 2, 0),
+    CV_SCAN_CFG(256, 2, 2, 64, 3, 0),
+    CV_SCAN_CFG(256, 2, 2, 128, 3, 0),
+    CV_SCAN_CFG(256, 1, 3, 64, 3, 0),
+    CV_SCAN_CFG(128, 1, 2, 128, 2, 0),
+    CV_SCAN_CFG(128, 1, 4, 64, 0, 0),
 };
 
 const ScanCfg* scan_configs(int* n) {
   *n = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
   return kConfigs;
+}
+
+int launch_wait_selftest(uint32_t* status, uint64_t timeout_ns, void* stream) {
+  wait_timeout_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(status, timeout_ns);
+  return (int)cudaGetLastError();
 }
 
 uint64_t tile_offsets_scratch_words(uint64_t n_tiles) { return (n_tiles + kOffChunk - 1) / kOffChunk + 1; }

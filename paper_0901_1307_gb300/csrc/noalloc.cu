@@ -39,7 +39,7 @@ namespace {
 
 // Scratch layout (offsets in bytes); sized for CV_NOALLOC_MAX_SECTORS with the smallest tile.
 constexpr uint64_t kMaxSectors = CV_NOALLOC_MAX_SECTORS;
-constexpr uint64_t kMaxTiles = kMaxSectors / 32 + 8;  // output tiles of 32 sectors, plus a ragged tile
+constexpr uint64_t kMaxTiles = kMaxSectors / 32 + 32;  // output tiles of 32 sectors, plus a ragged tile
 constexpr uint64_t kOffSeg = 128;                               // Segment
 constexpr uint64_t kOffCounters = 256;                          // seg_off[1], total, status
 constexpr uint64_t kOffSums = 512;                              // chunk sums of the offset pass
@@ -47,7 +47,7 @@ constexpr uint64_t kOffNhit = kOffSums + 1024;                  // u32 per tile
 constexpr uint64_t kOffNtrip = kOffNhit + ((kMaxTiles * 4 + 255) / 256) * 256;   // u64 per tile
 constexpr uint64_t kOffToff = kOffNtrip + ((kMaxTiles * 8 + 255) / 256) * 256;   // u64 per tile
 constexpr uint64_t kOffHits = kOffToff + ((kMaxTiles * 8 + 255) / 256) * 256;    // uint4 per sector slot
-constexpr uint64_t kHitSlots = kMaxSectors + 256;
+constexpr uint64_t kHitSlots = kMaxTiles * 32;
 constexpr uint64_t kNoAllocScratchBytes = kOffHits + kHitSlots * 16;
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoAllocScratchBytes];
@@ -142,7 +142,7 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   CUtensorMap& map = p.maps[0];
   cuuint64_t dims[2] = {128, (cuuint64_t)S};
   cuuint64_t strides[1] = {CV_SECTOR_BYTES};
-  cuuint32_t box[2] = {(cuuint32_t)(cfg.BOXB / 4), (cuuint32_t)cfg.T};
+  cuuint32_t box[2] = {(cuuint32_t)(cfg.BOXB / 4), (cuuint32_t)(cfg.T / ((cfg.T + 255) / 256))};
   cuuint32_t es[2] = {1, 1};
   CUresult cr = d->encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(image), dims, strides, box, es,
                           CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -158,6 +158,7 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   seg.map = 0;
   const uint64_t n_tiles = (S + cfg.T - 1) / cfg.T;
   const uint64_t n_out_tiles = n_tiles * (uint64_t)(cfg.T / 32);  // output tiles of 32 sectors
+  if (n_out_tiles > kMaxTiles) return CV_EINVAL;                   // tile wider than the layout allows
 
   cudaError_t e;
   if ((e = cudaMemsetAsync(status_d, 0, 4, stream)) != cudaSuccess) return fail(e);

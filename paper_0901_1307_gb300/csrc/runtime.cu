@@ -128,7 +128,7 @@ int classify(DevCtx* ctx, const void* p, BufKind* kind) {
 int make_tmap(DevCtx* ctx, const ScanCfg& cfg, const void* base, uint64_t n_rows, CUtensorMap* out) {
   cuuint64_t dims[2] = {128, (cuuint64_t)n_rows};
   cuuint64_t strides[1] = {kSector};
-  cuuint32_t box[2] = {(cuuint32_t)(cfg.BOXB / 4), (cuuint32_t)cfg.T};
+  cuuint32_t box[2] = {(cuuint32_t)(cfg.BOXB / 4), (cuuint32_t)(cfg.T / ((cfg.T + 255) / 256))};
   cuuint32_t es[2] = {1, 1};
   CUtensorMapSwizzle sw = cfg.BOXB == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   CUresult r = ctx->encode(out, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(base), dims, strides, box, es,

@@ -61,13 +61,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 
 // Wait for the phase with the given parity to complete; false on timeout or abort.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile uint32_t* abort_flag,
-                                          uint32_t* status) {
+                                          uint32_t* status, uint64_t timeout_ns = kWaitTimeoutNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
+    if (globaltimer_ns() - t0 > timeout_ns) {
       *abort_flag = 1u;
       atomicOr(status, kStTimeout);
       return false;
@@ -140,13 +140,17 @@ struct ScanSmem {
 
 // T: sectors per tile; SPT: sectors per hashing thread (1 or 2; the block has C = T / SPT
 // hashing threads plus one producer warp); NS: ring stages; BOXB: bytes of each sector row per
-// stage (64 or 128); PIPE: which MD5 additions use the FMA pipe (see md5_fma_adds).
+// stage (64 or 128); PIPE: which MD5 additions use the FMA pipe (see md5_fma_adds); MINB: the
+// blocks per SM the register allocation must allow (0: no constraint).
 // Thread t hashes rows t, t + C, ... of the tile. Matches are compacted per warp and row group:
 // rows [32v, 32v + 32) of tile k form output tile k * (T / 32) + v.
-template <int T, int SPT, int NS, int BOXB, int MODE, int PIPE>
-__global__ void __launch_bounds__(T / SPT + 32) scan_kernel(const __grid_constant__ ScanParams p) {
+template <int T, int SPT, int NS, int BOXB, int MODE, int PIPE, int MINB>
+__global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_constant__ ScanParams p) {
   constexpr int C = T / SPT;
-  static_assert(T % 32 == 0 && T <= 256 && C % 32 == 0, "tile rows");
+  // A tile larger than the 256-row TMA box limit is loaded as several boxes per stage.
+  constexpr int kBoxes = (T + 255) / 256;
+  constexpr int kBoxRows = T / kBoxes;
+  static_assert(T % 32 == 0 && T <= 1024 && C % 32 == 0 && T % kBoxes == 0 && kBoxRows % 8 == 0, "tile rows");
   static_assert(SPT == 1 || SPT == 2, "sectors per thread");
   static_assert(BOXB == 64 || BOXB == 128, "box width");
   using L = ScanSmem<T, NS, BOXB>;
@@ -195,7 +199,10 @@ __global__ void __launch_bounds__(T / SPT + 32) scan_kernel(const __grid_constan
           break;
         }
         mbar_arrive_expect_tx(bar_full + 8 * s, L::kStageBytes);
-        tma_load_2d(base + s * L::kStageBytes, map, c * (BOXB / 4), row0, bar_full + 8 * s, policy);
+#pragma unroll
+        for (int k = 0; k < kBoxes; k++)
+          tma_load_2d(base + s * L::kStageBytes + k * kBoxRows * BOXB, map, c * (BOXB / 4), row0 + k * kBoxRows,
+                      bar_full + 8 * s, policy);
       }
     }
     // Wait (bounded) for the copies still in flight so none lands after the block exits.
@@ -307,6 +314,20 @@ __global__ void __launch_bounds__(T / SPT + 32) scan_kernel(const __grid_constan
         }
       }
     }
+  }
+}
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing completes. The
+// wait gives up after timeout_ns, sets kStTimeout and the kernel returns normally.
+__global__ void wait_timeout_selftest_kernel(uint32_t* status, uint64_t timeout_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t abort_flag;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mbar_init(smem_addr(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const bool ok = mbar_wait(smem_addr(&bar), 0, &abort_flag, status, timeout_ns);
+    if (ok) atomicOr(status, kStProbeBound);  // must not happen: nothing arrives
   }
 }
 

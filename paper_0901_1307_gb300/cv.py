@@ -36,7 +36,7 @@ EXPORTS = ("cv_master_build", "cv_master_get_info", "cv_scan", "cv_matches", "cv
            "cv_strerror", "cv_last_cuda_error", "cv_sector_digests", "cv_kernel_config_count",
            "cv_kernel_config_name", "cv_scan_noalloc", "cv_batch_create", "cv_batch_run", "cv_batch_wait",
            "cv_batch_matches", "cv_batch_get_info", "cv_server_create", "cv_submit", "cv_poll",
-           "cv_server_get_stats")
+           "cv_server_get_stats", "cv_int_peak", "cv_selftest_wait_timeout")
 CV_EAGAIN = -9
 CV_BATCH_BLOOM_AUTO = 0
 CV_BATCH_BLOOM_OFF = 1
@@ -103,6 +103,12 @@ class cv_server_stats(ctypes.Structure):
                 ("max_ms", ctypes.c_double), ("wall_s", ctypes.c_double)]
 
 
+class cv_int_peak_info(ctypes.Structure):
+    _fields_ = [("alu_ops_per_s", ctypes.c_double), ("fma_ops_per_s", ctypes.c_double),
+                ("mixed_ops_per_s", ctypes.c_double), ("sm_clock_mhz", ctypes.c_double), ("sms", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -160,6 +166,10 @@ def load(path: str = LIB_PATH):
         lib.cv_poll.restype = i32
         lib.cv_server_get_stats.argtypes = [vp, ctypes.POINTER(cv_server_stats)]
         lib.cv_server_get_stats.restype = i32
+        lib.cv_int_peak.argtypes = [ctypes.POINTER(cv_int_peak_info)]
+        lib.cv_int_peak.restype = i32
+        lib.cv_selftest_wait_timeout.argtypes = [u32, vp]
+        lib.cv_selftest_wait_timeout.restype = i32
         _lib = lib
         return lib
 
@@ -484,3 +494,15 @@ def server_create(master: Master, max_live: int = 0, hbm_budget_bytes: int = 0, 
     h = ctypes.c_void_p()
     _check(load().cv_server_create(master.handle, ctypes.byref(o), ctypes.byref(h)), "cv_server_create")
     return Server(h.value)
+
+
+def int_peak() -> dict:
+    """cv_int_peak: measured integer operation rates of this GPU."""
+    inf = cv_int_peak_info()
+    _check(load().cv_int_peak(ctypes.byref(inf)), "cv_int_peak")
+    return {k: getattr(inf, k) for k, _ in cv_int_peak_info._fields_ if k != "reserved"}
+
+
+def selftest_wait_timeout(timeout_us: int, stream=None) -> int:
+    """cv_selftest_wait_timeout: return code of a bounded wait that runs out (CV_ETIMEOUT)."""
+    return int(load().cv_selftest_wait_timeout(timeout_us, _stream(stream)))
