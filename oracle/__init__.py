@@ -17,6 +17,8 @@ Functions and the passages they follow:
   file_sector), sorted.
 * ``match_hash(image, files)`` / ``OracleDB`` -- the method's route (Section 3.1): signatures of the
   kept master sectors, each disk sector's signature looked up, equal signatures reported, sorted.
+* ``match_sig(image, files, sig)`` -- the same with another signature: MD5 without padding, djb2-64
+  (Eq. 1) or CRC64 (Section 2.1); candidates of the 64-bit ones are confirmed byte for byte.
 
 Parity pins (tests/test_oracle.py): MD5 against hashlib (OpenSSL) and md5sum; ``match_hash``
 against ``match_brute`` on tiny inputs with duplicates, fills and partial sectors; both against
@@ -77,6 +79,20 @@ def bind(lib):
     lib.oracle_db_free.restype = None
     lib.oracle_db_lookup.argtypes = [vp, vp, u64, u64, vp, u64]
     lib.oracle_db_lookup.restype = ctypes.c_int64
+    lib.oracle_md5_nopad.argtypes = [vp, vp]
+    lib.oracle_md5_nopad.restype = None
+    lib.oracle_md5_finish_sector.argtypes = [vp, vp]
+    lib.oracle_md5_finish_sector.restype = None
+    lib.oracle_djb2_64.argtypes = [vp, u64]
+    lib.oracle_djb2_64.restype = u64
+    lib.oracle_crc64.argtypes = [vp, u64]
+    lib.oracle_crc64.restype = u64
+    lib.oracle_signature.argtypes = [vp, ctypes.c_int, vp]
+    lib.oracle_signature.restype = None
+    lib.oracle_match_sig.argtypes = [vp, u64, vp, vp, u32, ctypes.c_int, vp, u64]
+    lib.oracle_match_sig.restype = ctypes.c_int64
+    lib.oracle_db_build_sig.argtypes = [vp, vp, u32, ctypes.c_int]
+    lib.oracle_db_build_sig.restype = vp
     lib.oracle_threads.argtypes = []
     lib.oracle_threads.restype = ctypes.c_int
     lib.oracle_set_threads.argtypes = [ctypes.c_int]
@@ -168,6 +184,49 @@ def match_brute(image, files) -> np.ndarray:
     return _run_match(_load().oracle_match_brute, image, files)
 
 
+SIG_MD5, SIG_MD5_NOPAD, SIG_DJB2_64, SIG_CRC64 = 0, 1, 2, 3
+
+
+def md5_nopad(sector) -> bytes:
+    """MD5 state after the 8 data blocks of a 512-byte sector (no padding block)."""
+    a = _u8(sector)
+    assert a.size == SECTOR
+    out = np.zeros(16, np.uint8)
+    _load().oracle_md5_nopad(_ptr(a), out.ctypes.data)
+    return out.tobytes()
+
+
+def md5_finish_sector(state: bytes) -> bytes:
+    a = _u8(state)
+    out = np.zeros(16, np.uint8)
+    _load().oracle_md5_finish_sector(_ptr(a), out.ctypes.data)
+    return out.tobytes()
+
+
+def djb2_64(data) -> int:
+    a = _u8(data)
+    return int(_load().oracle_djb2_64(_ptr(a), a.size))
+
+
+def crc64(data) -> int:
+    a = _u8(data)
+    return int(_load().oracle_crc64(_ptr(a), a.size))
+
+
+def signature(sector, sig: int) -> bytes:
+    a = _u8(sector)
+    assert a.size == SECTOR
+    out = np.zeros(16, np.uint8)
+    _load().oracle_signature(_ptr(a), sig, out.ctypes.data)
+    return out.tobytes()
+
+
+def match_sig(image, files, sig: int) -> np.ndarray:
+    """The method with a chosen signature (64-bit ones confirmed byte for byte)."""
+    lib = _load()
+    return _run_match(lambda *a: lib.oracle_match_sig(*a[:5], sig, *a[5:]), image, files)
+
+
 def match_hash(image, files) -> np.ndarray:
     """The same result reached through MD5 signatures and a sorted signature database."""
     return _run_match(_load().oracle_match_hash, image, files)
@@ -176,10 +235,11 @@ def match_hash(image, files) -> np.ndarray:
 class OracleDB:
     """The signature database of a master set, for looking up any subset of disk sectors."""
 
-    def __init__(self, files):
+    def __init__(self, files, sig: int = 0):
         fl = _Files(files)
+        self._files = fl  # borrowed by the database
         lib = _load()
-        self._h = lib.oracle_db_build(fl.ptrs, fl.sizes, fl.n)
+        self._h = lib.oracle_db_build_sig(fl.ptrs, fl.sizes, fl.n, sig)
         if not self._h:
             raise MemoryError("oracle: database allocation failed")
 

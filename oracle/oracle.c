@@ -27,6 +27,12 @@
  *                         binary search as an alternative to its hash tables); the table
  *                         layout does not change the result.
  *
+ * Other signatures (Section 2): MD5 without the padding block (Section 2.1 notes it adds nothing
+ * for fixed-size sectors), djb2 with a 64-bit accumulator (Eq. 1) and CRC64 with the generator
+ * x^64 + x^4 + x^3 + x + 1 (Section 2.1). With a 64-bit signature, equal signatures are only
+ * candidates: oracle_match_sig confirms each one byte for byte (Section 3.1), so every
+ * signature yields the same result as oracle_match_brute.
+ *
  * MD5 (oracle_md5) follows the prose of RFC 1321 Section 3: pad with one 1-bit then zeros to
  * 448 mod 512 bits, append the 64-bit little-endian bit length, then for every 512-bit block
  * run four rounds of sixteen operations a = b + ((a + F(b,c,d) + X[k] + T[i]) <<< s), where
@@ -129,6 +135,89 @@ void oracle_md5_sectors(const uint8_t* data, uint64_t n_sectors, uint8_t* out) {
   for (int64_t i = 0; i < (int64_t)n_sectors; i++) oracle_md5(data + (uint64_t)i * SECTOR, SECTOR, out + 16 * i);
 }
 
+/* ----------------------------------------------------- other sector signatures (Section 2) */
+
+/* The MD5 state (A, B, C, D) after the 8 data blocks of a 512-byte message, without the
+ * padding block (Section 2.1: for fixed 4096-bit sectors the padding block depends on nothing
+ * but the length). 16 bytes, same byte order as an MD5 digest. */
+void oracle_md5_nopad(const uint8_t* sector, uint8_t out[16]) {
+  md5_init_table();
+  uint32_t st[4] = {0x67452301u, 0xefcdab89u, 0x98badcfeu, 0x10325476u};
+  for (int b = 0; b < 8; b++) md5_block(st, sector + 64 * b);
+  for (int j = 0; j < 4; j++)
+    for (int q = 0; q < 4; q++) out[4 * j + q] = (uint8_t)(st[j] >> (8 * q));
+}
+
+/* Finish a 512-byte message's MD5 from the state oracle_md5_nopad returned: one more block
+ * holding the RFC padding for a 4096-bit message. */
+void oracle_md5_finish_sector(const uint8_t state[16], uint8_t out[16]) {
+  md5_init_table();
+  uint32_t st[4];
+  for (int j = 0; j < 4; j++)
+    st[j] = (uint32_t)state[4 * j] | ((uint32_t)state[4 * j + 1] << 8) | ((uint32_t)state[4 * j + 2] << 16) |
+            ((uint32_t)state[4 * j + 3] << 24);
+  uint8_t pad[64];
+  memset(pad, 0, sizeof pad);
+  pad[0] = 0x80;
+  const uint64_t bits = 512u * 8u;
+  for (int j = 0; j < 8; j++) pad[56 + j] = (uint8_t)(bits >> (8 * j));
+  md5_block(st, pad);
+  for (int j = 0; j < 4; j++)
+    for (int q = 0; q < 4; q++) out[4 * j + q] = (uint8_t)(st[j] >> (8 * q));
+}
+
+/* djb2 with a 64-bit accumulator (Eq. 1, Section 4): h = 5381, then h = h * 33 + s_i for
+ * every byte s_i, modulo 2^64. */
+uint64_t oracle_djb2_64(const uint8_t* msg, uint64_t len) {
+  uint64_t h = 5381u;
+  for (uint64_t i = 0; i < len; i++) h = h * 33u + msg[i];
+  return h;
+}
+
+/* CRC64 with the generator polynomial x^64 + x^4 + x^3 + x + 1 (Section 2.1): the remainder
+ * of M(x) * x^64 divided by the generator in modulo-2 arithmetic, where M(x) takes the
+ * message's bits most significant bit of the first byte first. No initial value and no final
+ * XOR (the paper defines the CRC as that remainder). Bit-serial long division. */
+uint64_t oracle_crc64(const uint8_t* msg, uint64_t len) {
+  const uint64_t low = 0x1Bu; /* x^4 + x^3 + x + 1; the x^64 term is the bit shifted out */
+  uint64_t rem = 0;
+  for (uint64_t i = 0; i < len; i++) {
+    for (int b = 7; b >= 0; b--) {
+      const uint64_t in = (msg[i] >> b) & 1u;
+      const uint64_t top = rem >> 63;
+      rem = (rem << 1) | in;
+      if (top) rem ^= low;
+    }
+  }
+  /* the x^64 factor: shift 64 zero bits through */
+  for (int b = 0; b < 64; b++) {
+    const uint64_t top = rem >> 63;
+    rem <<= 1;
+    if (top) rem ^= low;
+  }
+  return rem;
+}
+
+/* Signature kinds shared with the library's options. */
+#define SIG_MD5 0
+#define SIG_MD5_NOPAD 1
+#define SIG_DJB2_64 2
+#define SIG_CRC64 3
+
+/* The 16-byte signature of one 512-byte sector; 64-bit signatures are stored little-endian in
+ * the first 8 bytes, the rest zero. */
+void oracle_signature(const uint8_t* sector, int sig, uint8_t out[16]) {
+  memset(out, 0, 16);
+  if (sig == SIG_MD5) {
+    oracle_md5(sector, SECTOR, out);
+  } else if (sig == SIG_MD5_NOPAD) {
+    oracle_md5_nopad(sector, out);
+  } else {
+    const uint64_t h = sig == SIG_DJB2_64 ? oracle_djb2_64(sector, SECTOR) : oracle_crc64(sector, SECTOR);
+    for (int j = 0; j < 8; j++) out[j] = (uint8_t)(h >> (8 * j));
+  }
+}
+
 /* ------------------------------------------------------------------ the exclusion rule */
 
 /* A master sector is excluded iff all 512 of its bytes are equal. */
@@ -189,6 +278,8 @@ typedef struct {
 typedef struct {
   db_entry* e;
   uint64_t n;
+  int sig;                     /* signature kind */
+  const uint8_t* const* files; /* borrowed; used to confirm matches of 64-bit signatures */
 } oracle_db;
 
 static int db_cmp(const void* pa, const void* pb) {
@@ -201,8 +292,9 @@ static int db_cmp(const void* pa, const void* pb) {
   return 0;
 }
 
-/* The signature database: one (MD5, f, s) entry per kept master sector, sorted. */
-oracle_db* oracle_db_build(const uint8_t* const* files, const uint64_t* file_bytes, uint32_t n_files) {
+/* The signature database: one (signature, f, s) entry per kept master sector, sorted. The
+ * files stay borrowed by the database (64-bit signatures are confirmed against their bytes). */
+oracle_db* oracle_db_build_sig(const uint8_t* const* files, const uint64_t* file_bytes, uint32_t n_files, int sig) {
   md5_init_table();
   uint64_t total = 0;
   for (uint32_t f = 0; f < n_files; f++) total += file_bytes[f] / SECTOR;
@@ -227,10 +319,17 @@ oracle_db* oracle_db_build(const uint8_t* const* files, const uint64_t* file_byt
   /* hash in parallel; every entry is independent */
 #pragma omp parallel for schedule(static)
   for (int64_t q = 0; q < (int64_t)n; q++)
-    oracle_md5(files[db->e[q].file_id] + (uint64_t)db->e[q].file_sector * SECTOR, SECTOR, db->e[q].digest);
+    oracle_signature(files[db->e[q].file_id] + (uint64_t)db->e[q].file_sector * SECTOR, sig, db->e[q].digest);
   qsort(db->e, (size_t)n, sizeof(db_entry), db_cmp);
   db->n = n;
+  db->sig = sig;
+  db->files = files;
   return db;
+}
+
+/* The MD5 database. */
+oracle_db* oracle_db_build(const uint8_t* const* files, const uint64_t* file_bytes, uint32_t n_files) {
+  return oracle_db_build_sig(files, file_bytes, n_files, SIG_MD5);
 }
 
 uint64_t oracle_db_size(const oracle_db* db) { return db->n; }
@@ -268,15 +367,21 @@ int64_t oracle_db_lookup(const oracle_db* db, const uint8_t* sectors, uint64_t n
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < (int64_t)n_sectors; i++) {
     uint8_t dg[16];
-    oracle_md5(sectors + (uint64_t)i * SECTOR, SECTOR, dg);
+    oracle_signature(sectors + (uint64_t)i * SECTOR, db->sig, dg);
     uint64_t a = db_lower_bound(db, dg), b = a;
     while (b < db->n && memcmp(db->e[b].digest, dg, 16) == 0) b++;
     lo[i] = a;
     cnt[i] = b - a;
   }
+  /* 64-bit signatures collide: confirm every candidate byte for byte (Section 3.1) */
+  const int confirm = db->sig == SIG_DJB2_64 || db->sig == SIG_CRC64;
   uint64_t n = 0;
   for (uint64_t i = 0; i < n_sectors; i++)
     for (uint64_t q = 0; q < cnt[i]; q++) {
+      const db_entry* e = &db->e[lo[i] + q];
+      if (confirm && memcmp(sectors + i * SECTOR, db->files[e->file_id] + (uint64_t)e->file_sector * SECTOR,
+                            SECTOR) != 0)
+        continue;
       if (n < cap) {
         out[n].disk_sector = first_index + i;
         out[n].file_id = db->e[lo[i] + q].file_id;
@@ -288,6 +393,17 @@ int64_t oracle_db_lookup(const oracle_db* db, const uint8_t* sectors, uint64_t n
   free(cnt);
   if (n <= cap) qsort(out, (size_t)n, sizeof(oracle_triple), triple_cmp);
   return (int64_t)n;
+}
+
+/* The whole method over one image with a chosen signature: database, lookup of every whole
+ * sector (confirmed for 64-bit signatures), sorted result. */
+int64_t oracle_match_sig(const uint8_t* image, uint64_t image_bytes, const uint8_t* const* files,
+                         const uint64_t* file_bytes, uint32_t n_files, int sig, oracle_triple* out, uint64_t cap) {
+  oracle_db* db = oracle_db_build_sig(files, file_bytes, n_files, sig);
+  if (!db) return -1;
+  int64_t n = oracle_db_lookup(db, image, image_bytes / SECTOR, 0, out, cap);
+  oracle_db_free(db);
+  return n;
 }
 
 /* The whole method over one image: database, lookup of every whole sector, sorted result. */

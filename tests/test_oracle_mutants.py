@@ -31,7 +31,7 @@ MUTANTS = {
     "register roles": ("c = b;\n    b = t;", "c = t;\n    b = b;"),
     "big-endian words": ("(uint32_t)blk[4 * j] | ((uint32_t)blk[4 * j + 1] << 8)",
                          "(uint32_t)blk[4 * j + 1] | ((uint32_t)blk[4 * j] << 8)"),
-    "initial state": ("0x98badcfeu", "0x98badcffu"),
+    "initial state": ("0x10325476u}; /* Section 3.3 */", "0x10325477u}; /* Section 3.3 */"),
     "trivial rule only zero": ("if (sector[j] != sector[0]) return 0;", "if (sector[j] != 0) return 0;"),
     "trivial rule off": ("for (uint32_t j = 1; j < SECTOR; j++)\n    if (sector[j] != sector[0]) return 0;\n  return 1;",
                          "return 0;"),
@@ -42,6 +42,16 @@ MUTANTS = {
     "window offset dropped": ("out[n].disk_sector = first_index + i;", "out[n].disk_sector = i;"),
     "last master sector dropped": ("uint64_t n_fs = file_bytes[f] / SECTOR;\n    for (uint64_t s = 0; s < n_fs; s++) {\n      const uint8_t* m = files[f] + s * SECTOR;\n      if (oracle_sector_trivial(m)) continue;\n      db",
                                    "uint64_t n_fs = file_bytes[f] / SECTOR;\n    if (n_fs) n_fs--;\n    for (uint64_t s = 0; s < n_fs; s++) {\n      const uint8_t* m = files[f] + s * SECTOR;\n      if (oracle_sector_trivial(m)) continue;\n      db"),
+    "djb2 multiplier": ("h = h * 33u + msg[i];", "h = h * 31u + msg[i];"),
+    "djb2 initial value": ("uint64_t h = 5381u;", "uint64_t h = 5380u;"),
+    "crc polynomial": ("const uint64_t low = 0x1Bu;", "const uint64_t low = 0x1Au;"),
+    "crc bit order": ("for (int b = 7; b >= 0; b--) {", "for (int b = 0; b <= 7; b++) {"),
+    "crc without the x^64 factor": ("for (int b = 0; b < 64; b++) {\n    const uint64_t top = rem >> 63;\n    rem <<= 1;",
+                                    "for (int b = 0; b < 0; b++) {\n    const uint64_t top = rem >> 63;\n    rem <<= 1;"),
+    "weak signatures not confirmed": ("const int confirm = db->sig == SIG_DJB2_64 || db->sig == SIG_CRC64;",
+                                      "const int confirm = 0;"),
+    "no-pad state after 7 blocks": ("for (int b = 0; b < 8; b++) md5_block(st, sector + 64 * b);",
+                                    "for (int b = 0; b < 7; b++) md5_block(st, sector + 64 * b);"),
 }
 
 
@@ -56,8 +66,34 @@ def _build_mutant(src: str, old: str, new: str, td: str) -> str:
     return lib
 
 
+def _signature_pins_pass() -> bool:
+    """The pins of tests/test_oracle_signatures.py, condensed."""
+    import test_oracle_signatures as ts
+
+    rng = np.random.default_rng(6)
+    x = rng.integers(40, 200, 512, dtype=np.uint8)
+    if oracle.md5_finish_sector(oracle.md5_nopad(x)) != hashlib.md5(x.tobytes()).digest():
+        return False
+    if oracle.djb2_64(b"") != 5381 or oracle.djb2_64(np.zeros(512, np.uint8)) != (5381 * pow(33, 512, 1 << 64)) & ts.M64:
+        return False
+    msg = bytearray(16)
+    msg[3] = 2
+    if oracle.crc64(bytes(msg)) != ts.x_pow_mod(8 * 12 + 1 + 64, ts.GEN):
+        return False
+    if oracle.crc64(x) != ts.poly_mod(int.from_bytes(x.tobytes(), "big") << 64, ts.GEN):
+        return False
+    image, files = tricky_case(1)
+    m = files[0][2 * 512:3 * 512]
+    m[:] = x
+    image = np.concatenate([image[: image.size // 512 * 512], ts.djb2_collision(x, 10), ts.crc_collision(x, 99), x])
+    want = py_match(image.tobytes(), [f.tobytes() for f in files])
+    return all(as_list(oracle.match_sig(image, files, sig)) == want for sig in (1, 2, 3))
+
+
 def _pins_pass() -> bool:
     """The pins of tests/test_oracle.py, condensed; False as soon as one fails."""
+    if not _signature_pins_pass():
+        return False
     rng = np.random.default_rng(5)
     for length in (0, 1, 55, 56, 63, 64, 100, 512, 1000):
         d = rng.integers(0, 256, length, dtype=np.uint8).tobytes()
