@@ -70,11 +70,20 @@ typedef struct cv_result cv_result; /* the results of one scan */
 
 #define CV_BLOOM_AUTO 0xFFFFFFFFu
 
+/* Sector signatures (cv_master_opts.signature). The paper proposes MD5 (Section 2.1) and
+ * measures djb2 with a 64-bit accumulator (Eq. 1) and CRC64 (Section 4). 64-bit signatures
+ * collide (Section 4.1), so the library confirms every candidate byte for byte against a copy of
+ * the master sectors it keeps on the device (Section 3.1); results are identical for all four. */
+#define CV_SIG_MD5 0u        /* RFC 1321 with the padding block: 9 compressions per sector */
+#define CV_SIG_MD5_NOPAD 1u  /* the MD5 state after the 8 data blocks (Section 2.1) */
+#define CV_SIG_DJB2_64 2u    /* h = 5381; h = 33 h + byte, mod 2^64 (Eq. 1) */
+#define CV_SIG_CRC64 3u      /* remainder of M(x) x^64 mod x^64+x^4+x^3+x+1, MSB first, no init/final XOR */
+
 typedef struct {
   uint32_t struct_size;         /* sizeof(cv_master_opts) */
   float max_load;               /* table load factor cap in (0, 0.9]; 0 selects 0.5 */
   uint32_t bloom_bits_per_key;  /* 0 = no Bloom prefilter; CV_BLOOM_AUTO = 16 */
-  uint32_t reserved;
+  uint32_t signature;           /* CV_SIG_*; 0 = MD5 */
   void* stream;                 /* cudaStream_t */
 } cv_master_opts;
 
@@ -113,7 +122,7 @@ typedef struct {
   uint64_t n_slots;          /* table slots (power of two) */
   uint64_t bloom_bytes;      /* 0 when there is no Bloom prefilter */
   uint32_t max_probe;        /* longest linear-probe run of any stored digest, plus one */
-  uint32_t reserved2;
+  uint32_t signature;        /* CV_SIG_* of the table */
   uint64_t device_bytes;     /* device memory the handle holds */
 } cv_master_info;
 

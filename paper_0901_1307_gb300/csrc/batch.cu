@@ -89,17 +89,8 @@ int enqueue_run(DevCtx* ctx, int cfg_i, const TableView& tab, const Job& job, co
   CV_CUDA((cudaError_t)launch_tile_offsets(b.tile_ntrip, n_out, b.tile_off, b.segs_d, (uint32_t)nseg,
                                            (uint32_t)(cfg.T / 32), b.counters_d, total_d, b.off_scratch, stream));
   if (launches) *launches += 4;
-  const uint4* hr = b.hit_rec;
-  const uint32_t* nh = b.tile_nhit;
-  const uint64_t* to = b.tile_off;
-  const Segment* sg = b.segs_d;
-  uint32_t ns32 = (uint32_t)nseg;
-  uint64_t nt = n_out;
-  const uint2* post = tab.postings;
-  MatchOut* o = b.out_d;
-  uint64_t cap = capacity;
-  void* eargs[] = {&hr, &nh, &to, &nt, &sg, &ns32, &post, &o, &cap, &status};
-  CV_CUDA(cudaLaunchKernel(cfg.expand_fn, dim3(grid_for(n_out * 32, 256, ctx->sms)), dim3(256), eargs, 0, stream));
+  CV_CUDA((cudaError_t)launch_expand(cfg, b.hit_rec, b.tile_nhit, b.tile_off, n_out, b.segs_d, (uint32_t)nseg, tab,
+                                     b.out_d, capacity, status, ctx->sms, stream));
   if (launches) *launches += 1;
   if (counters_h) CV_CUDA(cudaMemcpyAsync(counters_h, b.counters_d, (nseg + 2) * 8, cudaMemcpyDeviceToHost, stream));
   return CV_OK;
@@ -219,6 +210,7 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
     if (opts->kernel_config > (uint32_t)ncfg) return CV_EINVAL;
     cfg_i = (int)opts->kernel_config - 1;
   }
+  scan_config_for(cfg_i, (int)tab.sig, &cfg_i);
   if (opts && opts->bloom == CV_BATCH_BLOOM_OFF) bloom = 0;
 
   cv_batch* b = new (std::nothrow) cv_batch();
@@ -265,6 +257,7 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
       } else {
         float best = 1e30f;
         for (int k = 0; k < ncfg && k < 64; k++) {
+          if (!cfgs[k].scan_fn[tab.sig]) continue;  // not built for this signature
           Job job;
           std::vector<size_t> first;
           CV_TRY(build_job(k, &job, &first));

@@ -43,6 +43,7 @@ struct cv_master {
   void* slots;
   void* postings;
   void* bloom;
+  void* confirm;  // kept master sectors in posting order (64-bit signatures)
   cv_master_info info;
 };
 
@@ -109,9 +110,8 @@ const char* cv_kernel_config_name(int k) {
   return (k >= 0 && k < n) ? c[k].name : nullptr;
 }
 
-static int digest_job(DevCtx* ctx, Job& job, uint4* digests, uint8_t* trivial, uint32_t* status, cudaStream_t stream,
-                      Temps& tmp) {
-  const int cfg_i = ctx->cfg_index;
+static int digest_job(DevCtx* ctx, int cfg_i, int sig, Job& job, uint4* digests, uint8_t* trivial, uint32_t* status,
+                      cudaStream_t stream, Temps& tmp) {
   Segment* segs_d;
   CV_TRY(tmp.alloc(&segs_d, job.segs.size() * sizeof(Segment)));
   CV_CUDA(cudaMemcpyAsync(segs_d, job.segs.data(), job.segs.size() * sizeof(Segment), cudaMemcpyHostToDevice, stream));
@@ -120,6 +120,7 @@ static int digest_job(DevCtx* ctx, Job& job, uint4* digests, uint8_t* trivial, u
   p.status = status;
   p.digests = digests;
   p.trivial = trivial;
+  p.tab.sig = (uint32_t)sig;
   CV_TRY(launch_range(ctx, cfg_i, true, job, segs_d, 0, job.segs.size(), p, stream));
   return CV_OK;
 }
@@ -131,15 +132,15 @@ int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t
   DevCtx* ctx;
   CV_TRY(get_ctx(&ctx));
   cudaStream_t stream = (cudaStream_t)stream_;
-  int n;
-  const ScanCfg& cfg = scan_configs(&n)[ctx->cfg_index];
+  int cfg_i;
+  const ScanCfg& cfg = scan_config_for(ctx->cfg_index, kSigMd5, &cfg_i);
   Temps tmp(ctx, stream);
   Job job;
   CV_TRY(job.add(ctx, cfg, in, n_sectors, 0, 0, false));
   uint32_t* status;
   CV_TRY(tmp.alloc(&status, 4));
   CV_CUDA(cudaMemsetAsync(status, 0, 4, stream));
-  return digest_job(ctx, job, (uint4*)digests, trivial, status, stream, tmp);
+  return digest_job(ctx, cfg_i, kSigMd5, job, (uint4*)digests, trivial, status, stream, tmp);
 }
 
 int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts* opts, cv_master** out) {
@@ -151,11 +152,13 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
   uint32_t bpk = opts ? opts->bloom_bits_per_key : CV_BLOOM_AUTO;
   if (bpk == CV_BLOOM_AUTO) bpk = 16;
   if (bpk > 64) return CV_EINVAL;
+  const int sig = opts ? (int)opts->signature : kSigMd5;
+  if (sig < 0 || sig > kSigCrc64) return CV_EINVAL;
   cudaStream_t stream = opts ? (cudaStream_t)opts->stream : nullptr;
   DevCtx* ctx;
   CV_TRY(get_ctx(&ctx));
-  int ncfg;
-  const ScanCfg& cfg = scan_configs(&ncfg)[ctx->cfg_index];
+  int cfg_i;
+  const ScanCfg& cfg = scan_config_for(ctx->cfg_index, sig, &cfg_i);
 
   // whole sectors of every file, concatenated
   std::vector<uint64_t> file_base(n_files + 1, 0);
@@ -216,7 +219,7 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       if (M) {
         Job job;
         CV_TRY(job.add(ctx, cfg, arena, M, 0, 0, false));
-        CV_TRY(digest_job(ctx, job, dig, trivial, counters + 3, stream, tmp));
+        CV_TRY(digest_job(ctx, cfg_i, sig, job, dig, trivial, counters + 3, stream, tmp));
         const unsigned g = grid_for(M, 256, ctx->sms);
         insert_kernel<<<g, 256, 0, stream>>>(dig, trivial, M, owner, cnt, slot_of, mask, counters, counters + 1,
                                             counters + 3);
@@ -241,6 +244,13 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
         fill_kernel<<<g, 256, 0, stream>>>(kin, vin, M, (uint32_t)n_slots, owner, cnt, dig, file_base_d, n_files,
                                           (uint4*)m->slots, (uint2*)m->postings, counters + 2);
         CV_CUDA(cudaGetLastError());
+        if (sig_is_weak(sig)) {
+          // a copy of the kept master sectors in posting order, to confirm matches byte for byte
+          CV_CUDA(cudaMalloc(&m->confirm, M * kSector));
+          gather_sectors_kernel<<<grid_for(M * (kSector / 16), 256, ctx->sms), 256, 0, stream>>>(
+              (const uint4*)arena, kin, vin, M, (uint32_t)n_slots, (uint4*)m->confirm);
+          CV_CUDA(cudaGetLastError());
+        }
         if (bpk) {
           bloom_kernel<<<grid_for(n_slots, 256, ctx->sms), 256, 0, stream>>>((const uint4*)m->slots,
                                                                              (uint32_t)n_slots, (uint32_t*)m->bloom,
@@ -261,6 +271,9 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       m->tab.bloom_mask = bpk ? (uint32_t)(n_blocks - 1) : 0u;
       m->tab.max_probe = hc[0] + 1;
       m->tab.use_bloom = bpk ? 1u : 0u;
+      m->tab.sig = (uint32_t)sig;
+      m->tab.confirm = (const uint8_t*)m->confirm;
+      m->info.signature = (uint32_t)sig;
       m->info.n_files = n_files;
       m->info.n_sectors = M;
       m->info.n_kept = hc[1];
@@ -268,7 +281,8 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       m->info.n_slots = n_slots;
       m->info.bloom_bytes = n_blocks * 32;
       m->info.max_probe = hc[0] + 1;
-      m->info.device_bytes = n_slots * 32 + std::max<uint64_t>(M, 1) * 8 + n_blocks * 32;
+      m->info.device_bytes = n_slots * 32 + std::max<uint64_t>(M, 1) * 8 + n_blocks * 32 +
+                             (m->confirm ? M * kSector : 0);
       return CV_OK;
     };
     rc = body();
@@ -347,13 +361,17 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
   CV_TRY(get_ctx(&ctx));
   if (ctx->dev != m->dev) return CV_EINVAL;
   int ncfg;
-  const ScanCfg* cfgs = scan_configs(&ncfg);
+  scan_configs(&ncfg);
   int cfg_i = ctx->cfg_index;
   if (opts && opts->kernel_config) {
     if (opts->kernel_config > (uint32_t)ncfg) return CV_EINVAL;
     cfg_i = (int)opts->kernel_config - 1;
   }
-  const ScanCfg& cfg = cfgs[cfg_i];
+  const int sig = (int)m->tab.sig;
+  const ScanCfg& cfg = scan_config_for(cfg_i, sig, &cfg_i);
+  // With a 64-bit signature every candidate is confirmed against the disk sector's bytes after
+  // the scan, so host images are copied whole to the device instead of streamed through a ring.
+  Temps staging(ctx, stream);
 
   // ------------------------------------------------------------ plan the segments
   std::vector<BufKind> kind(n_images);
@@ -371,7 +389,12 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
     if (ns == 0) continue;
     if (!images[i].data) return CV_EINVAL;
     CV_TRY(classify(ctx, images[i].data, &kind[i]));
-    if (kind[i] == kDevice) {
+    if (kind[i] == kHost && sig_is_weak(sig)) {
+      uint8_t* copy;
+      CV_TRY(staging.alloc(&copy, ns * kSector));
+      CV_CUDA(cudaMemcpyAsync(copy, images[i].data, ns * kSector, cudaMemcpyHostToDevice, stream));
+      CV_TRY(job.add(ctx, cfg, copy, ns, 0, i, false));
+    } else if (kind[i] == kDevice) {
       if ((uintptr_t)images[i].data & 15u) return CV_EINVAL;
       CV_TRY(job.add(ctx, cfg, images[i].data, ns, 0, i, true));
     } else {
@@ -493,12 +516,8 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         total = seg_off[nseg];
         if (total) {
           CV_CUDA(cudaMallocFromPoolAsync((void**)&r->dev_out, total * sizeof(MatchOut), ctx->pool, stream));
-          const unsigned eg = grid_for(n_out * 32, 256, ctx->sms);
-          uint64_t cap = total;
-          const uint2* postings = m->tab.postings;
-          MatchOut* outp = r->dev_out;
-          void* eargs[] = {&hit_rec, &tile_nhit, &tile_off, &nt_arg, &segs_d, &nseg32, &postings, &outp, &cap, &status};
-          CV_CUDA(cudaLaunchKernel(cfg.expand_fn, dim3(eg), dim3(256), eargs, 0, stream));
+          CV_CUDA((cudaError_t)launch_expand(cfg, hit_rec, tile_nhit, tile_off, n_out, segs_d, nseg32, m->tab,
+                                             r->dev_out, total, status, ctx->sms, stream));
           r->launches += 1;
         }
         r->launches += 4;  // the offset pass
@@ -583,6 +602,7 @@ void cv_free(void* handle) {
     if (m->slots) cudaFree(m->slots);
     if (m->postings) cudaFree(m->postings);
     if (m->bloom) cudaFree(m->bloom);
+    if (m->confirm) cudaFree(m->confirm);
     free(m);
   } else if (magic == kMagicResult) {
     cv_result* r = (cv_result*)handle;

@@ -102,12 +102,14 @@ __global__ void segment_offsets_kernel(const uint64_t* tile_off, uint64_t n, con
   }
 }
 
-// One warp per output tile (32 consecutive sectors) with hits. out_cap bounds the writes
-// (kStOverflow when exceeded).
+// One warp per output tile (32 consecutive sectors) with hits. A hit record is {lane, post_off,
+// post_cnt, n_emit}: the sector emits n_emit triples, all of its postings, or with a 64-bit
+// signature (confirm != null) those whose master sector equals the disk sector byte for byte.
+// out_cap bounds the writes (kStOverflow when exceeded).
 template <int T>
 __global__ void expand_kernel(const uint4* hit_rec, const uint32_t* tile_nhit, const uint64_t* tile_off,
                               uint64_t n_out_tiles, const Segment* segs, uint32_t n_segs, const uint2* postings,
-                              MatchOut* out, uint64_t out_cap, uint32_t* status) {
+                              MatchOut* out, uint64_t out_cap, uint32_t* status, const uint8_t* confirm) {
   constexpr uint32_t kW = T / 32;
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
@@ -116,24 +118,27 @@ __global__ void expand_kernel(const uint4* hit_rec, const uint32_t* tile_nhit, c
     if (n == 0) continue;
     const uint64_t ctile = u / kW;
     const uint32_t sg = find_segment(segs, n_segs, ctile);
-    const uint64_t first_sector = segs[sg].sector_base + (ctile - segs[sg].tile_base) * T + (u % kW) * 32;
+    const uint64_t row_first = (ctile - segs[sg].tile_base) * T + (u % kW) * 32;  // within the segment
+    const uint64_t first_sector = segs[sg].sector_base + row_first;
     uint4 rec = make_uint4(0, 0, 0, 0);
     if ((uint32_t)lane < n) rec = hit_rec[u * 32 + lane];
-    uint32_t incl = rec.z;
+    uint32_t incl = rec.w;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
       if (lane >= d) incl += v;
     }
-    const uint64_t my = tile_off[u] + (incl - rec.z);
+    uint64_t o = tile_off[u] + (incl - rec.w);
+    const uint8_t* mine = confirm ? segs[sg].bytes + (row_first + rec.x) * kSector : nullptr;
     for (uint32_t k = 0; k < rec.z; k++) {
-      const uint64_t o = my + k;
+      if (confirm && !sectors_equal(mine, confirm + (uint64_t)(rec.y + k) * kSector)) continue;
       if (o < out_cap) {
         const uint2 pf = postings[rec.y + k];
         out[o] = MatchOut{first_sector + rec.x, pf.x, pf.y};
       } else {
         atomicOr(status, kStOverflow);
       }
+      o++;
     }
   }
 }

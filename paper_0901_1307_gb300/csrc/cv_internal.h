@@ -25,7 +25,13 @@ struct Segment {
   uint64_t row_base;     // row of the segment's first sector in its tensor map
   uint32_t image;        // index of the image the segment belongs to
   uint32_t map;          // index of its tensor map within the job
+  const uint8_t* bytes;  // device address of the segment's first sector (byte confirmation)
 };
+
+// Signature kinds (the values of CV_SIG_*).
+enum : int { kSigMd5 = 0, kSigMd5NoPad = 1, kSigDjb2 = 2, kSigCrc64 = 3 };
+
+__host__ __device__ constexpr bool sig_is_weak(int sig) { return sig == kSigDjb2 || sig == kSigCrc64; }
 
 // Device view of a master table.
 //   slots: 2 x uint4 per slot: {d0, d1, d2, d3} and {post_off, post_cnt, 0, 0}; post_cnt == 0
@@ -33,15 +39,46 @@ struct Segment {
 //   postings: (file_id, file_sector) per kept master sector, grouped by slot, ascending.
 //   bloom: 8 u32 words (32 bytes) per block; block d3 & bloom_mask; in word j the bit
 //          (d1 >> 5j) & 31 for j < 6, (d2 >> 5(j-6)) & 31 for j = 6, 7.
+//   confirm: for 64-bit signatures, the master sector bytes of posting q at confirm + 512 q.
 struct TableView {
   const uint4* slots;
   const uint2* postings;
   const uint4* bloom;
+  const uint8_t* confirm;
   uint32_t slot_mask;
   uint32_t bloom_mask;
   uint32_t max_probe;  // no stored digest sits further than max_probe - 1 slots from home
   uint32_t use_bloom;
+  uint32_t sig;        // kSig* of the table
+  uint32_t pad;
 };
+
+// The four table words of a 64-bit signature h: h itself (low word first, so the home slot is
+// given by the signature's least significant bits, Eq. 3) and a SplitMix64-style finalizer of h
+// that spreads it over the Bloom bits. Equal words <=> equal h.
+__host__ __device__ inline void sig64_words(uint64_t h, uint32_t w[4]) {
+  uint64_t z = h + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  w[0] = (uint32_t)h;
+  w[1] = (uint32_t)(h >> 32);
+  w[2] = (uint32_t)z;
+  w[3] = (uint32_t)(z >> 32);
+}
+
+// Byte-for-byte comparison of two device sectors (16-byte aligned).
+__device__ inline bool sectors_equal(const uint8_t* a, const uint8_t* b) {
+  const uint4* x = reinterpret_cast<const uint4*>(a);
+  const uint4* y = reinterpret_cast<const uint4*>(b);
+  uint32_t diff = 0;
+#pragma unroll 4
+  for (int k = 0; k < 32; k++) {
+    const uint4 u = __ldg(x + k), v = __ldg(y + k);
+    diff |= (u.x ^ v.x) | (u.y ^ v.y) | (u.z ^ v.z) | (u.w ^ v.w);
+  }
+  return diff == 0;
+}
 
 // Tensor maps one launch of the scan kernel can carry.
 constexpr int kMapsPerLaunch = 64;

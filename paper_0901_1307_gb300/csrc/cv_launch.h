@@ -2,6 +2,8 @@
 #pragma once
 #include <stdint.h>
 
+#include "cv_internal.h"
+
 namespace cvk {
 
 struct ScanCfg {
@@ -11,15 +13,23 @@ struct ScanCfg {
   int threads;  // block size: T / SPT hashing threads + one producer warp
   int NS;       // shared-memory ring stages
   int BOXB;   // bytes of each sector row per stage (64 or 128)
-  const void* scan_fn;    // scan_kernel<T, NS, BOXB, kModeScan>
-  const void* digest_fn;  // scan_kernel<T, NS, BOXB, kModeDigest>
-  const void* expand_fn;  // expand_kernel<T>
-  uint32_t smem;          // dynamic shared memory bytes
+  const void* scan_fn[4];    // scan_kernel per signature (kSig*); null: not built for this one
+  const void* digest_fn[4];  // the same in digest mode
+  const void* expand_fn;     // expand_kernel<T>
+  uint32_t smem;             // dynamic shared memory bytes
 };
 
 const ScanCfg* scan_configs(int* n);
 
-struct Segment;
+// Configuration cfg_i if it has kernels for signature sig, else the default one (index 0, which
+// has every signature); *used receives the index in use.
+const ScanCfg& scan_config_for(int cfg_i, int sig, int* used);
+
+// The expand pass over n_out_tiles output tiles (see expand_kernel). Returns a CUDA error code.
+int launch_expand(const ScanCfg& cfg, const uint4* hit_rec, const uint32_t* tile_nhit, const uint64_t* tile_off,
+                  uint64_t n_out_tiles, const Segment* segs, uint32_t n_segs, const TableView& tab, MatchOut* out,
+                  uint64_t out_cap, uint32_t* status, int sms, void* stream);
+
 
 // Scratch (u64 words) the offset pass needs for n tiles.
 uint64_t tile_offsets_scratch_words(uint64_t n_tiles);

@@ -6,22 +6,36 @@
 
 namespace cvk {
 
+#define CV_KS(T, SPT, NS, B, MODE, P, MB, SIG) (const void*)scan_kernel<T, SPT, NS, B, MODE, P, MB, SIG>
+
+// A configuration with MD5 kernels only.
 #define CV_SCAN_CFG(T, SPT, NS, B, P, MB)                                                                  \
   ScanCfg {                                                                                                \
     "t" #T "_x" #SPT "_s" #NS "_b" #B "_p" #P, T, SPT, T / SPT + 32, NS, B,                                 \
-        (const void*)scan_kernel<T, SPT, NS, B, kModeScan, P, MB>,                                        \
-        (const void*)scan_kernel<T, SPT, NS, B, kModeDigest, P, MB>, (const void*)expand_kernel<T>,        \
-        ScanSmem<T, NS, B>::kAlloc                                                                         \
+        {CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigMd5), nullptr, nullptr, nullptr},                      \
+        {CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigMd5), nullptr, nullptr, nullptr},                    \
+        (const void*)expand_kernel<T>, ScanSmem<T, NS, B>::kAlloc                                          \
+  }
+
+// A configuration with kernels for every signature.
+#define CV_SCAN_CFG_ALL(T, SPT, NS, B, P, MB)                                                              \
+  ScanCfg {                                                                                                \
+    "t" #T "_x" #SPT "_s" #NS "_b" #B "_p" #P, T, SPT, T / SPT + 32, NS, B,                                 \
+        {CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigMd5), CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigMd5NoPad), \
+         CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigDjb2), CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigCrc64)},  \
+        {CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigMd5),                                                \
+         CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigMd5NoPad),                                           \
+         CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigDjb2),                                               \
+         CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigCrc64)},                                             \
+        (const void*)expand_kernel<T>, ScanSmem<T, NS, B>::kAlloc                                          \
   }
 
 // The first entry is the default configuration (the fastest measured on GB300 for the 32 GiB
-// image workload); the others stay selectable and are what the batch autotuner tries.
+// image workload) and the only one built for every signature; the others stay selectable and
+// are what the batch autotuner tries.
 static const ScanCfg kConfigs[] = {
-    CV_SCAN_CFG(256, 1, 2, 64, 3, 0),
+    CV_SCAN_CFG_ALL(256, 1, 2, 64, 3, 0),
     CV_SCAN_CFG(480, 1, 2, 64, 3, 3),
-    CV_SCAN_CFG(352, 1, 2, 64, 3, 4),
-    CV_SCAN_CFG(224, 1, 2, 64, 3, 6),
-    CV_SCAN_CFG(480, 1, 3, 64, 3, 3),
     CV_SCAN_CFG(256, 1, 2, 64, 0, 0),
     CV_SCAN_CFG(256, 1, 2, 64, 2, 0),
     CV_SCAN_CFG(256, 2, 2, 64, 3, 0),
@@ -34,6 +48,27 @@ static const ScanCfg kConfigs[] = {
 const ScanCfg* scan_configs(int* n) {
   *n = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
   return kConfigs;
+}
+
+const ScanCfg& scan_config_for(int cfg_i, int sig, int* used) {
+  int n;
+  const ScanCfg* c = scan_configs(&n);
+  if (cfg_i < 0 || cfg_i >= n || sig < 0 || sig > 3 || !c[cfg_i].scan_fn[sig]) cfg_i = 0;
+  if (used) *used = cfg_i;
+  return c[cfg_i];
+}
+
+int launch_expand(const ScanCfg& cfg, const uint4* hit_rec, const uint32_t* tile_nhit, const uint64_t* tile_off,
+                  uint64_t n_out_tiles, const Segment* segs, uint32_t n_segs, const TableView& tab, MatchOut* out,
+                  uint64_t out_cap, uint32_t* status, int sms, void* stream) {
+  const uint2* post = tab.postings;
+  const uint8_t* confirm = sig_is_weak((int)tab.sig) ? tab.confirm : nullptr;
+  uint64_t g = (n_out_tiles * 32 + 255) / 256;
+  if (g > (uint64_t)sms * 16) g = (uint64_t)sms * 16;
+  if (g == 0) g = 1;
+  void* args[] = {&hit_rec, &tile_nhit, &tile_off, &n_out_tiles, &segs, &n_segs, &post, &out, &out_cap, &status,
+                  &confirm};
+  return (int)cudaLaunchKernel(cfg.expand_fn, dim3((unsigned)g), dim3(256), args, 0, (cudaStream_t)stream);
 }
 
 int launch_wait_selftest(uint32_t* status, uint64_t timeout_ns, void* stream) {

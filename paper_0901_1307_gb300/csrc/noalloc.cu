@@ -82,9 +82,12 @@ int setup(int dev, NoAllocDev** out) {
     const ScanCfg& cfg = scan_configs(&n)[0];
     e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(e);
-    e = cudaFuncSetAttribute(cfg.scan_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
-    if (e != cudaSuccess) return fail(e);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, cfg.scan_fn, cfg.threads, cfg.smem);
+    for (int sig = 0; sig < 4; sig++) {
+      if (!cfg.scan_fn[sig]) continue;
+      e = cudaFuncSetAttribute(cfg.scan_fn[sig], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+      if (e != cudaSuccess) return fail(e);
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, cfg.scan_fn[0], cfg.threads, cfg.smem);
     if (e != cudaSuccess || d.blocks_per_sm < 1) return fail(e);
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
@@ -122,8 +125,7 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   int rc = setup(dev, &d);
   if (rc != CV_OK) return rc;
   cudaStream_t stream = (cudaStream_t)stream_;
-  int ncfg;
-  const ScanCfg& cfg = scan_configs(&ncfg)[0];
+  const ScanCfg& cfg = scan_config_for(0, (int)tab.sig, nullptr);
 
   uint8_t* sc = d->scratch;
   Segment* seg_d = (Segment*)(sc + kOffSeg);
@@ -156,6 +158,7 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   seg.row_base = 0;
   seg.image = 0;
   seg.map = 0;
+  seg.bytes = (const uint8_t*)image;
   const uint64_t n_tiles = (S + cfg.T - 1) / cfg.T;
   const uint64_t n_out_tiles = n_tiles * (uint64_t)(cfg.T / 32);  // output tiles of 32 sectors
   if (n_out_tiles > kMaxTiles) return CV_EINVAL;                   // tile wider than the layout allows
@@ -177,7 +180,8 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   p.status = status_d;
   const uint64_t grid = n_tiles < (uint64_t)d->sms * d->blocks_per_sm ? n_tiles : (uint64_t)d->sms * d->blocks_per_sm;
   void* sargs[] = {&p};
-  if ((e = cudaLaunchKernel(cfg.scan_fn, dim3((unsigned)grid), dim3(cfg.threads), sargs, cfg.smem, stream)) !=
+  if ((e = cudaLaunchKernel(cfg.scan_fn[tab.sig], dim3((unsigned)grid), dim3(cfg.threads), sargs, cfg.smem,
+                            stream)) !=
       cudaSuccess)
     return fail(e);
   uint32_t one = 1;
@@ -187,16 +191,8 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   if ((e = (cudaError_t)launch_tile_offsets(tile_ntrip, nt, tile_off, segc, one, (uint32_t)(cfg.T / 32), seg_off_d,
                                             total_d, (uint64_t*)(sc + kOffSums), stream)) != cudaSuccess)
     return fail(e);
-  const uint4* hr = hit_rec;
-  const uint32_t* nh = tile_nhit;
-  const uint64_t* to = tile_off;
-  const uint2* post = tab.postings;
-  MatchOut* o = (MatchOut*)out;
-  uint64_t cap = out_capacity;
-  uint64_t eg = (n_out_tiles * 32 + 255) / 256;
-  if (eg > (uint64_t)d->sms * 16) eg = (uint64_t)d->sms * 16;
-  void* eargs[] = {&hr, &nh, &to, &nt, &segc, &one, &post, &o, &cap, &status_d};
-  if ((e = cudaLaunchKernel(cfg.expand_fn, dim3((unsigned)eg), dim3(256), eargs, 0, stream)) != cudaSuccess)
+  if ((e = (cudaError_t)launch_expand(cfg, hit_rec, tile_nhit, tile_off, nt, segc, one, tab, (MatchOut*)out,
+                                      out_capacity, status_d, d->sms, stream)) != cudaSuccess)
     return fail(e);
   uint64_t hc[2] = {0, 0};  // total, status
   if ((e = cudaMemcpyAsync(hc, total_d, 16, cudaMemcpyDeviceToHost, stream)) != cudaSuccess) return fail(e);

@@ -74,14 +74,21 @@ int get_ctx(DevCtx** out) {
     c.blocks_per_sm.assign(n, 0);
     c.blocks_per_sm_digest.assign(n, 0);
     for (int i = 0; i < n; i++) {
-      CV_CUDA(cudaFuncSetAttribute(cfgs[i].scan_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfgs[i].smem));
-      CV_CUDA(cudaFuncSetAttribute(cfgs[i].digest_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfgs[i].smem));
-      CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.blocks_per_sm[i], cfgs[i].scan_fn, cfgs[i].threads,
+      for (int sig = 0; sig < 4; sig++) {
+        if (cfgs[i].scan_fn[sig])
+          CV_CUDA(cudaFuncSetAttribute(cfgs[i].scan_fn[sig], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)cfgs[i].smem));
+        if (cfgs[i].digest_fn[sig])
+          CV_CUDA(cudaFuncSetAttribute(cfgs[i].digest_fn[sig], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)cfgs[i].smem));
+      }
+      CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.blocks_per_sm[i], cfgs[i].scan_fn[0], cfgs[i].threads,
                                                             cfgs[i].smem));
-      CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.blocks_per_sm_digest[i], cfgs[i].digest_fn,
+      CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.blocks_per_sm_digest[i], cfgs[i].digest_fn[0],
                                                             cfgs[i].threads, cfgs[i].smem));
       if (c.blocks_per_sm[i] < 1 || c.blocks_per_sm_digest[i] < 1) return CV_ECUDA;
     }
+
     c.cfg_index = 0;
     const char* env = getenv("CV_SCAN_CONFIG");
     if (env && *env) {
@@ -173,6 +180,7 @@ int Job::add(DevCtx* ctx, const ScanCfg& cfg, const void* base, uint64_t n_in, u
     s.tile_base = n_tiles;
     s.sector_base = sector_base + done;
     s.image = image;
+    s.bytes = base ? (const uint8_t*)base + done * kSector : nullptr;
     if (map >= 0) {
       s.map = (uint32_t)map;
       s.row_base = row_base + done;
@@ -197,6 +205,7 @@ int Job::set_map(DevCtx* ctx, const ScanCfg& cfg, size_t s, const void* base) {
   Segment& sg = segs[s];
   CV_TRY(make_tmap(ctx, cfg, base, sg.n_sectors, &maps[sg.map]));
   map_base[sg.map] = (uintptr_t)base;
+  sg.bytes = (const uint8_t*)base;
   return CV_OK;
 }
 
@@ -204,6 +213,9 @@ int launch_range(DevCtx* ctx, int cfg_i, bool digest, const Job& job, const Segm
                  const ScanParams& base, cudaStream_t stream, int* launches) {
   int n;
   const ScanCfg& cfg = scan_configs(&n)[cfg_i];
+  const int sig = (int)base.tab.sig;
+  const void* fn = digest ? cfg.digest_fn[sig] : cfg.scan_fn[sig];
+  if (!fn) return CV_EINVAL;  // the caller picks a configuration built for the signature
   const int bps = digest ? ctx->blocks_per_sm_digest[cfg_i] : ctx->blocks_per_sm[cfg_i];
   size_t a = s0;
   while (a < s1) {
@@ -238,8 +250,7 @@ int launch_range(DevCtx* ctx, int cfg_i, bool digest, const Job& job, const Segm
     if (p.n_tiles) {
       const uint64_t grid = std::min<uint64_t>(p.n_tiles, (uint64_t)ctx->sms * bps);
       void* args[] = {&p};
-      CV_CUDA(cudaLaunchKernel(digest ? cfg.digest_fn : cfg.scan_fn, dim3((unsigned)grid), dim3(cfg.threads), args,
-                               cfg.smem, stream));
+      CV_CUDA(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(cfg.threads), args, cfg.smem, stream));
       if (launches) (*launches)++;
     }
     a = b;

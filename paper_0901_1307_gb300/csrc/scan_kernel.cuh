@@ -126,6 +126,49 @@ __device__ __forceinline__ uint32_t table_probe(const TableView& tab, uint32_t d
   return 0u;
 }
 
+// djb2 over one 64-byte block (Eq. 1): four bytes at a time, h = h * 33^4 + the word's bytes
+// in Horner form (byte 0 is the word's low byte; at most 255 * 37060 < 2^32).
+__device__ __forceinline__ uint64_t djb2_block(uint64_t h, const uint32_t (&X)[16]) {
+#pragma unroll
+  for (int q = 0; q < 16; q++) {
+    const uint32_t w = X[q];
+    const uint32_t part = (((w & 0xFFu) * 33u + ((w >> 8) & 0xFFu)) * 33u + ((w >> 16) & 0xFFu)) * 33u + (w >> 24);
+    h = h * 1185921ull + part;  // 33^4
+  }
+  return h;
+}
+
+// The CRC64 byte table for the generator x^64 + x^4 + x^3 + x + 1 (most significant bit
+// first): entry i is the remainder of i(x) x^64, built at compile time by shifting i through
+// eight steps of the division.
+struct Crc64Table {
+  uint64_t v[256];
+};
+constexpr Crc64Table make_crc64_table() {
+  Crc64Table t{};
+  for (uint64_t i = 0; i < 256; i++) {
+    uint64_t c = i << 56;
+    for (int b = 0; b < 8; b++) c = (c & (1ull << 63)) ? (c << 1) ^ 0x1Bull : (c << 1);
+    t.v[i] = c;
+  }
+  return t;
+}
+__device__ constexpr Crc64Table kCrc64Table = make_crc64_table();
+
+// CRC64 over one 64-byte block, a byte at a time through the 256-entry table in shared memory:
+// crc = (crc << 8) ^ T[(crc >> 56) ^ byte], bytes in memory order.
+__device__ __forceinline__ uint64_t crc64_block(uint64_t crc, const uint32_t (&X)[16], const uint64_t* T) {
+#pragma unroll
+  for (int q = 0; q < 16; q++) {
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      const uint32_t byte = (X[q] >> (8 * b)) & 0xFFu;
+      crc = (crc << 8) ^ T[(uint32_t)(crc >> 56) ^ byte];
+    }
+  }
+  return crc;
+}
+
 enum : int { kModeScan = 0, kModeDigest = 1 };
 
 template <int T, int NS, int BOXB>
@@ -134,7 +177,8 @@ struct ScanSmem {
   // stages first (1024-byte aligned), then the barriers and the abort flag
   static constexpr uint32_t kBarOff = NS * kStageBytes;
   static constexpr uint32_t kMiscOff = kBarOff + 2 * NS * 8;
-  static constexpr uint32_t kBytes = kMiscOff + 16;
+  static constexpr uint32_t kCrcOff = kMiscOff + 16;  // CRC64 byte table (256 x 8 bytes)
+  static constexpr uint32_t kBytes = kCrcOff + 256 * 8;
   static constexpr uint32_t kAlloc = kBytes + 1024;  // room to align the base
 };
 
@@ -144,7 +188,7 @@ struct ScanSmem {
 // blocks per SM the register allocation must allow (0: no constraint).
 // Thread t hashes rows t, t + C, ... of the tile. Matches are compacted per warp and row group:
 // rows [32v, 32v + 32) of tile k form output tile k * (T / 32) + v.
-template <int T, int SPT, int NS, int BOXB, int MODE, int PIPE, int MINB>
+template <int T, int SPT, int NS, int BOXB, int MODE, int PIPE, int MINB, int SIG>
 __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_constant__ ScanParams p) {
   constexpr int C = T / SPT;
   // A tile larger than the 256-row TMA box limit is loaded as several boxes per stage.
@@ -166,6 +210,7 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
   const uint32_t bar_full = base + L::kBarOff;  // NS x 8 bytes
   const uint32_t bar_empty = bar_full + NS * 8;
   volatile uint32_t* const s_abort = reinterpret_cast<uint32_t*>(gbase + L::kMiscOff);
+  uint64_t* const s_crc = reinterpret_cast<uint64_t*>(gbase + L::kCrcOff);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -178,6 +223,9 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
     }
     *s_abort = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if constexpr (SIG == kSigCrc64) {
+    for (int k = tid; k < 256; k += blockDim.x) s_crc[k] = kCrc64Table.v[k];
   }
   __syncthreads();
 
@@ -238,10 +286,12 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
     const uint64_t row0 = (tile - seg.tile_base) * T;  // within the segment
 
     uint32_t st[SPT][4];
+    uint64_t h[SPT];  // djb2 / CRC64 accumulators
     uint32_t diff[SPT], ref[SPT];
 #pragma unroll
     for (int k = 0; k < SPT; k++) {
       md5_init(st[k]);
+      h[k] = SIG == kSigDjb2 ? 5381ull : 0ull;
       diff[k] = 0;
       ref[k] = 0;
     }
@@ -279,7 +329,13 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
             for (int q = 0; q < 16; q++) diff[k] |= X[k][q] ^ ref[k];
           }
         }
-        if constexpr (SPT == 2) {
+        if constexpr (SIG == kSigDjb2) {
+#pragma unroll
+          for (int k = 0; k < SPT; k++) h[k] = djb2_block(h[k], X[k]);
+        } else if constexpr (SIG == kSigCrc64) {
+#pragma unroll
+          for (int k = 0; k < SPT; k++) h[k] = crc64_block(h[k], X[k], s_crc);
+        } else if constexpr (SPT == 2) {
           md5_compress_x2<PIPE>(st[0], X[0], st[1], X[1], p.one);
         } else {
           md5_compress<PIPE>(st[0], X[0], p.one);
@@ -287,7 +343,10 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
       }
     }
 #pragma unroll
-    for (int k = 0; k < SPT; k++) md5_compress_sector_padding(st[k]);
+    for (int k = 0; k < SPT; k++) {
+      if constexpr (SIG == kSigMd5) md5_compress_sector_padding(st[k]);
+      if constexpr (sig_is_weak(SIG)) sig64_words(h[k], st[k]);
+    }
 
 #pragma unroll
     for (int k = 0; k < SPT; k++) {
@@ -303,11 +362,22 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
         uint32_t post_off = 0, post_cnt = 0;
         if (valid && (!p.tab.use_bloom || bloom_test(p.tab, st[k][1], st[k][2], st[k][3])))
           post_cnt = table_probe(p.tab, st[k][0], st[k][1], st[k][2], st[k][3], post_off);
-        const bool hit = post_cnt != 0u;
+        // triples this sector emits: every posting, or for a 64-bit signature the postings whose
+        // master sector equals this sector byte for byte
+        uint32_t n_emit = post_cnt;
+        if constexpr (sig_is_weak(SIG)) {
+          if (post_cnt) {
+            const uint8_t* mine = seg.bytes + r * kSector;
+            n_emit = 0;
+            for (uint32_t q = 0; q < post_cnt; q++)
+              n_emit += sectors_equal(mine, p.tab.confirm + (uint64_t)(post_off + q) * kSector) ? 1u : 0u;
+          }
+        }
+        const bool hit = n_emit != 0u;
         const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, hit);
-        const uint32_t wtrip = __reduce_add_sync(0xFFFFFFFFu, post_cnt);
+        const uint32_t wtrip = __reduce_add_sync(0xFFFFFFFFu, n_emit);
         const uint64_t u = tile * kW + (uint64_t)(warp + k * kCW);  // this row group's output tile
-        if (hit) p.hit_rec[u * 32 + __popc(ballot & lane_lt)] = make_uint4((uint32_t)lane, post_off, post_cnt, 0u);
+        if (hit) p.hit_rec[u * 32 + __popc(ballot & lane_lt)] = make_uint4((uint32_t)lane, post_off, post_cnt, n_emit);
         if (lane == 0) {
           p.tile_nhit[u] = __popc(ballot);
           p.tile_ntrip[u] = wtrip;

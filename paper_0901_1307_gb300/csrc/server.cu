@@ -232,6 +232,7 @@ int cv_server::iterate(bool* did_work) {
         s.row_base = (uint64_t)u.slot * unit_sectors;
         s.image = (uint32_t)refs.size();
         s.map = 0;
+        s.bytes = arena + (uint64_t)u.slot * unit_bytes;
         job.segs.push_back(s);
         job.n_tiles += (u.n_sectors + cfg.T - 1) / cfg.T;
         job.n_sectors += u.n_sectors;
@@ -273,7 +274,14 @@ int cv_server::iterate(bool* did_work) {
   if (st0 & kStTimeout) return CV_ETIMEOUT;
   if (st0) return CV_ECORRUPT;
   std::vector<uint64_t> seg_off(counters_h, counters_h + nseg + 1);
-  // the scan read the arena: its slots are free again
+  if (total) {
+    CV_TRY(ensure_buffers(0, 0, total));
+    CV_CUDA((cudaError_t)launch_expand(cfg, hit_rec, tile_nhit, tile_off, n_out, segs_d, (uint32_t)nseg, tab, out_d,
+                                       cap_out, status, ctx->sms, stream));
+    CV_CUDA(cudaMemcpyAsync(out_h, out_d, total * sizeof(MatchOut), cudaMemcpyDeviceToHost, stream));
+    CV_CUDA(cudaStreamSynchronize(stream));
+  }
+  // scan and expand (which rereads units for byte confirmation) are done: the slots are free
   for (const Ref& f : refs) {
     Unit& u = f.r->units[f.unit];
     if (u.slot >= 0) {
@@ -282,22 +290,6 @@ int cv_server::iterate(bool* did_work) {
       u.slot = -1;
     }
     u.scanned = true;
-  }
-  if (total) {
-    CV_TRY(ensure_buffers(0, 0, total));
-    const uint4* hr = hit_rec;
-    const uint32_t* nh = tile_nhit;
-    const uint64_t* to = tile_off;
-    const Segment* sg = segs_d;
-    uint32_t ns32 = (uint32_t)nseg;
-    uint64_t nt = n_out;
-    const uint2* post = tab.postings;
-    MatchOut* o = out_d;
-    uint64_t cap = cap_out;
-    void* eargs[] = {&hr, &nh, &to, &nt, &sg, &ns32, &post, &o, &cap, &status};
-    CV_CUDA(cudaLaunchKernel(cfg.expand_fn, dim3(grid_for(n_out * 32, 256, ctx->sms)), dim3(256), eargs, 0, stream));
-    CV_CUDA(cudaMemcpyAsync(out_h, out_d, total * sizeof(MatchOut), cudaMemcpyDeviceToHost, stream));
-    CV_CUDA(cudaStreamSynchronize(stream));
   }
   // distribute: segment k belongs to refs[k] (one segment per unit)
   std::vector<Request*> completed;
@@ -375,6 +367,7 @@ int cv_server_create(const cv_master* m, const cv_server_opts* opts, cv_server**
     if (opts->kernel_config > (uint32_t)ncfg) return CV_EINVAL;
     cfg_i = (int)opts->kernel_config - 1;
   }
+  scan_config_for(cfg_i, (int)tab.sig, &cfg_i);
   uint64_t unit = (opts && opts->work_unit_bytes) ? opts->work_unit_bytes : (64ull << 20);
   uint64_t budget = (opts && opts->hbm_budget_bytes) ? opts->hbm_budget_bytes : (8ull << 30);
   if (unit % kSector || unit > kMaxSegmentSectors * kSector || budget < unit) return CV_EINVAL;

@@ -27,6 +27,7 @@ CV_ETIMEOUT = -6
 CV_ENODEV = -7
 CV_ERANGE = -8
 CV_BLOOM_AUTO = 0xFFFFFFFF
+CV_SIG_MD5, CV_SIG_MD5_NOPAD, CV_SIG_DJB2_64, CV_SIG_CRC64 = 0, 1, 2, 3
 CV_KEEP_ON_DEVICE = 1
 SECTOR = 512
 
@@ -55,7 +56,7 @@ class cv_buf(ctypes.Structure):
 
 class cv_master_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("max_load", ctypes.c_float),
-                ("bloom_bits_per_key", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("stream", ctypes.c_void_p)]
+                ("bloom_bits_per_key", ctypes.c_uint32), ("signature", ctypes.c_uint32), ("stream", ctypes.c_void_p)]
 
 
 class cv_scan_opts(ctypes.Structure):
@@ -66,7 +67,7 @@ class cv_scan_opts(ctypes.Structure):
 class cv_master_info(ctypes.Structure):
     _fields_ = [("n_files", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("n_sectors", ctypes.c_uint64),
                 ("n_kept", ctypes.c_uint64), ("n_unique", ctypes.c_uint64), ("n_slots", ctypes.c_uint64),
-                ("bloom_bytes", ctypes.c_uint64), ("max_probe", ctypes.c_uint32), ("reserved2", ctypes.c_uint32),
+                ("bloom_bytes", ctypes.c_uint64), ("max_probe", ctypes.c_uint32), ("signature", ctypes.c_uint32),
                 ("device_bytes", ctypes.c_uint64)]
 
 
@@ -316,10 +317,11 @@ class Result:
             pass
 
 
-def master_build(files, max_load: float = 0.0, bloom_bits_per_key: int = CV_BLOOM_AUTO, stream=None) -> Master:
+def master_build(files, max_load: float = 0.0, bloom_bits_per_key: int = CV_BLOOM_AUTO, stream=None,
+                 signature: int = CV_SIG_MD5) -> Master:
     """cv_master_build: the signature table of a list of master files."""
     arr, keep = _bufs(list(files))
-    o = cv_master_opts(ctypes.sizeof(cv_master_opts), max_load, bloom_bits_per_key, 0, _stream(stream))
+    o = cv_master_opts(ctypes.sizeof(cv_master_opts), max_load, bloom_bits_per_key, signature, _stream(stream))
     h = ctypes.c_void_p()
     _check(load().cv_master_build(arr, len(files), ctypes.byref(o), ctypes.byref(h)), "cv_master_build")
     del keep
