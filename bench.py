@@ -36,6 +36,18 @@ SM_COUNT = 152
 INT_LANES_PER_SM_CLK = 128  # 4 schedulers x 32 lanes, integer work split over the ALU and FMA pipes
 
 
+def max_over_ranks(value: float, dist=None, device: str = "cpu") -> float:
+    """The largest value over all ranks (the step time of the slowest rank); no collective on
+    the data path, only this reduction of one number."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def rank_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
         os.environ.get("LOCAL_RANK", "0"))
@@ -220,6 +232,42 @@ def expected_window(expect: np.ndarray, a: int, n: int) -> np.ndarray:
     return out
 
 
+def run_signatures(torch, cv, synth, plan, image, stream, steps):
+    """The same device-resident scan with the paper's other signatures: MD5 without padding,
+    djb2-64 and CRC64 (64-bit ones confirmed byte for byte on the device)."""
+    base = plan.file_base()
+    base_d = torch.from_numpy(base.view(np.uint8).copy()).cuda()
+    masters = torch.empty(plan.n_master_sectors * SECTOR, dtype=torch.uint8, device="cuda")
+    plan.masters_device(masters.data_ptr(), base_d.data_ptr())
+    torch.cuda.synchronize()
+    files = [(masters.data_ptr() + int(base[f]) * SECTOR, int(plan.file_nsect[f]) * SECTOR)
+             for f in range(plan.n_files)]
+    out = {}
+    ref_matches = None
+    for sig, name in ((0, "md5"), (1, "md5_nopad"), (2, "djb2_64"), (3, "crc64")):
+        m = cv.master_build(files, signature=sig)
+        for _ in range(3):
+            cv.scan(m, [image], keep_on_device=True, stream=stream).close()
+        kms, matches = [], 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            r = cv.scan(m, [image], keep_on_device=True, stream=stream)
+            st = r.stats()
+            kms.append(st["kernel_ms"])
+            matches = st["matches"]
+            r.close()
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / steps
+        ref_matches = matches if ref_matches is None else ref_matches
+        out[name] = {"GBps": plan.n_bytes / wall / 1e9, "kernel_GBps": plan.n_bytes / (statistics.mean(kms) * 1e-3) / 1e9,
+                     "matches": matches, "same_matches_as_md5": matches == ref_matches}
+        m.close()
+    del masters
+    torch.cuda.synchronize()
+    return out
+
+
 def run_batched(torch, cv, synth, args, stream):
     """512 device images of uneven sizes (one device arena) against one 8M-sector table: one CUDA
     graph launch per run, autotuned, against 512 sequential cv_scan calls on the same images."""
@@ -362,6 +410,8 @@ def main():
     ap.add_argument("--ref-sample-sectors", type=int, default=1 << 19)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-sigs", action="store_true")
+    ap.add_argument("--sig-steps", type=int, default=20)
     ap.add_argument("--batch-images", type=int, default=512)
     ap.add_argument("--batch-total-gib", type=int, default=64)
     ap.add_argument("--batch-density", type=float, default=0.01)
@@ -421,14 +471,14 @@ def main():
             r.close()
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, "cuda")
     clocks = clk.summary()
     nbytes = plan.n_bytes
     value = world * nbytes / (ms * 1e-3) / 1e9
+
+    sigs = None
+    if not args.no_sigs:
+        sigs = run_signatures(torch, cv, synth, plan, image, stream, args.sig_steps)
 
     # end to end through the C ABI from pinned host memory
     e2e = None
@@ -487,6 +537,7 @@ def main():
                      "hbm_peak_GBps_measured": hbm, "int_peak_measured": int_peak},
         "clocks": clocks,
         "e2e": e2e,
+        "signatures": sigs,
         "gpu_launches": launches,
     }
     master.close()
