@@ -91,6 +91,8 @@ def bind(lib):
     lib.oracle_signature.restype = None
     lib.oracle_match_sig.argtypes = [vp, u64, vp, vp, u32, ctypes.c_int, vp, u64]
     lib.oracle_match_sig.restype = ctypes.c_int64
+    lib.oracle_match_position.argtypes = [vp, u64, vp, vp, u32, u64, vp, u64]
+    lib.oracle_match_position.restype = ctypes.c_int64
     lib.oracle_db_build_sig.argtypes = [vp, vp, u32, ctypes.c_int]
     lib.oracle_db_build_sig.restype = vp
     lib.oracle_threads.argtypes = []
@@ -225,6 +227,13 @@ def match_sig(image, files, sig: int) -> np.ndarray:
     """The method with a chosen signature (64-bit ones confirmed byte for byte)."""
     lib = _load()
     return _run_match(lambda *a: lib.oracle_match_sig(*a[:5], sig, *a[5:]), image, files)
+
+
+def match_position(image, files, base_offset: int = 0) -> np.ndarray:
+    """Position-keyed matching (tables S_tau): triples whose disk sector has the master sector's
+    position in its 8-sector cluster, disk clusters counted from sector base_offset."""
+    lib = _load()
+    return _run_match(lambda *a: lib.oracle_match_position(*a[:5], int(base_offset), *a[5:]), image, files)
 
 
 def match_hash(image, files) -> np.ndarray:

@@ -406,6 +406,46 @@ int64_t oracle_match_sig(const uint8_t* image, uint64_t image_bytes, const uint8
   return n;
 }
 
+/* Position-keyed matching (Section 3.1: tables S_tau, one per sector position tau in an
+ * 8-sector cluster): the result restricted to triples whose disk sector sits at the same cluster
+ * position as the master sector, disk positions counted from sector base_offset (the start of
+ * the partition the clusters belong to): ((i - base_offset) mod 8) == (s mod 8). */
+int64_t oracle_match_position(const uint8_t* image, uint64_t image_bytes, const uint8_t* const* files,
+                              const uint64_t* file_bytes, uint32_t n_files, uint64_t base_offset, oracle_triple* out,
+                              uint64_t cap) {
+  oracle_db* db = oracle_db_build(files, file_bytes, n_files);
+  if (!db) return -1;
+  const uint64_t n_disk = image_bytes / SECTOR;
+  uint64_t cap_all = 1024;
+  oracle_triple* all = NULL;
+  int64_t n_all;
+  for (;;) {
+    free(all);
+    all = (oracle_triple*)malloc(sizeof(oracle_triple) * cap_all);
+    if (!all) {
+      oracle_db_free(db);
+      return -1;
+    }
+    n_all = oracle_db_lookup(db, image, n_disk, 0, all, cap_all);
+    if (n_all < 0 || (uint64_t)n_all <= cap_all) break;
+    cap_all = (uint64_t)n_all;
+  }
+  oracle_db_free(db);
+  if (n_all < 0) {
+    free(all);
+    return -1;
+  }
+  uint64_t n = 0;
+  for (int64_t k = 0; k < n_all; k++) {
+    const uint64_t tau_disk = ((all[k].disk_sector % 8u) + 8u - (base_offset % 8u)) % 8u;
+    if (tau_disk != all[k].file_sector % 8u) continue;
+    if (n < cap) out[n] = all[k];
+    n++;
+  }
+  free(all);
+  return (int64_t)n;
+}
+
 /* The whole method over one image: database, lookup of every whole sector, sorted result. */
 int64_t oracle_match_hash(const uint8_t* image, uint64_t image_bytes, const uint8_t* const* files,
                           const uint64_t* file_bytes, uint32_t n_files, oracle_triple* out, uint64_t cap) {

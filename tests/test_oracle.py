@@ -210,3 +210,24 @@ def test_tiny_workload_plant_log():
         f = files[t["file_id"]]
         s = int(t["file_sector"])
         assert np.array_equal(secs[t["disk_sector"]], f[s * SECTOR:(s + 1) * SECTOR])
+
+
+@pytest.mark.parametrize("base", [0, 3, 8, 13])
+def test_position_keyed_matching(base):
+    """S_tau restricts the result to equal cluster positions: the definition's triples filtered
+    by ((i - base) mod 8) == (s mod 8); planted whole clusters all survive at base 0 and none at
+    a base that is not a multiple of 8."""
+    plan = synth.config_plan("small:8192:20:31")
+    img = plan.image_host()
+    files = plan.masters_host()
+    want = [t for t in py_match(img.tobytes(), [f.tobytes() for f in files]) if (t[0] - base) % 8 == t[2] % 8]
+    got = as_list(oracle.match_position(img, files, base))
+    assert got == want
+    full = oracle.match_hash(img, files)
+    if base % 8 == 0:
+        assert got == as_list(full)
+    else:
+        assert got == []
+    image, files2 = tricky_case(2)
+    want2 = [t for t in py_match(image.tobytes(), [f.tobytes() for f in files2]) if (t[0] - base) % 8 == t[2] % 8]
+    assert as_list(oracle.match_position(image, files2, base)) == want2

@@ -50,6 +50,10 @@ MUTANTS = {
                                     "for (int b = 0; b < 0; b++) {\n    const uint64_t top = rem >> 63;\n    rem <<= 1;"),
     "weak signatures not confirmed": ("const int confirm = db->sig == SIG_DJB2_64 || db->sig == SIG_CRC64;",
                                       "const int confirm = 0;"),
+    "position base added not subtracted": ("((all[k].disk_sector % 8u) + 8u - (base_offset % 8u)) % 8u",
+                                           "((all[k].disk_sector % 8u) + (base_offset % 8u)) % 8u"),
+    "position from the disk sector only": ("if (tau_disk != all[k].file_sector % 8u) continue;",
+                                           "if (tau_disk != 0u) continue;"),
     "no-pad state after 7 blocks": ("for (int b = 0; b < 8; b++) md5_block(st, sector + 64 * b);",
                                     "for (int b = 0; b < 7; b++) md5_block(st, sector + 64 * b);"),
 }
@@ -90,9 +94,20 @@ def _signature_pins_pass() -> bool:
     return all(as_list(oracle.match_sig(image, files, sig)) == want for sig in (1, 2, 3))
 
 
+def _position_pins_pass() -> bool:
+    """The position-keyed pin: the definition's triples filtered by cluster position."""
+    image, files = tricky_case(2)
+    full = py_match(image.tobytes(), [f.tobytes() for f in files])
+    for base in (0, 3, 13):
+        want = [t for t in full if (t[0] - base) % 8 == t[2] % 8]
+        if as_list(oracle.match_position(image, files, base)) != want:
+            return False
+    return True
+
+
 def _pins_pass() -> bool:
     """The pins of tests/test_oracle.py, condensed; False as soon as one fails."""
-    if not _signature_pins_pass():
+    if not _signature_pins_pass() or not _position_pins_pass():
         return False
     rng = np.random.default_rng(5)
     for length in (0, 1, 55, 56, 63, 64, 100, 512, 1000):
