@@ -79,12 +79,24 @@ typedef struct cv_result cv_result; /* the results of one scan */
 #define CV_SIG_DJB2_64 2u    /* h = 5381; h = 33 h + byte, mod 2^64 (Eq. 1) */
 #define CV_SIG_CRC64 3u      /* remainder of M(x) x^64 mod x^64+x^4+x^3+x+1, MSB first, no init/final XOR */
 
+/* Table organisation (cv_master_opts.position_mode). Section 3.1 keeps one table S_tau per
+ * sector position tau (0..7) of an 8-sector cluster, so a disk sector only matches master
+ * sectors at its own position. CV_POSITION_CLUSTER builds that: a triple (i, f, s) is reported
+ * only when (i - base_offset) mod 8 == s mod 8, base_offset being cv_scan_opts.base_offset (the
+ * first sector of the partition whose clusters are meant; the paper counts from sector 0).
+ * CV_POSITION_ANY (the default) matches every position: one table over all sectors. */
+#define CV_POSITION_ANY 0u
+#define CV_POSITION_CLUSTER 1u
+
 typedef struct {
-  uint32_t struct_size;         /* sizeof(cv_master_opts) */
+  uint32_t struct_size;         /* sizeof(cv_master_opts); the size without position_mode and
+                                   reserved (24 bytes) is accepted and selects CV_POSITION_ANY */
   float max_load;               /* table load factor cap in (0, 0.9]; 0 selects 0.5 */
   uint32_t bloom_bits_per_key;  /* 0 = no Bloom prefilter; CV_BLOOM_AUTO = 16 */
   uint32_t signature;           /* CV_SIG_*; 0 = MD5 */
   void* stream;                 /* cudaStream_t */
+  uint32_t position_mode;       /* CV_POSITION_* */
+  uint32_t reserved;            /* 0 */
 } cv_master_opts;
 
 /* cv_scan_opts.flags */
@@ -97,6 +109,9 @@ typedef struct {
   uint64_t chunk_bytes;       /* host images are streamed in chunks of this size; 0 = 256 MiB */
   uint32_t kernel_config;     /* 0 = the tuned default; k + 1 selects configuration k */
   uint32_t reserved;
+  uint64_t base_offset;       /* position-keyed tables: disk sector of the first cluster (only its
+                                 value mod 8 matters); ignored for CV_POSITION_ANY tables. The
+                                 size without it (32 bytes) is accepted and means 0. */
 } cv_scan_opts;
 
 /* Kernel configurations of the scan (tile rows, ring stages, staging width). Every
@@ -115,10 +130,11 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
 
 typedef struct {
   uint32_t n_files;
-  uint32_t reserved;
+  uint32_t position_mode;    /* CV_POSITION_* of the table */
   uint64_t n_sectors;        /* whole master sectors */
   uint64_t n_kept;           /* after the exclusion rule */
-  uint64_t n_unique;         /* distinct digests among the kept sectors */
+  uint64_t n_unique;         /* distinct keys among the kept sectors: digests, or (digest, tau)
+                                pairs for position-keyed tables */
   uint64_t n_slots;          /* table slots (power of two) */
   uint64_t bloom_bytes;      /* 0 when there is no Bloom prefilter */
   uint32_t max_probe;        /* longest linear-probe run of any stored digest, plus one */
@@ -236,7 +252,9 @@ typedef struct {
   float scan_ms;              /* device time of the scan launch(es) of the last finished run */
 } cv_batch_info;
 
-/* Errors: CV_EINVAL (host or misaligned image, bad options), CV_ENOMEM, CV_ECUDA, CV_ENODEV. */
+/* With a position-keyed table (CV_POSITION_CLUSTER) every image's clusters are counted from its
+ * sector 0 (base_offset 0).
+ * Errors: CV_EINVAL (host or misaligned image, bad options), CV_ENOMEM, CV_ECUDA, CV_ENODEV. */
 int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images, const cv_batch_opts* opts,
                     cv_batch** out);
 /* One graph launch on stream; returns without waiting. */
@@ -280,7 +298,8 @@ typedef struct {
   double wall_s;                /* first submit to last completion */
 } cv_server_stats;
 
-/* Errors: CV_EINVAL, CV_ENOMEM, CV_ECUDA, CV_ENODEV. The master must outlive the server. */
+/* Errors: CV_EINVAL, CV_ENOMEM, CV_ECUDA, CV_ENODEV. The master must outlive the server. With a
+ * position-keyed table every request's clusters are counted from its sector 0. */
 int cv_server_create(const cv_master* m, const cv_server_opts* opts, cv_server** out);
 /* Queue one image (host memory, or device memory of the server's device), borrowed until its
  * result is polled. Never blocks on the GPU. *ticket identifies the request. */
@@ -308,7 +327,8 @@ int cv_server_get_stats(cv_server* s, cv_server_stats* st);
  * Runs on stream and returns after the work has finished. Every call shares the one scratch
  * array and finds the previous call's contents there; calls whose work could overlap on the
  * GPU must be serialized by the caller. The first call on a device performs a one-time set-up
- * (the array's device address, kernel attributes); make it before any stream capture.
+ * (the array's device address, kernel attributes); make it before any stream capture. With a
+ * position-keyed table the image's clusters are counted from its sector 0.
  * Errors: CV_EINVAL, CV_ERANGE, CV_ECUDA, CV_ETIMEOUT, CV_ECORRUPT, CV_ENODEV.
  */
 #define CV_NOALLOC_MAX_SECTORS (1u << 19)

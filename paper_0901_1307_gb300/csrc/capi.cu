@@ -12,6 +12,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -146,7 +147,11 @@ int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t
 int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts* opts, cv_master** out) {
   if (!out || (n_files && !files)) return CV_EINVAL;
   *out = nullptr;
-  if (opts && opts->struct_size < sizeof(cv_master_opts)) return CV_EINVAL;
+  if (opts && opts->struct_size < offsetof(cv_master_opts, position_mode)) return CV_EINVAL;
+  const uint32_t position_mode =
+      (opts && opts->struct_size >= sizeof(cv_master_opts)) ? opts->position_mode : CV_POSITION_ANY;
+  if (position_mode > CV_POSITION_CLUSTER) return CV_EINVAL;
+  const bool by_tau = position_mode == CV_POSITION_CLUSTER;
   float max_load = (opts && opts->max_load > 0.f) ? opts->max_load : 0.5f;
   if (!(max_load > 0.f && max_load <= 0.9f)) return CV_EINVAL;
   uint32_t bpk = opts ? opts->bloom_bits_per_key : CV_BLOOM_AUTO;
@@ -196,6 +201,8 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       CV_TRY(tmp.alloc(&vals2, M * 4));
       CV_TRY(tmp.alloc(&counters, 16));  // max_disp, n_kept, n_unique, status
       CV_TRY(tmp.alloc(&file_base_d, (n_files + 1) * 8));
+      uint8_t* tau = nullptr;  // per master sector cluster position (position-keyed tables)
+      if (by_tau) CV_TRY(tmp.alloc(&tau, std::max<uint64_t>(M, 1)));
       CV_CUDA(cudaMemsetAsync(owner, 0, n_slots * 4, stream));
       CV_CUDA(cudaMemsetAsync(cnt, 0, n_slots * 4, stream));
       CV_CUDA(cudaMemsetAsync(counters, 0, 16, stream));
@@ -221,7 +228,11 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
         CV_TRY(job.add(ctx, cfg, arena, M, 0, 0, false));
         CV_TRY(digest_job(ctx, cfg_i, sig, job, dig, trivial, counters + 3, stream, tmp));
         const unsigned g = grid_for(M, 256, ctx->sms);
-        insert_kernel<<<g, 256, 0, stream>>>(dig, trivial, M, owner, cnt, slot_of, mask, counters, counters + 1,
+        if (tau) {
+          tau_kernel<<<g, 256, 0, stream>>>(file_base_d, n_files, M, tau);
+          CV_CUDA(cudaGetLastError());
+        }
+        insert_kernel<<<g, 256, 0, stream>>>(dig, trivial, tau, M, owner, cnt, slot_of, mask, counters, counters + 1,
                                             counters + 3);
         CV_CUDA(cudaGetLastError());
         iota_kernel<<<g, 256, 0, stream>>>(vals, M);
@@ -241,8 +252,8 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
           std::swap(kin, kout);
           std::swap(vin, vout);
         }
-        fill_kernel<<<g, 256, 0, stream>>>(kin, vin, M, (uint32_t)n_slots, owner, cnt, dig, file_base_d, n_files,
-                                          (uint4*)m->slots, (uint2*)m->postings, counters + 2);
+        fill_kernel<<<g, 256, 0, stream>>>(kin, vin, M, (uint32_t)n_slots, owner, cnt, dig, tau, file_base_d,
+                                          n_files, (uint4*)m->slots, (uint2*)m->postings, counters + 2);
         CV_CUDA(cudaGetLastError());
         if (sig_is_weak(sig)) {
           // a copy of the kept master sectors in posting order, to confirm matches byte for byte
@@ -273,7 +284,10 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       m->tab.use_bloom = bpk ? 1u : 0u;
       m->tab.sig = (uint32_t)sig;
       m->tab.confirm = (const uint8_t*)m->confirm;
+      m->tab.tau_mask = by_tau ? 7u : 0u;
+      m->tab.tau_add = 0u;
       m->info.signature = (uint32_t)sig;
+      m->info.position_mode = position_mode;
       m->info.n_files = n_files;
       m->info.n_sectors = M;
       m->info.n_kept = hc[1];
@@ -351,7 +365,8 @@ int cv_master_get_info(const cv_master* m, cv_master_info* info) {
 int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const cv_scan_opts* opts, cv_result** out) {
   if (!m || m->magic != kMagicMaster || !out || (n_images && !images)) return CV_EINVAL;
   *out = nullptr;
-  if (opts && opts->struct_size < sizeof(cv_scan_opts)) return CV_EINVAL;
+  if (opts && opts->struct_size < offsetof(cv_scan_opts, base_offset)) return CV_EINVAL;
+  const uint64_t base_offset = (opts && opts->struct_size >= sizeof(cv_scan_opts)) ? opts->base_offset : 0u;
   const uint32_t flags = opts ? opts->flags : 0u;
   cudaStream_t stream = opts ? (cudaStream_t)opts->stream : nullptr;
   uint64_t chunk = (opts && opts->chunk_bytes) ? opts->chunk_bytes : (256ull << 20);
@@ -369,6 +384,8 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
   }
   const int sig = (int)m->tab.sig;
   const ScanCfg& cfg = scan_config_for(cfg_i, sig, &cfg_i);
+  TableView tab = m->tab;  // disk sector g sits at cluster position (g - base_offset) mod 8
+  tab.tau_add = (uint32_t)((8u - base_offset % 8u) % 8u);
   // With a 64-bit signature every candidate is confirmed against the disk sector's bytes after
   // the scan, so host images are copied whole to the device instead of streamed through a ring.
   Temps staging(ctx, stream);
@@ -471,7 +488,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         CV_CUDA(cudaMemcpyAsync(segs_d, job.segs.data(), nseg * sizeof(Segment), cudaMemcpyHostToDevice, stream));
         ScanParams p;
         memset(&p, 0, sizeof p);
-        p.tab = m->tab;
+        p.tab = tab;
         p.hit_rec = hit_rec;
         p.tile_nhit = tile_nhit;
         p.tile_ntrip = tile_ntrip;
@@ -516,7 +533,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         total = seg_off[nseg];
         if (total) {
           CV_CUDA(cudaMallocFromPoolAsync((void**)&r->dev_out, total * sizeof(MatchOut), ctx->pool, stream));
-          CV_CUDA((cudaError_t)launch_expand(cfg, hit_rec, tile_nhit, tile_off, n_out, segs_d, nseg32, m->tab,
+          CV_CUDA((cudaError_t)launch_expand(cfg, hit_rec, tile_nhit, tile_off, n_out, segs_d, nseg32, tab,
                                              r->dev_out, total, status, ctx->sms, stream));
           r->launches += 1;
         }

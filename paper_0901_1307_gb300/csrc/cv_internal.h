@@ -34,10 +34,11 @@ enum : int { kSigMd5 = 0, kSigMd5NoPad = 1, kSigDjb2 = 2, kSigCrc64 = 3 };
 __host__ __device__ constexpr bool sig_is_weak(int sig) { return sig == kSigDjb2 || sig == kSigCrc64; }
 
 // Device view of a master table.
-//   slots: 2 x uint4 per slot: {d0, d1, d2, d3} and {post_off, post_cnt, 0, 0}; post_cnt == 0
-//          marks an empty slot. The home slot of digest d is d0 & slot_mask (Eq. 3).
+//   slots: 2 x uint4 per slot: {d0, d1, d2, d3} and {post_off, post_cnt, tau, 0}; post_cnt == 0
+//          marks an empty slot. The home slot of digest d at position tau is
+//          tau_home(d0, tau) & slot_mask, d0 & slot_mask when tau = 0 (Eq. 3).
 //   postings: (file_id, file_sector) per kept master sector, grouped by slot, ascending.
-//   bloom: 8 u32 words (32 bytes) per block; block d3 & bloom_mask; in word j the bit
+//   bloom: 8 u32 words (32 bytes) per block; block tau_block(d3, tau) & bloom_mask; in word j the bit
 //          (d1 >> 5j) & 31 for j < 6, (d2 >> 5(j-6)) & 31 for j = 6, 7.
 //   confirm: for 64-bit signatures, the master sector bytes of posting q at confirm + 512 q.
 struct TableView {
@@ -50,8 +51,17 @@ struct TableView {
   uint32_t max_probe;  // no stored digest sits further than max_probe - 1 slots from home
   uint32_t use_bloom;
   uint32_t sig;        // kSig* of the table
-  uint32_t pad;
+  uint32_t tau_mask;   // 7 for position-keyed tables (S_tau), 0 for one table over all positions
+  uint32_t tau_add;    // (8 - base_offset mod 8) mod 8: disk sector g sits at position (g + tau_add) & 7
+  uint32_t pad[3];
 };
+
+// Position-keyed tables (Section 3.1: one table S_tau per sector position tau of an 8-sector
+// cluster) are stored as one open-addressing table whose key is (signature, tau): tau moves the
+// home slot and the Bloom block and is stored in the slot's third value word. tau = 0 leaves both
+// unchanged, so a table over all positions is the same layout with every tau 0.
+__host__ __device__ inline uint32_t tau_home(uint32_t d0, uint32_t tau) { return d0 ^ (tau * 0x9E3779B9u); }
+__host__ __device__ inline uint32_t tau_block(uint32_t d3, uint32_t tau) { return d3 ^ (tau * 0x85EBCA6Bu); }
 
 // The four table words of a 64-bit signature h: h itself (low word first, so the home slot is
 // given by the signature's least significant bits, Eq. 3) and a SplitMix64-style finalizer of h

@@ -97,8 +97,9 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
 }
 
 // Blocked Bloom test: all eight bits of the digest's block set.
-__device__ __forceinline__ bool bloom_test(const TableView& tab, uint32_t d1, uint32_t d2, uint32_t d3) {
-  const uint4* blk = tab.bloom + 2ull * (d3 & tab.bloom_mask);
+__device__ __forceinline__ bool bloom_test(const TableView& tab, uint32_t d1, uint32_t d2, uint32_t d3,
+                                           uint32_t tau) {
+  const uint4* blk = tab.bloom + 2ull * (tau_block(d3, tau) & tab.bloom_mask);
   uint4 lo = __ldg(blk);
   uint4 hi = __ldg(blk + 1);
   uint32_t m = (lo.x >> (d1 & 31)) & (lo.y >> ((d1 >> 5) & 31)) & (lo.z >> ((d1 >> 10) & 31)) &
@@ -107,17 +108,17 @@ __device__ __forceinline__ bool bloom_test(const TableView& tab, uint32_t d1, ui
   return (m & 1u) != 0;
 }
 
-// Linear probing from the home slot (Eq. 3) until the digest or an empty slot is found, never
-// beyond the table's probe bound. Returns post_cnt (0: not present) and post_off.
+// Linear probing from the home slot (Eq. 3) until the key (digest, tau) or an empty slot is
+// found, never beyond the table's probe bound. Returns post_cnt (0: not present) and post_off.
 __device__ __forceinline__ uint32_t table_probe(const TableView& tab, uint32_t d0, uint32_t d1, uint32_t d2,
-                                                uint32_t d3, uint32_t& post_off) {
-  uint32_t idx = d0 & tab.slot_mask;
+                                                uint32_t d3, uint32_t tau, uint32_t& post_off) {
+  uint32_t idx = tau_home(d0, tau) & tab.slot_mask;
   for (uint32_t c = 0; c < tab.max_probe; c++) {
     const uint4* s = tab.slots + 2ull * idx;
     uint4 key = __ldg(s);
     uint4 val = __ldg(s + 1);
     if (val.y == 0u) return 0u;
-    if (key.x == d0 && key.y == d1 && key.z == d2 && key.w == d3) {
+    if (key.x == d0 && key.y == d1 && key.z == d2 && key.w == d3 && val.z == tau) {
       post_off = val.x;
       return val.y;
     }
@@ -360,8 +361,10 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
         }
       } else {
         uint32_t post_off = 0, post_cnt = 0;
-        if (valid && (!p.tab.use_bloom || bloom_test(p.tab, st[k][1], st[k][2], st[k][3])))
-          post_cnt = table_probe(p.tab, st[k][0], st[k][1], st[k][2], st[k][3], post_off);
+        // the disk sector's position in its cluster (0 for a table over all positions)
+        const uint32_t tau = (uint32_t)(seg.sector_base + r + p.tab.tau_add) & p.tab.tau_mask;
+        if (valid && (!p.tab.use_bloom || bloom_test(p.tab, st[k][1], st[k][2], st[k][3], tau)))
+          post_cnt = table_probe(p.tab, st[k][0], st[k][1], st[k][2], st[k][3], tau, post_off);
         // triples this sector emits: every posting, or for a 64-bit signature the postings whose
         // master sector equals this sector byte for byte
         uint32_t n_emit = post_cnt;

@@ -11,6 +11,8 @@
 //   fill     the sorted pairs become the postings; the first pair of each run writes its
 //            slot {digest, post_off, post_cnt}.
 //   bloom    every occupied slot sets its 8 bits in the blocked Bloom filter.
+// Position-keyed tables (one S_tau per cluster position, Section 3.1) key every slot by
+// (digest, tau) with tau = file_sector mod 8; the steps are the same.
 // Which slot a digest lands in depends on thread timing; the lookup result does not.
 #pragma once
 #include <stdint.h>
@@ -19,9 +21,25 @@
 
 namespace cvk {
 
-__global__ void insert_kernel(const uint4* dig, const uint8_t* trivial, uint64_t n, uint32_t* owner, uint32_t* cnt,
-                              uint32_t* slot_of, uint32_t mask, uint32_t* max_disp, uint32_t* n_kept,
-                              uint32_t* status) {
+// Position of every master sector in its file's clusters: tau[m] = file_sector mod 8, the
+// file found by binary search of file_base (n_files + 1 entries: first master index of every
+// file, then the total).
+__global__ void tau_kernel(const uint64_t* file_base, uint32_t n_files, uint64_t n, uint8_t* tau) {
+  for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = n_files;  // largest f with file_base[f] <= m
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (file_base[mid] <= m) lo = mid; else hi = mid;
+    }
+    tau[m] = (uint8_t)((m - file_base[lo]) & 7u);
+  }
+}
+
+// tau: per master sector position (position-keyed tables), or null for one table over all
+// positions (every tau 0). The key is (digest, tau).
+__global__ void insert_kernel(const uint4* dig, const uint8_t* trivial, const uint8_t* tau, uint64_t n,
+                              uint32_t* owner, uint32_t* cnt, uint32_t* slot_of, uint32_t mask, uint32_t* max_disp,
+                              uint32_t* n_kept, uint32_t* status) {
   const uint32_t none = mask + 1u;
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (uint64_t)gridDim.x * blockDim.x) {
     if (trivial[m]) {
@@ -29,7 +47,8 @@ __global__ void insert_kernel(const uint4* dig, const uint8_t* trivial, uint64_t
       continue;
     }
     const uint4 d = dig[m];
-    uint32_t idx = d.x & mask;
+    const uint32_t t = tau ? tau[m] : 0u;
+    uint32_t idx = tau_home(d.x, t) & mask;
     uint32_t c = 0;
     bool placed = false;
     for (; c <= mask; c++) {
@@ -39,7 +58,8 @@ __global__ void insert_kernel(const uint4* dig, const uint8_t* trivial, uint64_t
         break;
       }
       const uint4 e = dig[prev - 1u];
-      if (e.x == d.x && e.y == d.y && e.z == d.z && e.w == d.w) {
+      const uint32_t te = tau ? tau[prev - 1u] : 0u;
+      if (e.x == d.x && e.y == d.y && e.z == d.z && e.w == d.w && te == t) {
         placed = true;
         break;
       }
@@ -160,8 +180,9 @@ __global__ void __launch_bounds__(kRsThreads) rs_scatter_kernel(const uint32_t* 
 // Sorted (slot, master index) pairs -> postings and slot records. file_base has n_files + 1
 // entries: the first master index of every file, then the total.
 __global__ void fill_kernel(const uint32_t* keys, const uint32_t* vals, uint64_t n, uint32_t n_slots,
-                            const uint32_t* owner, const uint32_t* cnt, const uint4* dig, const uint64_t* file_base,
-                            uint32_t n_files, uint4* slots, uint2* postings, uint32_t* n_unique) {
+                            const uint32_t* owner, const uint32_t* cnt, const uint4* dig, const uint8_t* tau,
+                            const uint64_t* file_base, uint32_t n_files, uint4* slots, uint2* postings,
+                            uint32_t* n_unique) {
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t key = keys[q];
     if (key >= n_slots) continue;
@@ -173,8 +194,9 @@ __global__ void fill_kernel(const uint32_t* keys, const uint32_t* vals, uint64_t
     }
     postings[q] = make_uint2(lo, (uint32_t)(m - file_base[lo]));
     if (q == 0 || keys[q - 1] != key) {
-      slots[2ull * key] = dig[owner[key] - 1u];
-      slots[2ull * key + 1] = make_uint4((uint32_t)q, cnt[key], 0u, 0u);
+      const uint32_t o = owner[key] - 1u;
+      slots[2ull * key] = dig[o];
+      slots[2ull * key + 1] = make_uint4((uint32_t)q, cnt[key], tau ? (uint32_t)tau[o] : 0u, 0u);
       atomicAdd(n_unique, 1u);
     }
   }
@@ -198,7 +220,7 @@ __global__ void bloom_kernel(const uint4* slots, uint32_t n_slots, uint32_t* blo
     const uint4 val = slots[2ull * i + 1];
     if (val.y == 0u) continue;
     const uint4 d = slots[2ull * i];
-    uint32_t* blk = bloom + 8ull * (d.w & bloom_mask);
+    uint32_t* blk = bloom + 8ull * (tau_block(d.w, val.z) & bloom_mask);
     atomicOr(blk + 0, 1u << (d.y & 31));
     atomicOr(blk + 1, 1u << ((d.y >> 5) & 31));
     atomicOr(blk + 2, 1u << ((d.y >> 10) & 31));

@@ -29,6 +29,7 @@ CV_ERANGE = -8
 CV_BLOOM_AUTO = 0xFFFFFFFF
 CV_SIG_MD5, CV_SIG_MD5_NOPAD, CV_SIG_DJB2_64, CV_SIG_CRC64 = 0, 1, 2, 3
 CV_KEEP_ON_DEVICE = 1
+CV_POSITION_ANY, CV_POSITION_CLUSTER = 0, 1
 SECTOR = 512
 
 MATCH_DTYPE = np.dtype([("disk_sector", "<u8"), ("file_id", "<u4"), ("file_sector", "<u4")])
@@ -56,16 +57,18 @@ class cv_buf(ctypes.Structure):
 
 class cv_master_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("max_load", ctypes.c_float),
-                ("bloom_bits_per_key", ctypes.c_uint32), ("signature", ctypes.c_uint32), ("stream", ctypes.c_void_p)]
+                ("bloom_bits_per_key", ctypes.c_uint32), ("signature", ctypes.c_uint32), ("stream", ctypes.c_void_p),
+                ("position_mode", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class cv_scan_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("stream", ctypes.c_void_p),
-                ("chunk_bytes", ctypes.c_uint64), ("kernel_config", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("chunk_bytes", ctypes.c_uint64), ("kernel_config", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("base_offset", ctypes.c_uint64)]
 
 
 class cv_master_info(ctypes.Structure):
-    _fields_ = [("n_files", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("n_sectors", ctypes.c_uint64),
+    _fields_ = [("n_files", ctypes.c_uint32), ("position_mode", ctypes.c_uint32), ("n_sectors", ctypes.c_uint64),
                 ("n_kept", ctypes.c_uint64), ("n_unique", ctypes.c_uint64), ("n_slots", ctypes.c_uint64),
                 ("bloom_bytes", ctypes.c_uint64), ("max_probe", ctypes.c_uint32), ("signature", ctypes.c_uint32),
                 ("device_bytes", ctypes.c_uint64)]
@@ -318,10 +321,12 @@ class Result:
 
 
 def master_build(files, max_load: float = 0.0, bloom_bits_per_key: int = CV_BLOOM_AUTO, stream=None,
-                 signature: int = CV_SIG_MD5) -> Master:
-    """cv_master_build: the signature table of a list of master files."""
+                 signature: int = CV_SIG_MD5, position_mode: int = CV_POSITION_ANY) -> Master:
+    """cv_master_build: the signature table of a list of master files (one table over all sector
+    positions, or with position_mode=CV_POSITION_CLUSTER the tables S_tau of Section 3.1)."""
     arr, keep = _bufs(list(files))
-    o = cv_master_opts(ctypes.sizeof(cv_master_opts), max_load, bloom_bits_per_key, signature, _stream(stream))
+    o = cv_master_opts(ctypes.sizeof(cv_master_opts), max_load, bloom_bits_per_key, signature, _stream(stream),
+                       position_mode, 0)
     h = ctypes.c_void_p()
     _check(load().cv_master_build(arr, len(files), ctypes.byref(o), ctypes.byref(h)), "cv_master_build")
     del keep
@@ -335,12 +340,13 @@ def kernel_configs() -> list:
 
 
 def scan(master: Master, images, keep_on_device: bool = False, stream=None, chunk_bytes: int = 0,
-         kernel_config: int = 0) -> Result:
-    """cv_scan: every match of every image against the master table."""
+         kernel_config: int = 0, base_offset: int = 0) -> Result:
+    """cv_scan: every match of every image against the master table. base_offset: the disk sector
+    where clusters start, for position-keyed tables."""
     images = list(images)
     arr, keep = _bufs(images)
     o = cv_scan_opts(ctypes.sizeof(cv_scan_opts), CV_KEEP_ON_DEVICE if keep_on_device else 0, _stream(stream),
-                     chunk_bytes, kernel_config, 0)
+                     chunk_bytes, kernel_config, 0, base_offset)
     h = ctypes.c_void_p()
     _check(load().cv_scan(master.handle, arr, len(images), ctypes.byref(o), ctypes.byref(h)), "cv_scan")
     del keep

@@ -62,3 +62,56 @@ def test_no_cpu_path_without_gpu(lib):
     with pytest.raises(cv.CVError) as e:
         cv.master_build([bytes(1024)])
     assert e.value.code == cv.CV_ENODEV
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets the C compiler gives
+    the header's struct (a field added to one side only shows up here)."""
+    from paper_0901_1307_gb300 import cv
+
+    structs = [n for n in dir(cv) if n.startswith("cv_") and isinstance(getattr(cv, n), type)
+               and issubclass(getattr(cv, n), ctypes.Structure)]
+    assert {"cv_master_opts", "cv_scan_opts", "cv_master_info", "cv_batch_opts", "cv_server_opts"} <= set(structs)
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cv.h"', "int main(void) {"]
+    for n in structs:
+        lines.append(f'  printf("{n} %zu\\n", sizeof({n}));')
+        for f, _ in getattr(cv, n)._fields_:
+            lines.append(f'  printf("{n}.{f} %zu\\n", offsetof({n}, {f}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                        text=True).stdout.splitlines())
+    for n in structs:
+        st = getattr(cv, n)
+        assert int(got[n]) == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert int(got[f"{n}.{f}"]) == getattr(st, f).offset, f"{n}.{f}"
+
+
+def test_master_options_checked_before_the_device(lib):
+    """Option validation is host logic: without a GPU a well-formed request gets CV_ENODEV and a
+    malformed one CV_EINVAL (struct too small, unknown position mode or signature)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_0901_1307_gb300 import cv
+
+    h = ctypes.c_void_p()
+
+    def build(size, position_mode=0, signature=0):
+        o = cv.cv_master_opts(size, 0.0, 0, signature, None, position_mode, 0)
+        return lib.cv_master_build(None, 0, ctypes.byref(o), ctypes.byref(h))
+
+    full = ctypes.sizeof(cv.cv_master_opts)
+    assert build(full) == cv.CV_ENODEV
+    assert build(full, position_mode=cv.CV_POSITION_CLUSTER) == cv.CV_ENODEV
+    assert build(24) == cv.CV_ENODEV                   # the size before position_mode existed
+    assert build(24, position_mode=7) == cv.CV_ENODEV  # not read at that size
+    assert build(20) == cv.CV_EINVAL
+    assert build(full, position_mode=2) == cv.CV_EINVAL
+    assert build(full, signature=4) == cv.CV_EINVAL
