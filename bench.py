@@ -235,6 +235,29 @@ def expected_window(expect: np.ndarray, a: int, n: int) -> np.ndarray:
 def run_signatures(torch, cv, synth, plan, image, stream, steps):
     """The same device-resident scan with the paper's other signatures: MD5 without padding,
     djb2-64 and CRC64 (64-bit ones confirmed byte for byte on the device)."""
+    masters, files = device_masters(torch, plan)
+    out = {}
+    ref_matches = None
+    for sig, name in ((0, "md5"), (1, "md5_nopad"), (2, "djb2_64"), (3, "crc64")):
+        m = cv.master_build(files, signature=sig)
+        wall, kms, matches = time_scans(torch, cv, m, image, stream, steps)
+        ref_matches = matches if ref_matches is None else ref_matches
+        out[name] = {"GBps": plan.n_bytes / wall / 1e9, "kernel_GBps": plan.n_bytes / (kms * 1e-3) / 1e9,
+                     "matches": matches, "same_matches_as_md5": matches == ref_matches}
+        m.close()
+    # the paper's position-keyed tables S_tau on the same image (clusters from sector 0)
+    m = cv.master_build(files, position_mode=cv.CV_POSITION_CLUSTER)
+    wall, kms, matches = time_scans(torch, cv, m, image, stream, steps)
+    out["md5_position_tau"] = {"GBps": plan.n_bytes / wall / 1e9, "kernel_GBps": plan.n_bytes / (kms * 1e-3) / 1e9,
+                               "matches": matches}
+    m.close()
+    del masters
+    torch.cuda.synchronize()
+    return out
+
+
+def device_masters(torch, plan):
+    """The plan's master files generated on the device: (arena tensor, [(ptr, bytes)] per file)."""
     base = plan.file_base()
     base_d = torch.from_numpy(base.view(np.uint8).copy()).cuda()
     masters = torch.empty(plan.n_master_sectors * SECTOR, dtype=torch.uint8, device="cuda")
@@ -242,27 +265,51 @@ def run_signatures(torch, cv, synth, plan, image, stream, steps):
     torch.cuda.synchronize()
     files = [(masters.data_ptr() + int(base[f]) * SECTOR, int(plan.file_nsect[f]) * SECTOR)
              for f in range(plan.n_files)]
+    return masters, files
+
+
+def time_scans(torch, cv, m, image, stream, steps):
+    """Mean wall and kernel time of `steps` device-resident scans (after 3 untimed ones)."""
+    for _ in range(3):
+        cv.scan(m, [image], keep_on_device=True, stream=stream).close()
+    kms, matches = [], 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        r = cv.scan(m, [image], keep_on_device=True, stream=stream)
+        st = r.stats()
+        kms.append(st["kernel_ms"])
+        matches = st["matches"]
+        r.close()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / steps, statistics.mean(kms), matches
+
+
+def run_tables(torch, cv, synth, plan, image, stream, steps):
+    """Throughput against table occupancy (as the paper plots it for CRC64 and djb2), for the
+    linear-probing hash table and the sorted table searched by bisection, with and without the
+    Bloom filter. Occupancy is set by the number of master sectors in a 2^22-slot table: a
+    prefix of the master files holding about occ x 2^22 sectors."""
+    masters, files = device_masters(torch, plan)
+    cum = np.cumsum(plan.file_nsect.astype(np.int64))
+    slots = 1 << 22
     out = {}
-    ref_matches = None
-    for sig, name in ((0, "md5"), (1, "md5_nopad"), (2, "djb2_64"), (3, "crc64")):
-        m = cv.master_build(files, signature=sig)
-        for _ in range(3):
-            cv.scan(m, [image], keep_on_device=True, stream=stream).close()
-        kms, matches = [], 0
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            r = cv.scan(m, [image], keep_on_device=True, stream=stream)
-            st = r.stats()
-            kms.append(st["kernel_ms"])
-            matches = st["matches"]
-            r.close()
-        torch.cuda.synchronize()
-        wall = (time.perf_counter() - t0) / steps
-        ref_matches = matches if ref_matches is None else ref_matches
-        out[name] = {"GBps": plan.n_bytes / wall / 1e9, "kernel_GBps": plan.n_bytes / (statistics.mean(kms) * 1e-3) / 1e9,
-                     "matches": matches, "same_matches_as_md5": matches == ref_matches}
-        m.close()
+    for occ in (0.25, 0.5, 0.75, 0.9):
+        k = max(int(np.searchsorted(cum, occ * (slots - 1) * 0.999, side="right")), 1)
+        sub = files[:k]
+        # the load cap that sizes the table at exactly 2^22 slots for these sectors
+        max_load = min(0.9, float(cum[k - 1]) / (slots * 0.9999))
+        for layout, lname in ((0, "hash"), (1, "sorted")):
+            for bloom in (0, 16):
+                m = cv.master_build(sub, max_load=max_load, layout=layout, bloom_bits_per_key=bloom)
+                info = m.info()
+                wall, kms, matches = time_scans(torch, cv, m, image, stream, steps)
+                out[f"occ{occ}_{lname}_{'bloom' if bloom else 'nobloom'}"] = {
+                    "occupancy": info["n_unique"] / max(info["n_slots"], 1), "n_slots": info["n_slots"],
+                    "master_sectors": int(cum[k - 1]),
+                    "max_probe_or_steps": info["max_probe"], "GBps": plan.n_bytes / wall / 1e9,
+                    "kernel_GBps": plan.n_bytes / (kms * 1e-3) / 1e9, "matches": matches}
+                m.close()
     del masters
     torch.cuda.synchronize()
     return out
@@ -412,6 +459,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-sigs", action="store_true")
     ap.add_argument("--sig-steps", type=int, default=20)
+    ap.add_argument("--no-tables", action="store_true")
+    ap.add_argument("--table-steps", type=int, default=10)
     ap.add_argument("--batch-images", type=int, default=512)
     ap.add_argument("--batch-total-gib", type=int, default=64)
     ap.add_argument("--batch-density", type=float, default=0.01)
@@ -479,6 +528,9 @@ def main():
     sigs = None
     if not args.no_sigs:
         sigs = run_signatures(torch, cv, synth, plan, image, stream, args.sig_steps)
+    tables = None
+    if not args.no_tables:
+        tables = run_tables(torch, cv, synth, plan, image, stream, args.table_steps)
 
     # end to end through the C ABI from pinned host memory
     e2e = None
@@ -538,6 +590,7 @@ def main():
         "clocks": clocks,
         "e2e": e2e,
         "signatures": sigs,
+        "tables": tables,
         "gpu_launches": launches,
     }
     master.close()

@@ -88,15 +88,25 @@ typedef struct cv_result cv_result; /* the results of one scan */
 #define CV_POSITION_ANY 0u
 #define CV_POSITION_CLUSTER 1u
 
+/* Table layout (cv_master_opts.layout); results do not depend on it.
+ * CV_LAYOUT_HASH: open addressing with linear probing from the slot given by the signature's
+ *   low bits (Section 3.1, Eq. 3); slots = next power of two above n_kept / max_load.
+ * CV_LAYOUT_SORTED: the distinct keys in one array sorted by their first word, searched by
+ *   binary search (Section 4 proposes it for high occupancy, after Dandass): every slot is
+ *   used, and a lookup costs ceil(log2 n_unique) dependent reads whatever the occupancy. */
+#define CV_LAYOUT_HASH 0u
+#define CV_LAYOUT_SORTED 1u
+
 typedef struct {
   uint32_t struct_size;         /* sizeof(cv_master_opts); the size without position_mode and
-                                   reserved (24 bytes) is accepted and selects CV_POSITION_ANY */
+                                   layout (24 bytes) is accepted and selects CV_POSITION_ANY and
+                                   CV_LAYOUT_HASH */
   float max_load;               /* table load factor cap in (0, 0.9]; 0 selects 0.5 */
   uint32_t bloom_bits_per_key;  /* 0 = no Bloom prefilter; CV_BLOOM_AUTO = 16 */
   uint32_t signature;           /* CV_SIG_*; 0 = MD5 */
   void* stream;                 /* cudaStream_t */
   uint32_t position_mode;       /* CV_POSITION_* */
-  uint32_t reserved;            /* 0 */
+  uint32_t layout;              /* CV_LAYOUT_*; read only together with position_mode */
 } cv_master_opts;
 
 /* cv_scan_opts.flags */
@@ -135,11 +145,14 @@ typedef struct {
   uint64_t n_kept;           /* after the exclusion rule */
   uint64_t n_unique;         /* distinct keys among the kept sectors: digests, or (digest, tau)
                                 pairs for position-keyed tables */
-  uint64_t n_slots;          /* table slots (power of two) */
+  uint64_t n_slots;          /* table slots (hash layout: a power of two; sorted: n_unique) */
   uint64_t bloom_bytes;      /* 0 when there is no Bloom prefilter */
-  uint32_t max_probe;        /* longest linear-probe run of any stored digest, plus one */
+  uint32_t max_probe;        /* hash layout: longest linear-probe run of any stored digest,
+                                plus one; sorted layout: binary-search steps, ceil(log2 n_unique) */
   uint32_t signature;        /* CV_SIG_* of the table */
   uint64_t device_bytes;     /* device memory the handle holds */
+  uint32_t layout;           /* CV_LAYOUT_* of the table */
+  uint32_t reserved;
 } cv_master_info;
 
 int cv_master_get_info(const cv_master* m, cv_master_info* info);

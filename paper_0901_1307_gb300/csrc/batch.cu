@@ -100,7 +100,9 @@ int enqueue_run(DevCtx* ctx, int cfg_i, const TableView& tab, const Job& job, co
 std::mutex g_tune_mutex;
 std::map<std::string, std::pair<int, int>> g_tune;  // key -> (config, bloom)
 
-std::string tune_key(const char* gpu, int sms, uint64_t sectors, uint32_t images, uint64_t unique, bool bloom_avail) {
+// table_kind: signature, layout and position keying of the table (they change the probe's cost).
+std::string tune_key(const char* gpu, int sms, uint64_t sectors, uint32_t images, uint64_t unique, bool bloom_avail,
+                     uint32_t table_kind) {
   auto lg = [](uint64_t x) {
     int b = 0;
     while (x > 1) {
@@ -110,7 +112,8 @@ std::string tune_key(const char* gpu, int sms, uint64_t sectors, uint32_t images
     return b;
   };
   char buf[256];
-  snprintf(buf, sizeof buf, "%s|%d|s%d|i%d|u%d|b%d", gpu, sms, lg(sectors), lg(images), lg(unique), bloom_avail ? 1 : 0);
+  snprintf(buf, sizeof buf, "%s|%d|s%d|i%d|u%d|b%d|t%u", gpu, sms, lg(sectors), lg(images), lg(unique),
+           bloom_avail ? 1 : 0, table_kind);
   return buf;
 }
 
@@ -210,7 +213,7 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
     if (opts->kernel_config > (uint32_t)ncfg) return CV_EINVAL;
     cfg_i = (int)opts->kernel_config - 1;
   }
-  scan_config_for(cfg_i, (int)tab.sig, &cfg_i);
+  scan_config_for(cfg_i, table_kind(tab), &cfg_i);
   if (opts && opts->bloom == CV_BATCH_BLOOM_OFF) bloom = 0;
 
   cv_batch* b = new (std::nothrow) cv_batch();
@@ -248,8 +251,9 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
     if (opts && opts->autotune && total_sectors) {
       cudaDeviceProp prop;
       CV_CUDA(cudaGetDeviceProperties(&prop, ctx->dev));
-      const uint64_t unique = (uint64_t)tab.slot_mask + 1;
-      const std::string key = tune_key(prop.name, ctx->sms, total_sectors, n_images, unique, bloom_avail);
+      const uint64_t unique = tab.layout == kLayoutSorted ? tab.n_keys : (uint64_t)tab.slot_mask + 1;
+      const uint32_t tkey = (uint32_t)table_kind(tab) * 2u + (tab.tau_mask ? 1u : 0u);
+      const std::string key = tune_key(prop.name, ctx->sms, total_sectors, n_images, unique, bloom_avail, tkey);
       int tc, tb;
       if (tune_lookup(key, opts->tune_cache, &tc, &tb)) {
         cfg_i = tc;
@@ -257,7 +261,7 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
       } else {
         float best = 1e30f;
         for (int k = 0; k < ncfg && k < 64; k++) {
-          if (!cfgs[k].scan_fn[tab.sig]) continue;  // not built for this signature
+          if (!cfgs[k].scan_fn[table_kind(tab)]) continue;  // not built for this table kind
           Job job;
           std::vector<size_t> first;
           CV_TRY(build_job(k, &job, &first));

@@ -45,6 +45,7 @@ struct cv_master {
   void* postings;
   void* bloom;
   void* confirm;  // kept master sectors in posting order (64-bit signatures)
+  void* keys0;    // sorted layout: h0 of every record
   cv_master_info info;
 };
 
@@ -144,6 +145,27 @@ int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t
   return digest_job(ctx, cfg_i, kSigMd5, job, (uint4*)digests, trivial, status, stream, tmp);
 }
 
+// Stable LSD radix sort of n (key, value) pairs by the low `bits` bits of the key, 8 bits per
+// pass, ping-ponging between (k0, v0) and (k1, v1); *kres/*vres receive the pair holding the
+// result.
+static int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint64_t n, int bits, Temps& tmp,
+                            cudaStream_t stream, uint32_t** kres, uint32_t** vres) {
+  const uint32_t nb = (uint32_t)((n + kRsChunk - 1) / kRsChunk);
+  uint32_t* hist;
+  CV_TRY(tmp.alloc(&hist, (uint64_t)std::max<uint32_t>(nb, 1) * 256 * 4));
+  for (int shift = 0; shift < bits && n; shift += 8) {
+    rs_hist_kernel<<<nb, kRsThreads, 0, stream>>>(k0, n, shift, hist, nb);
+    exclusive_scan_u32_kernel<<<1, 1024, 0, stream>>>(hist, (uint64_t)nb * 256);
+    rs_scatter_kernel<<<nb, kRsThreads, 0, stream>>>(k0, v0, k1, v1, n, shift, hist, nb);
+    CV_CUDA(cudaGetLastError());
+    std::swap(k0, k1);
+    std::swap(v0, v1);
+  }
+  *kres = k0;
+  *vres = v0;
+  return CV_OK;
+}
+
 int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts* opts, cv_master** out) {
   if (!out || (n_files && !files)) return CV_EINVAL;
   *out = nullptr;
@@ -152,6 +174,8 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       (opts && opts->struct_size >= sizeof(cv_master_opts)) ? opts->position_mode : CV_POSITION_ANY;
   if (position_mode > CV_POSITION_CLUSTER) return CV_EINVAL;
   const bool by_tau = position_mode == CV_POSITION_CLUSTER;
+  const uint32_t layout = (opts && opts->struct_size >= sizeof(cv_master_opts)) ? opts->layout : CV_LAYOUT_HASH;
+  if (layout > CV_LAYOUT_SORTED) return CV_EINVAL;
   float max_load = (opts && opts->max_load > 0.f) ? opts->max_load : 0.5f;
   if (!(max_load > 0.f && max_load <= 0.9f)) return CV_EINVAL;
   uint32_t bpk = opts ? opts->bloom_bits_per_key : CV_BLOOM_AUTO;
@@ -240,18 +264,8 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
         // stable LSD radix sort of (slot_of, m) by slot_of; keys <= n_slots
         int bits = 1;
         while ((1ull << bits) <= n_slots) bits++;
-        const uint32_t nb = (uint32_t)((M + kRsChunk - 1) / kRsChunk);
-        uint32_t* hist;
-        CV_TRY(tmp.alloc(&hist, (uint64_t)nb * 256 * 4));
-        uint32_t *kin = slot_of, *vin = vals, *kout = keys2, *vout = vals2;
-        for (int shift = 0; shift < bits; shift += 8) {
-          rs_hist_kernel<<<nb, kRsThreads, 0, stream>>>(kin, M, shift, hist, nb);
-          exclusive_scan_u32_kernel<<<1, 1024, 0, stream>>>(hist, (uint64_t)nb * 256);
-          rs_scatter_kernel<<<nb, kRsThreads, 0, stream>>>(kin, vin, kout, vout, M, shift, hist, nb);
-          CV_CUDA(cudaGetLastError());
-          std::swap(kin, kout);
-          std::swap(vin, vout);
-        }
+        uint32_t *kin, *vin;
+        CV_TRY(radix_sort_pairs(slot_of, vals, keys2, vals2, M, bits, tmp, stream, &kin, &vin));
         fill_kernel<<<g, 256, 0, stream>>>(kin, vin, M, (uint32_t)n_slots, owner, cnt, dig, tau, file_base_d,
                                           n_files, (uint4*)m->slots, (uint2*)m->postings, counters + 2);
         CV_CUDA(cudaGetLastError());
@@ -275,7 +289,41 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       if (hc[3] & kStTableFull) return CV_ETABLEFULL;
       if (hc[3] & kStTimeout) return CV_ETIMEOUT;
       if (hc[3]) return CV_ECORRUPT;
+      uint32_t steps = 0;  // binary-search steps of the sorted layout
+      if (layout == CV_LAYOUT_SORTED) {
+        // the occupied slots, compacted in slot order, sorted by h0 (stable: deterministic)
+        const uint32_t nu = hc[2];
+        uint32_t *ck, *cv, *ck2, *cv2, *kr, *vr;
+        CV_TRY(tmp.alloc(&ck, n_slots * 4));
+        CV_TRY(tmp.alloc(&cv, n_slots * 4));
+        CV_TRY(tmp.alloc(&ck2, n_slots * 4));
+        CV_TRY(tmp.alloc(&cv2, n_slots * 4));
+        const unsigned gs = grid_for(n_slots, 256, ctx->sms);
+        occupied_keys_kernel<<<gs, 256, 0, stream>>>((const uint4*)m->slots, (uint32_t)n_slots, ck, cv);
+        CV_CUDA(cudaGetLastError());
+        CV_TRY(radix_sort_pairs(ck, cv, ck2, cv2, n_slots, 1, tmp, stream, &kr, &vr));
+        uint32_t* kfree = kr == ck ? ck2 : ck;  // the other key buffer is free for the h0 keys
+        uint32_t* vfree = vr == cv ? cv2 : cv;
+        const unsigned gu = grid_for(std::max<uint32_t>(nu, 1), 256, ctx->sms);
+        h0_keys_kernel<<<gu, 256, 0, stream>>>((const uint4*)m->slots, vr, nu, kfree);
+        CV_CUDA(cudaGetLastError());
+        uint32_t *hk, *hv;
+        CV_TRY(radix_sort_pairs(kfree, vr, kr, vfree, nu, 32, tmp, stream, &hk, &hv));
+        void* sorted_slots = nullptr;
+        CV_CUDA(cudaMalloc(&sorted_slots, std::max<uint64_t>(nu, 1) * 32));
+        CV_CUDA(cudaMalloc(&m->keys0, std::max<uint64_t>(nu, 1) * 4));
+        gather_slots_kernel<<<gu, 256, 0, stream>>>((const uint4*)m->slots, hv, nu, (uint4*)sorted_slots);
+        CV_CUDA(cudaGetLastError());
+        if (nu) CV_CUDA(cudaMemcpyAsync(m->keys0, hk, (uint64_t)nu * 4, cudaMemcpyDeviceToDevice, stream));
+        CV_CUDA(cudaStreamSynchronize(stream));
+        cudaFree(m->slots);
+        m->slots = sorted_slots;
+        while ((1ull << steps) < nu) steps++;
+      }
       m->tab.slots = (const uint4*)m->slots;
+      m->tab.keys0 = (const uint32_t*)m->keys0;
+      m->tab.layout = layout;
+      m->tab.n_keys = hc[2];
       m->tab.postings = (const uint2*)m->postings;
       m->tab.bloom = (const uint4*)m->bloom;
       m->tab.slot_mask = mask;
@@ -294,8 +342,12 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       m->info.n_unique = hc[2];
       m->info.n_slots = n_slots;
       m->info.bloom_bytes = n_blocks * 32;
-      m->info.max_probe = hc[0] + 1;
-      m->info.device_bytes = n_slots * 32 + std::max<uint64_t>(M, 1) * 8 + n_blocks * 32 +
+      m->info.max_probe = layout == CV_LAYOUT_SORTED ? steps : hc[0] + 1;
+      m->info.layout = layout;
+      const uint64_t table_bytes =
+          layout == CV_LAYOUT_SORTED ? std::max<uint64_t>(hc[2], 1) * 36 : n_slots * 32;
+      if (layout == CV_LAYOUT_SORTED) m->info.n_slots = hc[2];
+      m->info.device_bytes = table_bytes + std::max<uint64_t>(M, 1) * 8 + n_blocks * 32 +
                              (m->confirm ? M * kSector : 0);
       return CV_OK;
     };
@@ -383,7 +435,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
     cfg_i = (int)opts->kernel_config - 1;
   }
   const int sig = (int)m->tab.sig;
-  const ScanCfg& cfg = scan_config_for(cfg_i, sig, &cfg_i);
+  const ScanCfg& cfg = scan_config_for(cfg_i, table_kind(m->tab), &cfg_i);
   TableView tab = m->tab;  // disk sector g sits at cluster position (g - base_offset) mod 8
   tab.tau_add = (uint32_t)((8u - base_offset % 8u) % 8u);
   // With a 64-bit signature every candidate is confirmed against the disk sector's bytes after
@@ -620,6 +672,7 @@ void cv_free(void* handle) {
     if (m->postings) cudaFree(m->postings);
     if (m->bloom) cudaFree(m->bloom);
     if (m->confirm) cudaFree(m->confirm);
+    if (m->keys0) cudaFree(m->keys0);
     free(m);
   } else if (magic == kMagicResult) {
     cv_result* r = (cv_result*)handle;

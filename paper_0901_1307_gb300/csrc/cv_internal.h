@@ -41,19 +41,28 @@ __host__ __device__ constexpr bool sig_is_weak(int sig) { return sig == kSigDjb2
 //   bloom: 8 u32 words (32 bytes) per block; block tau_block(d3, tau) & bloom_mask; in word j the bit
 //          (d1 >> 5j) & 31 for j < 6, (d2 >> 5(j-6)) & 31 for j = 6, 7.
 //   confirm: for 64-bit signatures, the master sector bytes of posting q at confirm + 512 q.
+//   sorted layout: slots holds n_keys records (no empty ones) in ascending order of
+//          h0 = tau_home(d0, tau), and keys0[q] is record q's h0: a lookup is a binary search of
+//          keys0 (the alternative to linear probing for high occupancy, Section 4), then a
+//          comparison of the records whose h0 is equal.
+enum : uint32_t { kLayoutHash = 0, kLayoutSorted = 1 };
+
 struct TableView {
   const uint4* slots;
   const uint2* postings;
   const uint4* bloom;
   const uint8_t* confirm;
+  const uint32_t* keys0;  // sorted layout only
   uint32_t slot_mask;
   uint32_t bloom_mask;
-  uint32_t max_probe;  // no stored digest sits further than max_probe - 1 slots from home
+  uint32_t max_probe;  // hash: no stored digest sits further than max_probe - 1 slots from home
   uint32_t use_bloom;
   uint32_t sig;        // kSig* of the table
   uint32_t tau_mask;   // 7 for position-keyed tables (S_tau), 0 for one table over all positions
   uint32_t tau_add;    // (8 - base_offset mod 8) mod 8: disk sector g sits at position (g + tau_add) & 7
-  uint32_t pad[3];
+  uint32_t layout;     // kLayout*
+  uint32_t n_keys;     // sorted layout: records in slots and keys0
+  uint32_t pad;
 };
 
 // Position-keyed tables (Section 3.1: one table S_tau per sector position tau of an 8-sector

@@ -13,17 +13,22 @@ struct ScanCfg {
   int threads;  // block size: T / SPT hashing threads + one producer warp
   int NS;       // shared-memory ring stages
   int BOXB;   // bytes of each sector row per stage (64 or 128)
-  const void* scan_fn[4];    // scan_kernel per signature (kSig*); null: not built for this one
-  const void* digest_fn[4];  // the same in digest mode
+  const void* scan_fn[8];    // scan_kernel per table kind (table_kind); null: not built for it
+  const void* digest_fn[4];  // digest mode, per signature (kSig*)
   const void* expand_fn;     // expand_kernel<T>
   uint32_t smem;             // dynamic shared memory bytes
 };
 
 const ScanCfg* scan_configs(int* n);
 
-// Configuration cfg_i if it has kernels for signature sig, else the default one (index 0, which
-// has every signature); *used receives the index in use.
-const ScanCfg& scan_config_for(int cfg_i, int sig, int* used);
+// Scan kernels are selected by signature and table layout: kind = sig + 4 * layout.
+constexpr int kTableKinds = 8;
+inline int table_kind(const TableView& t) { return (int)t.sig + 4 * (int)t.layout; }
+
+// Configuration cfg_i if it has a scan kernel for table kind `kind` (table_kind, or a bare kSig*
+// for the digest pass), else the default one (index 0, which has every kind); *used receives the
+// index in use.
+const ScanCfg& scan_config_for(int cfg_i, int kind, int* used);
 
 // The expand pass over n_out_tiles output tiles (see expand_kernel). Returns a CUDA error code.
 int launch_expand(const ScanCfg& cfg, const uint4* hit_rec, const uint32_t* tile_nhit, const uint64_t* tile_off,

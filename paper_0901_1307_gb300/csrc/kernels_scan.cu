@@ -6,23 +6,27 @@
 
 namespace cvk {
 
-#define CV_KS(T, SPT, NS, B, MODE, P, MB, SIG) (const void*)scan_kernel<T, SPT, NS, B, MODE, P, MB, SIG>
+#define CV_KS(T, SPT, NS, B, MODE, P, MB, SIG) (const void*)scan_kernel<T, SPT, NS, B, MODE, P, MB, SIG, kLayoutHash>
+#define CV_KSS(T, SPT, NS, B, P, MB, SIG) (const void*)scan_kernel<T, SPT, NS, B, kModeScan, P, MB, SIG, kLayoutSorted>
 
-// A configuration with MD5 kernels only.
+// A configuration with MD5 kernels for the hash layout only.
 #define CV_SCAN_CFG(T, SPT, NS, B, P, MB)                                                                  \
   ScanCfg {                                                                                                \
     "t" #T "_x" #SPT "_s" #NS "_b" #B "_p" #P, T, SPT, T / SPT + 32, NS, B,                                 \
-        {CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigMd5), nullptr, nullptr, nullptr},                      \
+        {CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigMd5), nullptr, nullptr, nullptr,                       \
+         nullptr, nullptr, nullptr, nullptr},                                                              \
         {CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigMd5), nullptr, nullptr, nullptr},                    \
         (const void*)expand_kernel<T>, ScanSmem<T, NS, B>::kAlloc                                          \
   }
 
-// A configuration with kernels for every signature.
+// A configuration with kernels for every signature and both table layouts.
 #define CV_SCAN_CFG_ALL(T, SPT, NS, B, P, MB)                                                              \
   ScanCfg {                                                                                                \
     "t" #T "_x" #SPT "_s" #NS "_b" #B "_p" #P, T, SPT, T / SPT + 32, NS, B,                                 \
         {CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigMd5), CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigMd5NoPad), \
-         CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigDjb2), CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigCrc64)},  \
+         CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigDjb2), CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigCrc64),   \
+         CV_KSS(T, SPT, NS, B, P, MB, kSigMd5), CV_KSS(T, SPT, NS, B, P, MB, kSigMd5NoPad),                     \
+         CV_KSS(T, SPT, NS, B, P, MB, kSigDjb2), CV_KSS(T, SPT, NS, B, P, MB, kSigCrc64)},                      \
         {CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigMd5),                                                \
          CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigMd5NoPad),                                           \
          CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigDjb2),                                               \
@@ -31,8 +35,8 @@ namespace cvk {
   }
 
 // The first entry is the default configuration (the fastest measured on GB300 for the 32 GiB
-// image workload) and the only one built for every signature; the others stay selectable and
-// are what the batch autotuner tries.
+// image workload) and the only one built for every signature and the sorted layout; the others
+// stay selectable and are what the batch autotuner tries.
 static const ScanCfg kConfigs[] = {
     CV_SCAN_CFG_ALL(256, 1, 2, 64, 3, 0),
     CV_SCAN_CFG(480, 1, 2, 64, 3, 3),
@@ -50,10 +54,10 @@ const ScanCfg* scan_configs(int* n) {
   return kConfigs;
 }
 
-const ScanCfg& scan_config_for(int cfg_i, int sig, int* used) {
+const ScanCfg& scan_config_for(int cfg_i, int kind, int* used) {
   int n;
   const ScanCfg* c = scan_configs(&n);
-  if (cfg_i < 0 || cfg_i >= n || sig < 0 || sig > 3 || !c[cfg_i].scan_fn[sig]) cfg_i = 0;
+  if (cfg_i < 0 || cfg_i >= n || kind < 0 || kind >= kTableKinds || !c[cfg_i].scan_fn[kind]) cfg_i = 0;
   if (used) *used = cfg_i;
   return c[cfg_i];
 }

@@ -82,9 +82,9 @@ int setup(int dev, NoAllocDev** out) {
     const ScanCfg& cfg = scan_configs(&n)[0];
     e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(e);
-    for (int sig = 0; sig < 4; sig++) {
-      if (!cfg.scan_fn[sig]) continue;
-      e = cudaFuncSetAttribute(cfg.scan_fn[sig], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
+    for (int kind = 0; kind < kTableKinds; kind++) {
+      if (!cfg.scan_fn[kind]) continue;
+      e = cudaFuncSetAttribute(cfg.scan_fn[kind], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem);
       if (e != cudaSuccess) return fail(e);
     }
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.blocks_per_sm, cfg.scan_fn[0], cfg.threads, cfg.smem);
@@ -125,7 +125,7 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   int rc = setup(dev, &d);
   if (rc != CV_OK) return rc;
   cudaStream_t stream = (cudaStream_t)stream_;
-  const ScanCfg& cfg = scan_config_for(0, (int)tab.sig, nullptr);
+  const ScanCfg& cfg = scan_config_for(0, table_kind(tab), nullptr);
 
   uint8_t* sc = d->scratch;
   Segment* seg_d = (Segment*)(sc + kOffSeg);
@@ -180,7 +180,7 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   p.status = status_d;
   const uint64_t grid = n_tiles < (uint64_t)d->sms * d->blocks_per_sm ? n_tiles : (uint64_t)d->sms * d->blocks_per_sm;
   void* sargs[] = {&p};
-  if ((e = cudaLaunchKernel(cfg.scan_fn[tab.sig], dim3((unsigned)grid), dim3(cfg.threads), sargs, cfg.smem,
+  if ((e = cudaLaunchKernel(cfg.scan_fn[table_kind(tab)], dim3((unsigned)grid), dim3(cfg.threads), sargs, cfg.smem,
                             stream)) !=
       cudaSuccess)
     return fail(e);

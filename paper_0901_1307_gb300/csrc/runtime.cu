@@ -74,10 +74,11 @@ int get_ctx(DevCtx** out) {
     c.blocks_per_sm.assign(n, 0);
     c.blocks_per_sm_digest.assign(n, 0);
     for (int i = 0; i < n; i++) {
-      for (int sig = 0; sig < 4; sig++) {
-        if (cfgs[i].scan_fn[sig])
-          CV_CUDA(cudaFuncSetAttribute(cfgs[i].scan_fn[sig], cudaFuncAttributeMaxDynamicSharedMemorySize,
+      for (int kind = 0; kind < kTableKinds; kind++)
+        if (cfgs[i].scan_fn[kind])
+          CV_CUDA(cudaFuncSetAttribute(cfgs[i].scan_fn[kind], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)cfgs[i].smem));
+      for (int sig = 0; sig < 4; sig++) {
         if (cfgs[i].digest_fn[sig])
           CV_CUDA(cudaFuncSetAttribute(cfgs[i].digest_fn[sig], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)cfgs[i].smem));
@@ -213,8 +214,7 @@ int launch_range(DevCtx* ctx, int cfg_i, bool digest, const Job& job, const Segm
                  const ScanParams& base, cudaStream_t stream, int* launches) {
   int n;
   const ScanCfg& cfg = scan_configs(&n)[cfg_i];
-  const int sig = (int)base.tab.sig;
-  const void* fn = digest ? cfg.digest_fn[sig] : cfg.scan_fn[sig];
+  const void* fn = digest ? cfg.digest_fn[base.tab.sig] : cfg.scan_fn[table_kind(base.tab)];
   if (!fn) return CV_EINVAL;  // the caller picks a configuration built for the signature
   const int bps = digest ? ctx->blocks_per_sm_digest[cfg_i] : ctx->blocks_per_sm[cfg_i];
   size_t a = s0;

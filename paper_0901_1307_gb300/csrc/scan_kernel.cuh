@@ -127,6 +127,33 @@ __device__ __forceinline__ uint32_t table_probe(const TableView& tab, uint32_t d
   return 0u;
 }
 
+// Sorted layout: branch-free lower bound of h0 = tau_home(d0, tau) in keys0 (ceil(log2 n_keys)
+// dependent loads; the first levels are shared by every thread and stay in L1), then the
+// records with that h0 are compared in full. Returns post_cnt (0: not present) and post_off.
+__device__ __forceinline__ uint32_t sorted_probe(const TableView& tab, uint32_t d0, uint32_t d1, uint32_t d2,
+                                                 uint32_t d3, uint32_t tau, uint32_t& post_off) {
+  const uint32_t h0 = tau_home(d0, tau);
+  const uint32_t* k = tab.keys0;
+  uint32_t n = tab.n_keys;
+  if (n == 0u) return 0u;
+  uint32_t base = 0;
+  while (n > 1u) {
+    const uint32_t half = n >> 1;
+    base = __ldg(k + base + half) < h0 ? base + half : base;
+    n -= half;
+  }
+  for (uint32_t i = base + (__ldg(k + base) < h0 ? 1u : 0u); i < tab.n_keys && __ldg(k + i) == h0; i++) {
+    const uint4* s = tab.slots + 2ull * i;
+    const uint4 key = __ldg(s);
+    const uint4 val = __ldg(s + 1);
+    if (key.x == d0 && key.y == d1 && key.z == d2 && key.w == d3 && val.z == tau) {
+      post_off = val.x;
+      return val.y;
+    }
+  }
+  return 0u;
+}
+
 // djb2 over one 64-byte block (Eq. 1): four bytes at a time, h = h * 33^4 + the word's bytes
 // in Horner form (byte 0 is the word's low byte; at most 255 * 37060 < 2^32).
 __device__ __forceinline__ uint64_t djb2_block(uint64_t h, const uint32_t (&X)[16]) {
@@ -189,7 +216,7 @@ struct ScanSmem {
 // blocks per SM the register allocation must allow (0: no constraint).
 // Thread t hashes rows t, t + C, ... of the tile. Matches are compacted per warp and row group:
 // rows [32v, 32v + 32) of tile k form output tile k * (T / 32) + v.
-template <int T, int SPT, int NS, int BOXB, int MODE, int PIPE, int MINB, int SIG>
+template <int T, int SPT, int NS, int BOXB, int MODE, int PIPE, int MINB, int SIG, int LAYOUT>
 __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_constant__ ScanParams p) {
   constexpr int C = T / SPT;
   // A tile larger than the 256-row TMA box limit is loaded as several boxes per stage.
@@ -364,7 +391,9 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
         // the disk sector's position in its cluster (0 for a table over all positions)
         const uint32_t tau = (uint32_t)(seg.sector_base + r + p.tab.tau_add) & p.tab.tau_mask;
         if (valid && (!p.tab.use_bloom || bloom_test(p.tab, st[k][1], st[k][2], st[k][3], tau)))
-          post_cnt = table_probe(p.tab, st[k][0], st[k][1], st[k][2], st[k][3], tau, post_off);
+          post_cnt = LAYOUT == kLayoutSorted
+                         ? sorted_probe(p.tab, st[k][0], st[k][1], st[k][2], st[k][3], tau, post_off)
+                         : table_probe(p.tab, st[k][0], st[k][1], st[k][2], st[k][3], tau, post_off);
         // triples this sector emits: every posting, or for a 64-bit signature the postings whose
         // master sector equals this sector byte for byte
         uint32_t n_emit = post_cnt;

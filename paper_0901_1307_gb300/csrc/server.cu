@@ -367,7 +367,7 @@ int cv_server_create(const cv_master* m, const cv_server_opts* opts, cv_server**
     if (opts->kernel_config > (uint32_t)ncfg) return CV_EINVAL;
     cfg_i = (int)opts->kernel_config - 1;
   }
-  scan_config_for(cfg_i, (int)tab.sig, &cfg_i);
+  scan_config_for(cfg_i, table_kind(tab), &cfg_i);
   uint64_t unit = (opts && opts->work_unit_bytes) ? opts->work_unit_bytes : (64ull << 20);
   uint64_t budget = (opts && opts->hbm_budget_bytes) ? opts->hbm_budget_bytes : (8ull << 30);
   if (unit % kSector || unit > kMaxSegmentSectors * kSector || budget < unit) return CV_EINVAL;

@@ -11,6 +11,8 @@
 //   fill     the sorted pairs become the postings; the first pair of each run writes its
 //            slot {digest, post_off, post_cnt}.
 //   bloom    every occupied slot sets its 8 bits in the blocked Bloom filter.
+//   sorted   (sorted layout only) the occupied slots, compacted in slot order, are sorted by
+//            h0 and become the searched array.
 // Position-keyed tables (one S_tau per cluster position, Section 3.1) key every slot by
 // (digest, tau) with tau = file_sector mod 8; the steps are the same.
 // Which slot a digest lands in depends on thread timing; the lookup result does not.
@@ -211,6 +213,33 @@ __global__ void gather_sectors_kernel(const uint4* arena, const uint32_t* keys, 
     const uint64_t q = i / (kSector / 16);
     if (keys[q] >= n_slots) continue;
     out[i] = arena[(uint64_t)vals[q] * (kSector / 16) + i % (kSector / 16)];
+  }
+}
+
+// ------------------------------------------------------------------- sorted layout
+// Sort key of the occupied-slot compaction: 0 for an occupied slot, 1 for an empty one; a stable
+// sort by it puts the occupied slots first, in slot order.
+__global__ void occupied_keys_kernel(const uint4* slots, uint32_t n_slots, uint32_t* keys, uint32_t* vals) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += gridDim.x * blockDim.x) {
+    keys[i] = slots[2ull * i + 1].y != 0u ? 0u : 1u;
+    vals[i] = i;
+  }
+}
+
+// h0 = tau_home(d0, tau) of the slots vals[0..n).
+__global__ void h0_keys_kernel(const uint4* slots, const uint32_t* vals, uint32_t n, uint32_t* keys) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const uint32_t i = vals[q];
+    keys[q] = tau_home(slots[2ull * i].x, slots[2ull * i + 1].z);
+  }
+}
+
+// Slot records in the order of vals (ascending h0): out[q] = slots[vals[q]].
+__global__ void gather_slots_kernel(const uint4* slots, const uint32_t* vals, uint32_t n, uint4* out) {
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const uint32_t i = vals[q];
+    out[2ull * q] = slots[2ull * i];
+    out[2ull * q + 1] = slots[2ull * i + 1];
   }
 }
 

@@ -115,6 +115,38 @@ def crc_collision(x: np.ndarray, bit: int) -> np.ndarray:
     return np.frombuffer(m.to_bytes(SECTOR, "big"), np.uint8).copy()
 
 
+def _mulmod(a: int, b: int) -> int:
+    r = 0
+    while b:
+        if b & 1:
+            r ^= a
+        b >>= 1
+        a <<= 1
+        if a >> 64:
+            a ^= GEN
+    return r
+
+
+def crc_high_twin(x: np.ndarray, k: int) -> np.ndarray:
+    """A sector whose CRC64 equals x's XOR (k << 32): XOR x with E = k(x) x^32 x^-64 mod G, so the
+    low 32 bits (the table's first key word) agree and the high ones differ."""
+    inv_x = (1 << 63) | 0b1101  # x (x^63 + x^3 + x^2 + 1) = 1 mod G
+    e = k
+    for _ in range(32):
+        e = _mulmod(e, inv_x)
+    m = int.from_bytes(x.tobytes(), "big") ^ e
+    return np.frombuffer(m.to_bytes(SECTOR, "big"), np.uint8).copy()
+
+
+def test_crc_high_twin_construction():
+    x = np.random.default_rng(3).integers(0, 256, SECTOR, dtype=np.uint8)
+    for k in (1, 2, 0xDEAD):
+        y = crc_high_twin(x, k)
+        assert poly_mod(int.from_bytes(y.tobytes(), "big") << 64, GEN) == \
+            poly_mod(int.from_bytes(x.tobytes(), "big") << 64, GEN) ^ (k << 32)
+        assert oracle.crc64(y) == oracle.crc64(x) ^ (k << 32)
+
+
 def test_constructed_collisions_collide():
     rng = np.random.default_rng(5)
     x = rng.integers(40, 200, SECTOR, dtype=np.uint8)
