@@ -91,6 +91,12 @@ def bind(lib):
     lib.oracle_signature.restype = None
     lib.oracle_match_sig.argtypes = [vp, u64, vp, vp, u32, ctypes.c_int, vp, u64]
     lib.oracle_match_sig.restype = ctypes.c_int64
+    lib.oracle_frag_match_brute.argtypes = [vp, u64, vp, vp, u32, vp, u64]
+    lib.oracle_frag_match_brute.restype = ctypes.c_int64
+    lib.oracle_frag_match.argtypes = [vp, u64, vp, vp, u32, vp, u64]
+    lib.oracle_frag_match.restype = ctypes.c_int64
+    lib.oracle_fragment_trivial.argtypes = [vp]
+    lib.oracle_fragment_trivial.restype = ctypes.c_int
     lib.oracle_match_position.argtypes = [vp, u64, vp, vp, u32, u64, vp, u64]
     lib.oracle_match_position.restype = ctypes.c_int64
     lib.oracle_db_build_sig.argtypes = [vp, vp, u32, ctypes.c_int]
@@ -234,6 +240,28 @@ def match_position(image, files, base_offset: int = 0) -> np.ndarray:
     position in its 8-sector cluster, disk clusters counted from sector base_offset."""
     lib = _load()
     return _run_match(lambda *a: lib.oracle_match_position(*a[:5], int(base_offset), *a[5:]), image, files)
+
+
+FRAG, FRAG_STRIDE = 64, 4
+
+
+def frag_match_brute(image, files) -> np.ndarray:
+    """Fragments (Section 5): every (window k, file f, fragment j) with image bytes
+    [4k, 4k+64) equal to bytes [64j, 64j+64) of file f (kept fragments only), by exhaustive
+    memcmp. The window index is in the disk_sector field, j in file_sector."""
+    return _run_match(_load().oracle_frag_match_brute, image, files)
+
+
+def frag_match(image, files) -> np.ndarray:
+    """The fragment result through the kept fragments sorted by their bytes and a binary
+    search per window."""
+    return _run_match(_load().oracle_frag_match, image, files)
+
+
+def fragment_trivial(frag) -> bool:
+    a = _u8(frag)
+    assert a.size == FRAG
+    return bool(_load().oracle_fragment_trivial(_ptr(a)))
 
 
 def match_hash(image, files) -> np.ndarray:

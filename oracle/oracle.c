@@ -27,6 +27,10 @@
  *                         binary search as an alternative to its hash tables); the table
  *                         layout does not change the result.
  *
+ * Fragments (Section 5): oracle_frag_match_brute and oracle_frag_match give the same kind of
+ * result for every 64-byte window at a 4-byte offset against the 64-byte fragments of the
+ * master files (definition at the functions).
+ *
  * Other signatures (Section 2): MD5 without the padding block (Section 2.1 notes it adds nothing
  * for fixed-size sectors), djb2 with a 64-bit accumulator (Eq. 1) and CRC64 with the generator
  * x^64 + x^4 + x^3 + x + 1 (Section 2.1). With a 64-bit signature, equal signatures are only
@@ -454,6 +458,139 @@ int64_t oracle_match_hash(const uint8_t* image, uint64_t image_bytes, const uint
   int64_t n = oracle_db_lookup(db, image, image_bytes / SECTOR, 0, out, cap);
   oracle_db_free(db);
   return n;
+}
+
+/* ------------------------------------------------------ 64-byte fragments (Section 5) */
+
+/* Section 5 proposes scanning every 64-byte fragment of a disk that starts on a 32-bit boundary,
+ * to find small images and logos embedded in documents. The definition used here:
+ *   window k of the image is its bytes [4k, 4k + 64), for every k with 4k + 64 <= image_bytes;
+ *   fragment j of master file f is its bytes [64j, 64j + 64); only whole fragments count;
+ *   a fragment whose 64 bytes are all equal is excluded (the sector rule at fragment size);
+ *   the result is every (k, f, j) with window k byte-equal to kept fragment j of file f, sorted
+ *   (k in the triple's disk_sector field, j in its file_sector field). */
+#define FRAG 64u
+#define FRAG_STRIDE 4u
+
+int oracle_fragment_trivial(const uint8_t* frag) {
+  for (uint32_t j = 1; j < FRAG; j++)
+    if (frag[j] != frag[0]) return 0;
+  return 1;
+}
+
+static uint64_t frag_windows(uint64_t image_bytes) {
+  return image_bytes >= FRAG ? (image_bytes - FRAG) / FRAG_STRIDE + 1 : 0;
+}
+
+/* The definition itself: every window against every kept fragment. Tiny inputs only. */
+int64_t oracle_frag_match_brute(const uint8_t* image, uint64_t image_bytes, const uint8_t* const* files,
+                                const uint64_t* file_bytes, uint32_t n_files, oracle_triple* out, uint64_t cap) {
+  const uint64_t n_win = frag_windows(image_bytes);
+  uint64_t n = 0;
+  for (uint64_t k = 0; k < n_win; k++) {
+    const uint8_t* w = image + k * FRAG_STRIDE;
+    for (uint32_t f = 0; f < n_files; f++) {
+      const uint64_t n_fr = file_bytes[f] / FRAG;
+      for (uint64_t j = 0; j < n_fr; j++) {
+        const uint8_t* m = files[f] + j * FRAG;
+        if (oracle_fragment_trivial(m) || memcmp(w, m, FRAG) != 0) continue;
+        if (n < cap) {
+          out[n].disk_sector = k;
+          out[n].file_id = f;
+          out[n].file_sector = (uint32_t)j;
+        }
+        n++;
+      }
+    }
+  }
+  if (n <= cap) qsort(out, (size_t)n, sizeof(oracle_triple), triple_cmp);
+  return (int64_t)n;
+}
+
+typedef struct {
+  const uint8_t* bytes;
+  uint32_t file_id;
+  uint32_t frag;
+} frag_entry;
+
+static int frag_cmp(const void* pa, const void* pb) {
+  const frag_entry* a = (const frag_entry*)pa;
+  const frag_entry* b = (const frag_entry*)pb;
+  int c = memcmp(a->bytes, b->bytes, FRAG);
+  if (c) return c;
+  if (a->file_id != b->file_id) return a->file_id < b->file_id ? -1 : 1;
+  if (a->frag != b->frag) return a->frag < b->frag ? -1 : 1;
+  return 0;
+}
+
+/* First entry whose bytes are >= w (binary search in memcmp order). */
+static uint64_t frag_lower_bound(const frag_entry* e, uint64_t n, const uint8_t* w) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint64_t mid = lo + (hi - lo) / 2;
+    if (memcmp(e[mid].bytes, w, FRAG) < 0)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+/* The same result through the kept fragments sorted by their bytes (then by file and
+ * fragment): each window is binary-searched and the run of equal fragments reported. Windows
+ * are processed in blocks (count in parallel, then write in order), so the output is sorted. */
+int64_t oracle_frag_match(const uint8_t* image, uint64_t image_bytes, const uint8_t* const* files,
+                          const uint64_t* file_bytes, uint32_t n_files, oracle_triple* out, uint64_t cap) {
+  uint64_t total = 0;
+  for (uint32_t f = 0; f < n_files; f++) total += file_bytes[f] / FRAG;
+  frag_entry* e = (frag_entry*)malloc(sizeof(frag_entry) * (total ? total : 1));
+  if (!e) return -1;
+  uint64_t m = 0;
+  for (uint32_t f = 0; f < n_files; f++)
+    for (uint64_t j = 0; j < file_bytes[f] / FRAG; j++) {
+      const uint8_t* b = files[f] + j * FRAG;
+      if (oracle_fragment_trivial(b)) continue;
+      e[m].bytes = b;
+      e[m].file_id = f;
+      e[m].frag = (uint32_t)j;
+      m++;
+    }
+  qsort(e, (size_t)m, sizeof(frag_entry), frag_cmp);
+  const uint64_t n_win = frag_windows(image_bytes);
+  const uint64_t block = 1u << 20;
+  uint64_t* lo = (uint64_t*)malloc(sizeof(uint64_t) * block);
+  uint64_t* cnt = (uint64_t*)malloc(sizeof(uint64_t) * block);
+  if (!lo || !cnt) {
+    free(e);
+    free(lo);
+    free(cnt);
+    return -1;
+  }
+  uint64_t n = 0;
+  for (uint64_t k0 = 0; k0 < n_win; k0 += block) {
+    const uint64_t nb = n_win - k0 < block ? n_win - k0 : block;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < (int64_t)nb; i++) {
+      const uint8_t* w = image + (k0 + (uint64_t)i) * FRAG_STRIDE;
+      uint64_t a = frag_lower_bound(e, m, w), b = a;
+      while (b < m && memcmp(e[b].bytes, w, FRAG) == 0) b++;
+      lo[i] = a;
+      cnt[i] = b - a;
+    }
+    for (uint64_t i = 0; i < nb; i++)
+      for (uint64_t q = 0; q < cnt[i]; q++) {
+        if (n < cap) {
+          out[n].disk_sector = k0 + i;
+          out[n].file_id = e[lo[i] + q].file_id;
+          out[n].file_sector = e[lo[i] + q].frag;
+        }
+        n++;
+      }
+  }
+  free(e);
+  free(lo);
+  free(cnt);
+  return (int64_t)n;
 }
 
 /* Threads the parallel loops use (1 when built without OpenMP). */

@@ -371,3 +371,151 @@ def config_plan(name: str) -> Plan:
         nsect = rng.integers(16, 129, size=int(nf))
         return make_plan(int(seed), int(ns), nsect, 0.40)
     raise KeyError(name)
+
+
+# ----------------------------------------------------------------------------------------------
+# Fragment workloads (Section 5: every 64-byte fragment at a 32-bit boundary, to find small
+# images and logos embedded in documents).
+
+FRAG = 64
+FRAG_STRIDE = 4
+_LOGO_STREAM = 101
+_HEADER_STREAM = 102
+
+
+@dataclasses.dataclass
+class FragPlan:
+    """Small master files ("logos") embedded at 4-byte-aligned offsets of a background image.
+
+    Logos are random bytes; some start with a header shared by several logos (so one fragment
+    belongs to several files) and some hold a zero-filled run at a fragment boundary (fragments
+    the exclusion rule drops). Planted copies do not overlap one another."""
+
+    background: Plan           # the image's background: the three sector classes, nothing planted
+    n_bytes: int               # image length (need not be a multiple of 512 or 4)
+    logo_seed: int
+    logo_bytes: np.ndarray     # int64 [n_logos]
+    header_len: np.ndarray     # int64 [n_logos]: bytes of the shared header at the logo's start
+    zero_at: np.ndarray        # int64 [n_logos]: fragment index of a zero run (-1: none)
+    zero_len: np.ndarray       # int64 [n_logos]: its length in bytes
+    plant_logo: np.ndarray     # int64 [n_plants]
+    plant_off: np.ndarray      # int64 [n_plants]: byte offsets, multiples of 4
+
+    @property
+    def n_logos(self) -> int:
+        return int(self.logo_bytes.size)
+
+    def _header(self) -> np.ndarray:
+        n = int(self.header_len.max()) if self.n_logos else 0
+        return random_sectors(self.logo_seed, (n + SECTOR - 1) // SECTOR, 0, _HEADER_STREAM)[:n]
+
+    def logo(self, f: int, header: np.ndarray | None = None) -> np.ndarray:
+        nb = int(self.logo_bytes[f])
+        first = int(np.sum(((self.logo_bytes[:f] + SECTOR - 1) // SECTOR)))
+        out = random_sectors(self.logo_seed, (nb + SECTOR - 1) // SECTOR, first, _LOGO_STREAM)[:nb].copy()
+        h = int(self.header_len[f])
+        if h:
+            out[:h] = (self._header() if header is None else header)[:h]
+        if self.zero_at[f] >= 0:
+            z = int(self.zero_at[f]) * FRAG
+            out[z:z + int(self.zero_len[f])] = 0
+        return out
+
+    def logos(self) -> list:
+        header = self._header()
+        return [self.logo(f, header) for f in range(self.n_logos)]
+
+    def image_host(self) -> np.ndarray:
+        img = self.background.image_host()[: self.n_bytes].copy()
+        logos = self.logos()
+        for f, o in zip(self.plant_logo.tolist(), self.plant_off.tolist()):
+            img[o:o + logos[f].size] = logos[f]
+        return img
+
+    def image_device(self, torch, out) -> None:
+        """Write the image into the uint8 device tensor out (at least n_bytes long)."""
+        bg = self.background
+        pf, pc, po = (torch.from_numpy(a).cuda() for a in (bg.plant_file, bg.plant_fcluster.view(np.int32),
+                                                            bg.plant_over))
+        fn = torch.zeros(1, dtype=torch.int32).cuda()
+        vc = torch.from_numpy(vocab(bg.image_seed)).cuda()
+        bg.image_device(out.data_ptr(), 0, self.n_bytes // SECTOR,
+                        dev_plan=(pf.data_ptr(), pc.data_ptr(), po.data_ptr(), fn.data_ptr(), vc.data_ptr()))
+        tail = self.n_bytes % SECTOR
+        if tail:
+            out[self.n_bytes - tail:self.n_bytes].copy_(torch.from_numpy(bg.image_host(self.n_bytes // SECTOR, 1)[:tail]))
+        logos = self.logos()
+        sizes = np.array([x.size for x in logos], np.int64)
+        base = np.zeros(self.n_logos + 1, np.int64)
+        np.cumsum(sizes, out=base[1:])
+        flat = torch.from_numpy(np.concatenate(logos) if logos else np.zeros(0, np.uint8)).cuda()
+        for f, o in zip(self.plant_logo.tolist(), self.plant_off.tolist()):
+            out[o:o + int(sizes[f])].copy_(flat[int(base[f]):int(base[f + 1])])
+        torch.cuda.synchronize()
+
+    def expected_planted(self) -> np.ndarray:
+        """Triples (window, logo, fragment) of every planted logo's whole, non-zero-run fragments:
+        a subset of the result (logos are random, so the result adds only the other files that
+        share a header fragment)."""
+        rows = []
+        for f, o in zip(self.plant_logo.tolist(), self.plant_off.tolist()):
+            n_fr = int(self.logo_bytes[f]) // FRAG
+            j = np.arange(n_fr, dtype=np.int64)
+            if self.zero_at[f] >= 0:
+                z0, z1 = int(self.zero_at[f]) * FRAG, int(self.zero_at[f]) * FRAG + int(self.zero_len[f])
+                j = j[~((j * FRAG >= z0) & ((j + 1) * FRAG <= z1))]
+            t = np.zeros(j.size, TRIPLE_DTYPE)
+            t["disk_sector"] = o // FRAG_STRIDE + j * (FRAG // FRAG_STRIDE)
+            t["file_id"] = f
+            t["file_sector"] = j
+            rows.append(t)
+        out = np.concatenate(rows) if rows else np.zeros(0, TRIPLE_DTYPE)
+        out.sort(order=["disk_sector", "file_id", "file_sector"])
+        return out
+
+
+def make_frag_plan(seed: int, n_bytes: int, n_logos: int, lo_bytes: int = 1024, hi_bytes: int = 16384,
+                   header_frac: float = 0.1, header_bytes: int = 128, zero_frac: float = 0.2,
+                   plant_frac: float = 0.5, max_copies: int = 3) -> FragPlan:
+    """n_logos logos of log-uniform lo..hi bytes; header_frac of them start with a shared
+    header_bytes header, zero_frac hold a zero run of 64-192 bytes at a fragment boundary;
+    plant_frac of them are planted 1..max_copies times at non-overlapping 4-byte-aligned
+    offsets of an n_bytes image whose background is the usual sector mix."""
+    rng = np.random.default_rng([seed, 0xF4A6])
+    sizes = np.round(log_uniform_sizes(rng, n_logos, lo_bytes, hi_bytes)).astype(np.int64)
+    header_len = np.where(rng.random(n_logos) < header_frac, min(header_bytes, lo_bytes), 0).astype(np.int64)
+    zero_at = np.full(n_logos, -1, np.int64)
+    zero_len = np.zeros(n_logos, np.int64)
+    for f in np.nonzero(rng.random(n_logos) < zero_frac)[0].tolist():
+        n_fr = int(sizes[f]) // FRAG
+        if n_fr >= 4:
+            zero_at[f] = int(rng.integers(2, n_fr - 1))
+            zero_len[f] = FRAG * int(rng.integers(1, 4))
+    planted = np.nonzero(rng.random(n_logos) < plant_frac)[0]
+    plants = np.repeat(planted, rng.integers(1, max_copies + 1, size=planted.size))
+    rng.shuffle(plants)
+    P = plants.size
+    offs = np.zeros(P, np.int64)
+    if P:
+        region = (n_bytes // P) // FRAG_STRIDE * FRAG_STRIDE
+        if region < int(sizes[plants].max()):
+            raise ValueError("image too small for the planted logos")
+        room = (region - sizes[plants]) // FRAG_STRIDE
+        offs = np.arange(P, dtype=np.int64) * region + FRAG_STRIDE * rng.integers(0, room + 1)
+    n_sectors = (n_bytes + SECTOR - 1) // SECTOR
+    background = make_plan(seed, n_sectors, np.zeros(0, np.uint32), 0.0)
+    return FragPlan(background, n_bytes, seed + 0x10CC, sizes, header_len, zero_at, zero_len,
+                    plants.astype(np.int64), offs)
+
+
+def frag_config(name: str) -> FragPlan:
+    """The named fragment workloads.
+
+    frag  : 4 GiB image, seed 11; 2,000 logos of log-uniform 1-16 KiB, half planted 1-3 times.
+    frag_small:<bytes>:<logos>:<seed> -- scaled down for tests."""
+    if name == "frag":
+        return make_frag_plan(11, 4 << 30, 2000)
+    if name.startswith("frag_small:"):
+        _, nb, nl, seed = name.split(":")
+        return make_frag_plan(int(seed), int(nb), int(nl))
+    raise KeyError(name)

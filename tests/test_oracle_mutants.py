@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 from test_oracle import as_list, py_match, tricky_case
+from test_oracle_fragments import py_frag_match, tricky_frag_case
 
 MUTANTS = {
     "rotation amount": ("{7, 12, 17, 22}", "{7, 12, 17, 21}"),
@@ -54,6 +55,10 @@ MUTANTS = {
                                            "((all[k].disk_sector % 8u) + (base_offset % 8u)) % 8u"),
     "position from the disk sector only": ("if (tau_disk != all[k].file_sector % 8u) continue;",
                                            "if (tau_disk != 0u) continue;"),
+    "fragment window stride": ("#define FRAG_STRIDE 4u", "#define FRAG_STRIDE 8u"),
+    "fragment last window dropped": ("(image_bytes - FRAG) / FRAG_STRIDE + 1", "(image_bytes - FRAG) / FRAG_STRIDE"),
+    "fragment rule only zero": ("if (frag[j] != frag[0]) return 0;", "if (frag[j] != 0) return 0;"),
+    "fragment master stride": ("const uint8_t* b = files[f] + j * FRAG;", "const uint8_t* b = files[f] + j * FRAG_STRIDE;"),
     "no-pad state after 7 blocks": ("for (int b = 0; b < 8; b++) md5_block(st, sector + 64 * b);",
                                     "for (int b = 0; b < 7; b++) md5_block(st, sector + 64 * b);"),
 }
@@ -105,9 +110,21 @@ def _position_pins_pass() -> bool:
     return True
 
 
+def _fragment_pins_pass() -> bool:
+    """The fragment pins: both routes against the Python definition on the tricky inputs."""
+    for seed in range(3):
+        image, files = tricky_frag_case(seed)
+        want = py_frag_match(image.tobytes(), [f.tobytes() for f in files])
+        if as_list(oracle.frag_match_brute(image, files)) != want or as_list(oracle.frag_match(image, files)) != want:
+            return False
+    x = np.random.default_rng(1).integers(0, 256, 64, dtype=np.uint8)
+    img = np.concatenate([np.zeros(12, np.uint8), x])  # the last window ends at the image end
+    return as_list(oracle.frag_match(img, [x])) == [(3, 0, 0)] == as_list(oracle.frag_match_brute(img, [x]))
+
+
 def _pins_pass() -> bool:
     """The pins of tests/test_oracle.py, condensed; False as soon as one fails."""
-    if not _signature_pins_pass() or not _position_pins_pass():
+    if not _signature_pins_pass() or not _position_pins_pass() or not _fragment_pins_pass():
         return False
     rng = np.random.default_rng(5)
     for length in (0, 1, 55, 56, 63, 64, 100, 512, 1000):
