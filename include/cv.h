@@ -97,16 +97,32 @@ typedef struct cv_result cv_result; /* the results of one scan */
 #define CV_LAYOUT_HASH 0u
 #define CV_LAYOUT_SORTED 1u
 
+/* What the master files are cut into (cv_master_opts.unit).
+ * CV_UNIT_SECTOR: whole 512-byte sectors; disk images are scanned sector by sector.
+ * CV_UNIT_FRAGMENT: whole 64-byte fragments (fragment j of a file is its bytes [64j, 64j+64),
+ *   fragments whose 64 bytes are all equal excluded); a scan looks up every 64-byte window of
+ *   the image that starts at a multiple of 4 bytes (Section 5: small images and logos embedded
+ *   in other files at any 32-bit offset). A match (k, f, j) means image bytes [4k, 4k+64) equal
+ *   fragment j of file f: cv_match.disk_sector holds the window index k and cv_match.file_sector
+ *   the fragment index j. Signatures: MD5, MD5 without padding (one compression per window) and
+ *   djb2-64 (rolled from window to window; every candidate confirmed byte for byte); CRC64 and
+ *   CV_POSITION_CLUSTER are refused with CV_EINVAL. The Bloom filter is one 32-bit word per
+ *   lookup (3 bits per key). Batched, served and allocation-free scans take sector tables only. */
+#define CV_UNIT_SECTOR 0u
+#define CV_UNIT_FRAGMENT 1u
+
 typedef struct {
-  uint32_t struct_size;         /* sizeof(cv_master_opts); the size without position_mode and
-                                   layout (24 bytes) is accepted and selects CV_POSITION_ANY and
-                                   CV_LAYOUT_HASH */
+  uint32_t struct_size;         /* sizeof(cv_master_opts); 24 bytes (before position_mode) and
+                                   32 bytes (before unit) are accepted: the missing fields take
+                                   CV_POSITION_ANY, CV_LAYOUT_HASH and CV_UNIT_SECTOR */
   float max_load;               /* table load factor cap in (0, 0.9]; 0 selects 0.5 */
   uint32_t bloom_bits_per_key;  /* 0 = no Bloom prefilter; CV_BLOOM_AUTO = 16 */
   uint32_t signature;           /* CV_SIG_*; 0 = MD5 */
   void* stream;                 /* cudaStream_t */
   uint32_t position_mode;       /* CV_POSITION_* */
   uint32_t layout;              /* CV_LAYOUT_*; read only together with position_mode */
+  uint32_t unit;                /* CV_UNIT_*; read when struct_size covers it (else sectors) */
+  uint32_t reserved;            /* 0 */
 } cv_master_opts;
 
 /* cv_scan_opts.flags */
@@ -152,7 +168,7 @@ typedef struct {
   uint32_t signature;        /* CV_SIG_* of the table */
   uint64_t device_bytes;     /* device memory the handle holds */
   uint32_t layout;           /* CV_LAYOUT_* of the table */
-  uint32_t reserved;
+  uint32_t unit;             /* CV_UNIT_* of the table (n_sectors, n_kept: units of that size) */
 } cv_master_info;
 
 int cv_master_get_info(const cv_master* m, cv_master_info* info);
@@ -162,6 +178,9 @@ int cv_master_get_info(const cv_master* m, cv_master_info* info);
  * its signature looked up, matches reported to the host). Device images are scanned in one
  * launch; host images are streamed through device buffers in chunks, copies overlapping the
  * hashing. On success *out receives a handle owning the sorted results of every image.
+ * With a fragment table (CV_UNIT_FRAGMENT) every 64-byte window at a 4-byte offset is looked up
+ * instead; host images are then copied whole to the device, and chunk_bytes, kernel_config and
+ * base_offset are ignored.
  * Errors: CV_EINVAL, CV_ENOMEM, CV_ECUDA, CV_ETIMEOUT, CV_ECORRUPT, CV_ENODEV.
  */
 int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const cv_scan_opts* opts,
@@ -175,7 +194,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
 int cv_matches(const cv_result* r, uint32_t image_index, const cv_match** out, uint64_t* n_out);
 
 typedef struct {
-  uint64_t sectors;        /* whole sectors scanned */
+  uint64_t sectors;        /* whole sectors scanned (fragment tables: windows scanned) */
   uint64_t matches;        /* triples over all images */
   uint64_t hit_sectors;    /* reserved (0) */
   float kernel_ms;         /* device time of the hashing/probe launches */

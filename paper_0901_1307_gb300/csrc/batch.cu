@@ -192,7 +192,7 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
   if (opts && opts->struct_size < sizeof(cv_batch_opts)) return CV_EINVAL;
   TableView tab;
   int mdev;
-  if (master_view(m, &tab, &mdev) != CV_OK) return CV_EINVAL;
+  if (master_view(m, &tab, &mdev) != CV_OK || tab.unit != kUnitSector) return CV_EINVAL;
   DevCtx* ctx;
   CV_TRY(get_ctx(&ctx));
   if (ctx->dev != mdev) return CV_EINVAL;

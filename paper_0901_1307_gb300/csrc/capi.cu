@@ -170,12 +170,16 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
   if (!out || (n_files && !files)) return CV_EINVAL;
   *out = nullptr;
   if (opts && opts->struct_size < offsetof(cv_master_opts, position_mode)) return CV_EINVAL;
-  const uint32_t position_mode =
-      (opts && opts->struct_size >= sizeof(cv_master_opts)) ? opts->position_mode : CV_POSITION_ANY;
+  const bool has_v2 = opts && opts->struct_size >= offsetof(cv_master_opts, unit);
+  const uint32_t position_mode = has_v2 ? opts->position_mode : CV_POSITION_ANY;
   if (position_mode > CV_POSITION_CLUSTER) return CV_EINVAL;
   const bool by_tau = position_mode == CV_POSITION_CLUSTER;
-  const uint32_t layout = (opts && opts->struct_size >= sizeof(cv_master_opts)) ? opts->layout : CV_LAYOUT_HASH;
+  const uint32_t layout = has_v2 ? opts->layout : CV_LAYOUT_HASH;
   if (layout > CV_LAYOUT_SORTED) return CV_EINVAL;
+  const uint32_t unit = (opts && opts->struct_size >= sizeof(cv_master_opts)) ? opts->unit : CV_UNIT_SECTOR;
+  if (unit > CV_UNIT_FRAGMENT) return CV_EINVAL;
+  const bool frag = unit == CV_UNIT_FRAGMENT;
+  const uint64_t U = frag ? kFrag : kSector;  // bytes per master unit
   float max_load = (opts && opts->max_load > 0.f) ? opts->max_load : 0.5f;
   if (!(max_load > 0.f && max_load <= 0.9f)) return CV_EINVAL;
   uint32_t bpk = opts ? opts->bloom_bits_per_key : CV_BLOOM_AUTO;
@@ -183,17 +187,18 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
   if (bpk > 64) return CV_EINVAL;
   const int sig = opts ? (int)opts->signature : kSigMd5;
   if (sig < 0 || sig > kSigCrc64) return CV_EINVAL;
+  if (frag && (!frag_sig_supported(sig) || by_tau)) return CV_EINVAL;
   cudaStream_t stream = opts ? (cudaStream_t)opts->stream : nullptr;
   DevCtx* ctx;
   CV_TRY(get_ctx(&ctx));
   int cfg_i;
   const ScanCfg& cfg = scan_config_for(ctx->cfg_index, sig, &cfg_i);
 
-  // whole sectors of every file, concatenated
+  // whole units (sectors or fragments) of every file, concatenated
   std::vector<uint64_t> file_base(n_files + 1, 0);
   for (uint32_t f = 0; f < n_files; f++) {
     if (files[f].n_bytes && !files[f].data) return CV_EINVAL;
-    file_base[f + 1] = file_base[f] + files[f].n_bytes / kSector;
+    file_base[f + 1] = file_base[f] + files[f].n_bytes / U;
   }
   const uint64_t M = file_base[n_files];
   if (M >= (1ull << 27)) return CV_EINVAL;
@@ -214,7 +219,7 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       uint8_t* trivial;
       uint32_t *owner, *cnt, *slot_of, *keys2, *vals, *vals2, *counters;
       uint64_t* file_base_d;
-      CV_TRY(tmp.alloc(&arena, M * kSector));
+      CV_TRY(tmp.alloc(&arena, M * U));
       CV_TRY(tmp.alloc(&dig, M * sizeof(uint4)));
       CV_TRY(tmp.alloc(&trivial, M));
       CV_TRY(tmp.alloc(&owner, n_slots * 4));
@@ -234,23 +239,28 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       for (uint32_t f = 0; f < n_files; f++) {
         const uint64_t ns = file_base[f + 1] - file_base[f];
         if (ns)
-          CV_CUDA(cudaMemcpyAsync(arena + file_base[f] * kSector, files[f].data, ns * kSector, cudaMemcpyDefault,
-                                  stream));
+          CV_CUDA(cudaMemcpyAsync(arena + file_base[f] * U, files[f].data, ns * U, cudaMemcpyDefault, stream));
       }
       // long-lived table memory
       CV_CUDA(cudaMalloc(&m->slots, n_slots * 32));
       CV_CUDA(cudaMalloc(&m->postings, std::max<uint64_t>(M, 1) * 8));
       CV_CUDA(cudaMemsetAsync(m->slots, 0, n_slots * 32, stream));
+      // Bloom blocks: 32 bytes for sector tables, one 32-bit word for fragment tables
+      const uint64_t block_bytes = frag ? 4 : 32;
       uint64_t n_blocks = 0;
       if (bpk) {
-        n_blocks = std::max<uint64_t>(next_pow2((M * bpk + 255) / 256), 1);
-        CV_CUDA(cudaMalloc(&m->bloom, n_blocks * 32));
-        CV_CUDA(cudaMemsetAsync(m->bloom, 0, n_blocks * 32, stream));
+        n_blocks = std::max<uint64_t>(next_pow2((M * bpk + block_bytes * 8 - 1) / (block_bytes * 8)), frag ? 8 : 1);
+        CV_CUDA(cudaMalloc(&m->bloom, n_blocks * block_bytes));
+        CV_CUDA(cudaMemsetAsync(m->bloom, 0, n_blocks * block_bytes, stream));
       }
       if (M) {
-        Job job;
-        CV_TRY(job.add(ctx, cfg, arena, M, 0, 0, false));
-        CV_TRY(digest_job(ctx, cfg_i, sig, job, dig, trivial, counters + 3, stream, tmp));
+        if (frag) {
+          CV_CUDA((cudaError_t)frag_digests(sig, arena, M, dig, trivial, ctx->sms, stream));
+        } else {
+          Job job;
+          CV_TRY(job.add(ctx, cfg, arena, M, 0, 0, false));
+          CV_TRY(digest_job(ctx, cfg_i, sig, job, dig, trivial, counters + 3, stream, tmp));
+        }
         const unsigned g = grid_for(M, 256, ctx->sms);
         if (tau) {
           tau_kernel<<<g, 256, 0, stream>>>(file_base_d, n_files, M, tau);
@@ -270,13 +280,16 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
                                           n_files, (uint4*)m->slots, (uint2*)m->postings, counters + 2);
         CV_CUDA(cudaGetLastError());
         if (sig_is_weak(sig)) {
-          // a copy of the kept master sectors in posting order, to confirm matches byte for byte
-          CV_CUDA(cudaMalloc(&m->confirm, M * kSector));
-          gather_sectors_kernel<<<grid_for(M * (kSector / 16), 256, ctx->sms), 256, 0, stream>>>(
-              (const uint4*)arena, kin, vin, M, (uint32_t)n_slots, (uint4*)m->confirm);
+          // a copy of the kept master units in posting order, to confirm matches byte for byte
+          CV_CUDA(cudaMalloc(&m->confirm, M * U));
+          gather_units_kernel<<<grid_for(M * (U / 16), 256, ctx->sms), 256, 0, stream>>>(
+              (const uint4*)arena, kin, vin, M, (uint32_t)n_slots, (uint32_t)(U / 16), (uint4*)m->confirm);
           CV_CUDA(cudaGetLastError());
         }
-        if (bpk) {
+        if (bpk && frag) {
+          CV_CUDA((cudaError_t)frag_bloom((const uint4*)m->slots, (uint32_t)n_slots, (uint32_t*)m->bloom,
+                                          (uint32_t)(n_blocks - 1), ctx->sms, stream));
+        } else if (bpk) {
           bloom_kernel<<<grid_for(n_slots, 256, ctx->sms), 256, 0, stream>>>((const uint4*)m->slots,
                                                                              (uint32_t)n_slots, (uint32_t*)m->bloom,
                                                                              (uint32_t)(n_blocks - 1));
@@ -333,6 +346,8 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       m->tab.sig = (uint32_t)sig;
       m->tab.confirm = (const uint8_t*)m->confirm;
       m->tab.tau_mask = by_tau ? 7u : 0u;
+      m->tab.unit = unit;
+      m->info.unit = unit;
       m->tab.tau_add = 0u;
       m->info.signature = (uint32_t)sig;
       m->info.position_mode = position_mode;
@@ -341,14 +356,14 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       m->info.n_kept = hc[1];
       m->info.n_unique = hc[2];
       m->info.n_slots = n_slots;
-      m->info.bloom_bytes = n_blocks * 32;
+      m->info.bloom_bytes = n_blocks * block_bytes;
       m->info.max_probe = layout == CV_LAYOUT_SORTED ? steps : hc[0] + 1;
       m->info.layout = layout;
       const uint64_t table_bytes =
           layout == CV_LAYOUT_SORTED ? std::max<uint64_t>(hc[2], 1) * 36 : n_slots * 32;
       if (layout == CV_LAYOUT_SORTED) m->info.n_slots = hc[2];
-      m->info.device_bytes = table_bytes + std::max<uint64_t>(M, 1) * 8 + n_blocks * 32 +
-                             (m->confirm ? M * kSector : 0);
+      m->info.device_bytes = table_bytes + std::max<uint64_t>(M, 1) * 8 + n_blocks * block_bytes +
+                             (m->confirm ? M * U : 0);
       return CV_OK;
     };
     rc = body();
@@ -406,6 +421,144 @@ int master_view(const cv_master* m, TableView* tab, int* dev) {
 }
 }  // namespace cvk
 
+namespace {
+
+// cv_scan over a fragment table (Section 5): count kernel per image, one offset scan over all
+// tiles, emit kernel per image over its tiles with triples. Host images are copied whole.
+int frag_scan(DevCtx* ctx, const cv_master* m, const cv_buf* images, uint32_t n_images, uint32_t flags,
+              cudaStream_t stream, cv_result** out) {
+  Temps staging(ctx, stream);
+  std::vector<const uint8_t*> dptr(n_images, nullptr);
+  std::vector<uint64_t> nbytes(n_images, 0), tile_base(n_images + 1, 0);
+  uint64_t windows = 0, max_tiles = 0;
+  for (uint32_t i = 0; i < n_images; i++) {
+    nbytes[i] = images[i].n_bytes;
+    const uint64_t t = frag_tiles(nbytes[i]);
+    tile_base[i + 1] = tile_base[i] + t;
+    max_tiles = std::max(max_tiles, t);
+    windows += frag_windows(nbytes[i]);
+    if (!t) continue;
+    if (!images[i].data) return CV_EINVAL;
+    BufKind kind;
+    CV_TRY(classify(ctx, images[i].data, &kind));
+    if (kind == kHost) {
+      uint8_t* copy;
+      CV_TRY(staging.alloc(&copy, nbytes[i]));
+      CV_CUDA(cudaMemcpyAsync(copy, images[i].data, nbytes[i], cudaMemcpyHostToDevice, stream));
+      dptr[i] = copy;
+    } else {
+      if ((uintptr_t)images[i].data & 15u) return CV_EINVAL;
+      dptr[i] = (const uint8_t*)images[i].data;
+    }
+  }
+  const uint64_t T = tile_base[n_images];
+  if (T >= (1ull << 32)) return CV_EINVAL;
+
+  cv_result* r = new (std::nothrow) cv_result();
+  if (!r) return CV_ENOMEM;
+  r->magic = kMagicResult;
+  r->dev = ctx->dev;
+  r->on_device = (flags & CV_KEEP_ON_DEVICE) != 0;
+  r->n_images = n_images;
+  r->off.assign(n_images + 1, 0);
+  r->host = nullptr;
+  r->dev_out = nullptr;
+  r->free_stream = stream;
+  memset(&r->st, 0, sizeof r->st);
+  r->launches = 0;
+  r->st.sectors = windows;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int rc;
+  {
+    Temps tmp(ctx, stream);
+    auto body = [&]() -> int {
+      for (auto& e : ev) CV_CUDA(cudaEventCreate(&e));
+      CV_CUDA(cudaEventRecord(ev[0], stream));
+      uint64_t *tile_ntrip, *tile_off, *seg_off_d, *scratch;
+      uint32_t* list;
+      Segment* segs_d;
+      CV_TRY(tmp.alloc(&tile_ntrip, std::max<uint64_t>(T, 1) * 8));
+      CV_TRY(tmp.alloc(&tile_off, std::max<uint64_t>(T, 1) * 8));
+      CV_TRY(tmp.alloc(&seg_off_d, (n_images + 2) * 8));  // seg_off[n], total, status
+      CV_TRY(tmp.alloc(&scratch, tile_offsets_scratch_words(T) * 8 + 8));
+      CV_TRY(tmp.alloc(&list, (max_tiles + 1) * 4));
+      CV_TRY(tmp.alloc(&segs_d, std::max<uint32_t>(n_images, 1) * sizeof(Segment)));
+      std::vector<Segment> segs(n_images);
+      memset(segs.data(), 0, segs.size() * sizeof(Segment));
+      for (uint32_t i = 0; i < n_images; i++) {
+        segs[i].tile_base = tile_base[i];
+        segs[i].image = i;
+      }
+      if (n_images)
+        CV_CUDA(cudaMemcpyAsync(segs_d, segs.data(), n_images * sizeof(Segment), cudaMemcpyHostToDevice, stream));
+      uint32_t* status = (uint32_t*)(seg_off_d + n_images + 1);
+      CV_CUDA(cudaMemsetAsync(status, 0, 8, stream));
+      CV_CUDA(cudaEventRecord(ev[1], stream));
+      for (uint32_t i = 0; i < n_images; i++) {
+        if (tile_base[i + 1] == tile_base[i]) continue;
+        CV_CUDA((cudaError_t)frag_count(m->tab, dptr[i], nbytes[i], tile_base[i], tile_ntrip, status, ctx->sms, stream));
+        r->launches++;
+      }
+      CV_CUDA(cudaEventRecord(ev[2], stream));
+      CV_CUDA((cudaError_t)launch_tile_offsets(tile_ntrip, T, tile_off, segs_d, n_images, 1, seg_off_d,
+                                               seg_off_d + n_images, scratch, stream));
+      r->launches += 4;
+      std::vector<uint64_t> seg_off(n_images + 2, 0);
+      CV_CUDA(cudaMemcpyAsync(seg_off.data(), seg_off_d, (n_images + 2) * 8, cudaMemcpyDeviceToHost, stream));
+      CV_CUDA(cudaStreamSynchronize(stream));
+      const uint32_t st = (uint32_t)seg_off[n_images + 1];
+      if (st & kStTimeout) return CV_ETIMEOUT;
+      if (st) return CV_ECORRUPT;
+      const uint64_t total = seg_off[n_images];
+      if (total) {
+        CV_CUDA(cudaMallocFromPoolAsync((void**)&r->dev_out, total * sizeof(MatchOut), ctx->pool, stream));
+        for (uint32_t i = 0; i < n_images; i++) {
+          if (tile_base[i + 1] == tile_base[i]) continue;
+          CV_CUDA((cudaError_t)frag_emit(m->tab, dptr[i], nbytes[i], tile_base[i], tile_ntrip, tile_off, list,
+                                         r->dev_out, total, status, ctx->sms, stream, &r->launches));
+        }
+      }
+      for (uint32_t i = 0; i < n_images; i++) r->off[i] = seg_off[i];
+      r->off[n_images] = total;
+      r->st.matches = total;
+      if (total && !r->on_device) {
+        r->host = (MatchOut*)malloc(total * sizeof(MatchOut));
+        if (!r->host) return CV_ENOMEM;
+        CV_CUDA(cudaMemcpyAsync(r->host, r->dev_out, total * sizeof(MatchOut), cudaMemcpyDeviceToHost, stream));
+      }
+      uint32_t st2 = 0;
+      CV_CUDA(cudaMemcpyAsync(&st2, status, 4, cudaMemcpyDeviceToHost, stream));
+      CV_CUDA(cudaEventRecord(ev[3], stream));
+      CV_CUDA(cudaStreamSynchronize(stream));
+      if (st2 & kStTimeout) return CV_ETIMEOUT;
+      if (st2) return CV_ECORRUPT;
+      float ms = 0.f;
+      CV_CUDA(cudaEventElapsedTime(&ms, ev[1], ev[2]));
+      r->st.kernel_ms = ms;
+      CV_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[3]));
+      r->st.total_ms = ms;
+      r->st.kernel_launches = (uint32_t)r->launches;
+      if (total && !r->on_device) {
+        CV_CUDA(cudaFreeAsync(r->dev_out, stream));
+        r->dev_out = nullptr;
+      }
+      return CV_OK;
+    };
+    rc = body();
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (rc != CV_OK) {
+    cudaStreamSynchronize(stream);
+    cv_free(r);
+    return rc;
+  }
+  *out = r;
+  return CV_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int cv_master_get_info(const cv_master* m, cv_master_info* info) {
@@ -427,6 +580,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
   DevCtx* ctx;
   CV_TRY(get_ctx(&ctx));
   if (ctx->dev != m->dev) return CV_EINVAL;
+  if (m->tab.unit == kUnitFragment) return frag_scan(ctx, m, images, n_images, flags, stream, out);
   int ncfg;
   scan_configs(&ncfg);
   int cfg_i = ctx->cfg_index;

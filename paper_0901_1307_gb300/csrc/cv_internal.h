@@ -46,6 +46,9 @@ __host__ __device__ constexpr bool sig_is_weak(int sig) { return sig == kSigDjb2
 //          keys0 (the alternative to linear probing for high occupancy, Section 4), then a
 //          comparison of the records whose h0 is equal.
 enum : uint32_t { kLayoutHash = 0, kLayoutSorted = 1 };
+// What a table's keys are: 512-byte sectors, or 64-byte fragments (a fragment table's Bloom
+// filter is one u32 word per block, 3 bits per key: word d3 & bloom_mask, bits from d2).
+enum : uint32_t { kUnitSector = 0, kUnitFragment = 1 };
 
 struct TableView {
   const uint4* slots;
@@ -62,7 +65,7 @@ struct TableView {
   uint32_t tau_add;    // (8 - base_offset mod 8) mod 8: disk sector g sits at position (g + tau_add) & 7
   uint32_t layout;     // kLayout*
   uint32_t n_keys;     // sorted layout: records in slots and keys0
-  uint32_t pad;
+  uint32_t unit;       // kUnitSector or kUnitFragment
 };
 
 // Position-keyed tables (Section 3.1: one table S_tau per sector position tau of an 8-sector
@@ -84,6 +87,22 @@ __host__ __device__ inline void sig64_words(uint64_t h, uint32_t w[4]) {
   w[1] = (uint32_t)(h >> 32);
   w[2] = (uint32_t)z;
   w[3] = (uint32_t)(z >> 32);
+}
+
+// Fragment workloads (Section 5): 64-byte windows at every 4-byte offset of an image against
+// the whole 64-byte fragments of the master files.
+constexpr uint32_t kFrag = 64;
+constexpr uint32_t kFragStride = 4;
+
+// The four table words of a fragment's 64-bit signature h: h itself (low word first: the home
+// slot is given by the signature's least significant bits, Eq. 3) and h times an odd constant,
+// whose high bits (mixing every bit of h) choose the Bloom word and bits. Equal words <=> equal h.
+__host__ __device__ inline void frag64_words(uint64_t h, uint32_t w[4]) {
+  const uint64_t f = h * 0x9E3779B97F4A7C15ull;
+  w[0] = (uint32_t)h;
+  w[1] = (uint32_t)(h >> 32);
+  w[2] = (uint32_t)f;
+  w[3] = (uint32_t)(f >> 32);
 }
 
 // Byte-for-byte comparison of two device sectors (16-byte aligned).

@@ -6,6 +6,21 @@
 
 namespace cvk {
 
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing completes. The
+// wait gives up after timeout_ns, sets kStTimeout and the kernel returns normally.
+__global__ void wait_timeout_selftest_kernel(uint32_t* status, uint64_t timeout_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t abort_flag;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mbar_init(smem_addr(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const bool ok = mbar_wait(smem_addr(&bar), 0, &abort_flag, status, timeout_ns);
+    if (ok) atomicOr(status, kStProbeBound);  // must not happen: nothing arrives
+  }
+}
+
+
 #define CV_KS(T, SPT, NS, B, MODE, P, MB, SIG) (const void*)scan_kernel<T, SPT, NS, B, MODE, P, MB, SIG, kLayoutHash>
 #define CV_KSS(T, SPT, NS, B, P, MB, SIG) (const void*)scan_kernel<T, SPT, NS, B, kModeScan, P, MB, SIG, kLayoutSorted>
 

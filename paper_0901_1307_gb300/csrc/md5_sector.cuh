@@ -152,6 +152,15 @@ __device__ __forceinline__ void md5_compress_sector_padding(uint32_t (&st)[4]) {
   md5_compress<0>(st, X);
 }
 
+// The padding block of a message that is exactly one 64-byte block long (bit length 512).
+__device__ __forceinline__ void md5_compress_block_padding(uint32_t (&st)[4]) {
+  constexpr uint32_t P[16] = {0x80u, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 512u, 0};
+  uint32_t X[16];
+#pragma unroll
+  for (int j = 0; j < 16; j++) X[j] = P[j];
+  md5_compress<0>(st, X);
+}
+
 __device__ __forceinline__ void md5_init(uint32_t (&st)[4]) {
   st[0] = kMd5A0;
   st[1] = kMd5B0;

@@ -113,7 +113,7 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   *n_out = 0;
   TableView tab;
   int mdev;
-  if (master_view(m, &tab, &mdev) != CV_OK) return CV_EINVAL;
+  if (master_view(m, &tab, &mdev) != CV_OK || tab.unit != kUnitSector) return CV_EINVAL;
   int dev;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
     cudaGetLastError();

@@ -204,15 +204,16 @@ __global__ void fill_kernel(const uint32_t* keys, const uint32_t* vals, uint64_t
   }
 }
 
-// Kept master sectors in posting order: posting q (sorted pair q, key < n_slots) is master
-// sector vals[q]; its 512 bytes go to out + 512 q. One thread per 16-byte word.
-__global__ void gather_sectors_kernel(const uint4* arena, const uint32_t* keys, const uint32_t* vals, uint64_t n,
-                                      uint32_t n_slots, uint4* out) {
-  const uint64_t words = n * (kSector / 16);
+// Kept master units (sectors or fragments of wpu 16-byte words) in posting order: posting q
+// (sorted pair q, key < n_slots) is master unit vals[q]; its words go to out + wpu q. One thread
+// per 16-byte word.
+__global__ void gather_units_kernel(const uint4* arena, const uint32_t* keys, const uint32_t* vals, uint64_t n,
+                                    uint32_t n_slots, uint32_t wpu, uint4* out) {
+  const uint64_t words = n * wpu;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t q = i / (kSector / 16);
+    const uint64_t q = i / wpu;
     if (keys[q] >= n_slots) continue;
-    out[i] = arena[(uint64_t)vals[q] * (kSector / 16) + i % (kSector / 16)];
+    out[i] = arena[(uint64_t)vals[q] * wpu + i % wpu];
   }
 }
 

@@ -31,6 +31,7 @@ CV_SIG_MD5, CV_SIG_MD5_NOPAD, CV_SIG_DJB2_64, CV_SIG_CRC64 = 0, 1, 2, 3
 CV_KEEP_ON_DEVICE = 1
 CV_POSITION_ANY, CV_POSITION_CLUSTER = 0, 1
 CV_LAYOUT_HASH, CV_LAYOUT_SORTED = 0, 1
+CV_UNIT_SECTOR, CV_UNIT_FRAGMENT = 0, 1
 SECTOR = 512
 
 MATCH_DTYPE = np.dtype([("disk_sector", "<u8"), ("file_id", "<u4"), ("file_sector", "<u4")])
@@ -59,7 +60,8 @@ class cv_buf(ctypes.Structure):
 class cv_master_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("max_load", ctypes.c_float),
                 ("bloom_bits_per_key", ctypes.c_uint32), ("signature", ctypes.c_uint32), ("stream", ctypes.c_void_p),
-                ("position_mode", ctypes.c_uint32), ("layout", ctypes.c_uint32)]
+                ("position_mode", ctypes.c_uint32), ("layout", ctypes.c_uint32), ("unit", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
 
 class cv_scan_opts(ctypes.Structure):
@@ -72,7 +74,7 @@ class cv_master_info(ctypes.Structure):
     _fields_ = [("n_files", ctypes.c_uint32), ("position_mode", ctypes.c_uint32), ("n_sectors", ctypes.c_uint64),
                 ("n_kept", ctypes.c_uint64), ("n_unique", ctypes.c_uint64), ("n_slots", ctypes.c_uint64),
                 ("bloom_bytes", ctypes.c_uint64), ("max_probe", ctypes.c_uint32), ("signature", ctypes.c_uint32),
-                ("device_bytes", ctypes.c_uint64), ("layout", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("device_bytes", ctypes.c_uint64), ("layout", ctypes.c_uint32), ("unit", ctypes.c_uint32)]
 
 
 class cv_scan_stats(ctypes.Structure):
@@ -323,13 +325,15 @@ class Result:
 
 def master_build(files, max_load: float = 0.0, bloom_bits_per_key: int = CV_BLOOM_AUTO, stream=None,
                  signature: int = CV_SIG_MD5, position_mode: int = CV_POSITION_ANY,
-                 layout: int = CV_LAYOUT_HASH) -> Master:
+                 layout: int = CV_LAYOUT_HASH, unit: int = CV_UNIT_SECTOR) -> Master:
     """cv_master_build: the signature table of a list of master files (one table over all sector
     positions, or with position_mode=CV_POSITION_CLUSTER the tables S_tau of Section 3.1), as a
-    linear-probing hash table or (layout=CV_LAYOUT_SORTED) a sorted array searched by bisection."""
+    linear-probing hash table or (layout=CV_LAYOUT_SORTED) a sorted array searched by bisection.
+    unit=CV_UNIT_FRAGMENT cuts the files into 64-byte fragments instead of 512-byte sectors, and
+    scans then look up every 64-byte window at a 4-byte offset (Section 5)."""
     arr, keep = _bufs(list(files))
     o = cv_master_opts(ctypes.sizeof(cv_master_opts), max_load, bloom_bits_per_key, signature, _stream(stream),
-                       position_mode, layout)
+                       position_mode, layout, unit, 0)
     h = ctypes.c_void_p()
     _check(load().cv_master_build(arr, len(files), ctypes.byref(o), ctypes.byref(h)), "cv_master_build")
     del keep
