@@ -315,6 +315,55 @@ def run_tables(torch, cv, synth, plan, image, stream, steps):
     return out
 
 
+FRAG_OPS_PER_WINDOW_DJB2 = 31  # rolled djb2 step, key mix and one-word Bloom test (see DESIGN)
+
+
+def run_fragments(torch, cv, synth, stream, steps, cpu_sample_bytes, config="frag", sigs=(2, 1, 0)):
+    """Section 5's fragment scan on the 4 GiB fragment workload: every 64-byte window at a 4-byte
+    offset against the 64-byte fragments of 2,000 logos, for djb2-64 (rolled, confirmed), MD5
+    without padding and MD5, each checked against the plant log."""
+    import oracle
+
+    fp = synth.frag_config(config)
+    image = torch.empty(fp.n_bytes, dtype=torch.uint8, device="cuda")
+    fp.image_device(torch, image)
+    logos = fp.logos()
+    exp = fp.expected_planted()
+    windows = (fp.n_bytes - 64) // 4 + 1
+    out = {"workload": "%s: %d-byte image, %d logos of log-uniform 1-16 KiB (%d fragments), half planted "
+                       "1-3 times at 4-byte-aligned offsets" % (config, fp.n_bytes, fp.n_logos,
+                                                               sum(x.size // 64 for x in logos)),
+           "windows": windows}
+    names = {2: "djb2_64", 1: "md5_nopad", 0: "md5"}
+    for sig in sigs:
+        name = names[sig]
+        m = cv.master_build(logos, signature=sig, unit=cv.CV_UNIT_FRAGMENT)
+        n_steps = steps if sig == 2 else max(2, steps // 5)
+        wall, kms, matches = time_scans(torch, cv, m, image, stream, n_steps)
+        r = cv.scan(m, [image], stream=stream)
+        got = r.matches(0)
+        r.close()
+        planted_found = bool(np.isin(exp.view(np.dtype((np.void, 16))), got.view(np.dtype((np.void, 16)))).all())
+        out[name] = {"GBps": fp.n_bytes / wall / 1e9, "count_kernel_GBps": fp.n_bytes / (kms * 1e-3) / 1e9,
+                     "windows_per_s": windows / wall, "matches": matches, "planted_triples": int(exp.size),
+                     "all_planted_found": planted_found}
+        if sig == 2:
+            out[name]["achieved_Tops_est"] = windows * FRAG_OPS_PER_WINDOW_DJB2 / (kms * 1e-3) / 1e12
+        m.close()
+    if not cpu_sample_bytes:
+        return out
+    # the oracle on a bounded sample of the same image (all host cores)
+    sample = image[:cpu_sample_bytes].cpu().numpy()
+    t0 = time.perf_counter()
+    oracle.frag_match(sample, logos)
+    dt = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": sample.size / dt / 1e9, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
+                           "sample": f"the first {sample.size >> 20} MiB of the image"}
+    del image
+    torch.cuda.synchronize()
+    return out
+
+
 def run_batched(torch, cv, synth, args, stream):
     """512 device images of uneven sizes (one device arena) against one 8M-sector table: one CUDA
     graph launch per run, autotuned, against 512 sequential cv_scan calls on the same images."""
@@ -460,6 +509,13 @@ def main():
     ap.add_argument("--no-sigs", action="store_true")
     ap.add_argument("--sig-steps", type=int, default=20)
     ap.add_argument("--no-tables", action="store_true")
+    ap.add_argument("--no-frag", action="store_true")
+    ap.add_argument("--frag-steps", type=int, default=10)
+    ap.add_argument("--frag-cpu-mib", type=int, default=256)
+    ap.add_argument("--frag-only", action="store_true",
+                    help="run only the fragment scan (--frag-config, --frag-sigs) and print its JSON")
+    ap.add_argument("--frag-config", default="frag")
+    ap.add_argument("--frag-sigs", default="2,1,0")
     ap.add_argument("--table-steps", type=int, default=10)
     ap.add_argument("--batch-images", type=int, default=512)
     ap.add_argument("--batch-total-gib", type=int, default=64)
@@ -475,6 +531,18 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args)
+    if args.frag_only:
+        import torch
+
+        import __graft_entry__
+
+        __graft_entry__.build()
+        from paper_0901_1307_gb300 import cv, synth
+
+        sigs = tuple(int(x) for x in args.frag_sigs.split(","))
+        print(json.dumps(run_fragments(torch, cv, synth, torch.cuda.current_stream(), args.frag_steps,
+                                       args.frag_cpu_mib << 20, args.frag_config, sigs)))
+        return 0
 
     import torch
 
@@ -554,6 +622,11 @@ def main():
         e2e = {"value": world * nbytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
 
+    frags = None
+    if not args.no_frag and rank == 0:
+        frags = run_fragments(torch, cv, synth, stream, args.frag_steps, args.frag_cpu_mib << 20, args.frag_config,
+                              tuple(int(x) for x in args.frag_sigs.split(",")))
+
     ip = cv.int_peak()
     int_peak = {k: ip[k] / 1e12 for k in ("alu_ops_per_s", "fma_ops_per_s", "mixed_ops_per_s")}
     int_peak.update({"unit": "Top/s", "sm_clock_mhz": ip["sm_clock_mhz"],
@@ -591,6 +664,7 @@ def main():
         "e2e": e2e,
         "signatures": sigs,
         "tables": tables,
+        "fragments": frags,
         "gpu_launches": launches,
     }
     master.close()

@@ -46,6 +46,7 @@ struct cv_master {
   void* bloom;
   void* confirm;  // kept master sectors in posting order (64-bit signatures)
   void* keys0;    // sorted layout: h0 of every record
+  void* frag_l1;  // fragment tables: the shared-memory filter
   cv_master_info info;
 };
 
@@ -286,9 +287,12 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
               (const uint4*)arena, kin, vin, M, (uint32_t)n_slots, (uint32_t)(U / 16), (uint4*)m->confirm);
           CV_CUDA(cudaGetLastError());
         }
-        if (bpk && frag) {
+        if (frag) {
+          CV_CUDA(cudaMalloc(&m->frag_l1, kFragL1Bytes));
+          CV_CUDA(cudaMemsetAsync(m->frag_l1, 0, kFragL1Bytes, stream));
           CV_CUDA((cudaError_t)frag_bloom((const uint4*)m->slots, (uint32_t)n_slots, (uint32_t*)m->bloom,
-                                          (uint32_t)(n_blocks - 1), ctx->sms, stream));
+                                          bpk ? (uint32_t)(n_blocks - 1) : 0u, (uint32_t*)m->frag_l1, ctx->sms,
+                                          stream));
         } else if (bpk) {
           bloom_kernel<<<grid_for(n_slots, 256, ctx->sms), 256, 0, stream>>>((const uint4*)m->slots,
                                                                              (uint32_t)n_slots, (uint32_t*)m->bloom,
@@ -347,6 +351,7 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       m->tab.confirm = (const uint8_t*)m->confirm;
       m->tab.tau_mask = by_tau ? 7u : 0u;
       m->tab.unit = unit;
+      m->tab.frag_l1 = (const uint32_t*)m->frag_l1;
       m->info.unit = unit;
       m->tab.tau_add = 0u;
       m->info.signature = (uint32_t)sig;
@@ -363,7 +368,7 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
           layout == CV_LAYOUT_SORTED ? std::max<uint64_t>(hc[2], 1) * 36 : n_slots * 32;
       if (layout == CV_LAYOUT_SORTED) m->info.n_slots = hc[2];
       m->info.device_bytes = table_bytes + std::max<uint64_t>(M, 1) * 8 + n_blocks * block_bytes +
-                             (m->confirm ? M * U : 0);
+                             (m->confirm ? M * U : 0) + (m->frag_l1 ? kFragL1Bytes : 0);
       return CV_OK;
     };
     rc = body();
@@ -433,7 +438,7 @@ int frag_scan(DevCtx* ctx, const cv_master* m, const cv_buf* images, uint32_t n_
   uint64_t windows = 0, max_tiles = 0;
   for (uint32_t i = 0; i < n_images; i++) {
     nbytes[i] = images[i].n_bytes;
-    const uint64_t t = frag_tiles(nbytes[i]);
+    const uint64_t t = frag_tiles((int)m->tab.sig, nbytes[i]);
     tile_base[i + 1] = tile_base[i] + t;
     max_tiles = std::max(max_tiles, t);
     windows += frag_windows(nbytes[i]);
@@ -827,6 +832,7 @@ void cv_free(void* handle) {
     if (m->bloom) cudaFree(m->bloom);
     if (m->confirm) cudaFree(m->confirm);
     if (m->keys0) cudaFree(m->keys0);
+    if (m->frag_l1) cudaFree(m->frag_l1);
     free(m);
   } else if (magic == kMagicResult) {
     cv_result* r = (cv_result*)handle;

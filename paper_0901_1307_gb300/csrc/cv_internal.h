@@ -56,6 +56,7 @@ struct TableView {
   const uint4* bloom;
   const uint8_t* confirm;
   const uint32_t* keys0;  // sorted layout only
+  const uint32_t* frag_l1;  // fragment tables: the shared-memory filter (kFragL1Bytes)
   uint32_t slot_mask;
   uint32_t bloom_mask;
   uint32_t max_probe;  // hash: no stored digest sits further than max_probe - 1 slots from home
@@ -93,6 +94,9 @@ __host__ __device__ inline void sig64_words(uint64_t h, uint32_t w[4]) {
 // the whole 64-byte fragments of the master files.
 constexpr uint32_t kFrag = 64;
 constexpr uint32_t kFragStride = 4;
+// The shared-memory filter of a fragment table: 2^20 bits (128 KiB), bit = top 20 bits of d1.
+constexpr uint32_t kFragL1Log2Bits = 20;
+constexpr uint32_t kFragL1Bytes = (1u << kFragL1Log2Bits) / 8;
 
 // The four table words of a fragment's 64-bit signature h: h itself (low word first: the home
 // slot is given by the signature's least significant bits, Eq. 3) and h times an odd constant,

@@ -47,14 +47,16 @@ int launch_tile_offsets(const uint64_t* tile_ntrip, uint64_t n_tiles, uint64_t* 
                         void* stream);
 
 // ---------------------------------------------------------------- fragment scans (Section 5)
-uint64_t frag_windows(uint64_t n_bytes);  // 64-byte windows at 4-byte offsets in n_bytes
-uint64_t frag_tiles(uint64_t n_bytes);    // tiles of the fragment kernels over those windows
+uint64_t frag_windows(uint64_t n_bytes);       // 64-byte windows at 4-byte offsets in n_bytes
+uint64_t frag_tiles(int sig, uint64_t n_bytes);  // tiles of sig's fragment kernels over those windows
 bool frag_sig_supported(int sig);         // MD5, MD5 without padding, djb2-64
 
 // Key words and exclusion flags of n master fragments at arena (64 bytes each, 16-byte aligned).
 int frag_digests(int sig, const uint8_t* arena, uint64_t n, uint4* dig, uint8_t* trivial, int sms, void* stream);
-// The one-word Bloom filter of a fragment table (words zeroed by the caller; mask = words - 1).
-int frag_bloom(const uint4* slots, uint32_t n_slots, uint32_t* words, uint32_t mask, int sms, void* stream);
+// The filters of a fragment table (zeroed by the caller): the one-word Bloom filter (words, null
+// for none; mask = words - 1) and the shared-memory filter l1 (kFragL1Bytes).
+int frag_bloom(const uint4* slots, uint32_t n_slots, uint32_t* words, uint32_t mask, uint32_t* l1, int sms,
+               void* stream);
 // Triples per tile of one device image (16-byte aligned) into tile_ntrip[tile_base ..).
 int frag_count(const TableView& tab, const uint8_t* image, uint64_t n_bytes, uint64_t tile_base, uint64_t* tile_ntrip,
                uint32_t* status, int sms, void* stream);

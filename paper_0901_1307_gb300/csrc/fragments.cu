@@ -2,22 +2,30 @@
 // multiple of 4 bytes is looked up among the whole 64-byte fragments of the master files, to
 // find small files (logos, small images) embedded in other files at any 32-bit offset.
 //
-// Work layout. A tile is kFragTileWin = 256 x 33 consecutive windows: 33,792 bytes of window
-// starts, 33,856 bytes staged (the last window's tail). One 1-D bulk TMA copy per tile brings
-// the bytes into shared memory, double-buffered over a persistent grid with mbarrier completion
-// and bounded waits. Thread t takes windows [33 t, 33 t + 33) of the tile; with an odd count the
-// 32 threads of a warp read 32 different banks at every step.
+// Work layout. A tile is one warp's work: 32 x WPT consecutive windows. Each warp stages its own
+// tiles (the window starts plus the last window's 60-byte tail) into its own two shared-memory
+// buffers with 1-D bulk TMA copies issued by its lane 0, completion on the warp's own mbarriers,
+// every wait bounded; warps of a block never wait for one another, so a warp that meets a
+// candidate (an L2 probe) holds up no one. Lane l takes windows [WPT l, WPT l + WPT) of the tile;
+// with WPT odd the 32 lanes read 32 different banks at every step. Tiles are spread over every
+// warp of a persistent grid.
 //
 //   djb2-64 (Eq. 1) is rolled. With P(x) the base-33 Horner value of a 4-byte word x and
 //   g = h - 5381 * 33^64, a window W_k of words x_k .. x_{k+15} has g(W_k) = sum_q
 //   P(x_{k+q}) 33^{4 (15 - q)}, so g(W_{k+1}) = 33^4 g(W_k) - 33^64 P(x_k) + P(x_{k+16})
-//   (mod 2^64): after a thread's first window each one costs one word and a few multiply-adds.
-//   MD5 is computed per window (two compressions, or one without the padding block).
+//   (mod 2^64): after a lane's first window each one costs one word and a few multiply-adds.
+//   A rolled window is cheap enough that its Bloom lookup, not its hash, sets the pace, and an
+//   SM keeps only so many L2 misses in flight: so the djb2 kernel first tests a 2^20-bit filter
+//   held in shared memory (loaded once per block) and sends only the windows that pass it to
+//   the one-word Bloom filter in global memory.
+//   MD5 is computed per window (two compressions, or one without the padding block); there the
+//   hash dominates and the global Bloom word is tested directly.
 //
-// Passes (no worst-case hit buffer). The count kernel hashes every window, tests its key in a
-// one-word Bloom filter, resolves the candidates (probe; byte confirmation for djb2) and writes
-// the tile's triple count. An exclusive scan gives every tile its output offset. The emit kernel
-// redoes only the tiles that have triples and writes them in window order.
+// Passes (no worst-case hit buffer). The count kernel hashes every window, filters it, resolves
+// the candidates (probe; byte confirmation for djb2) and writes each tile's triple count; an
+// exclusive scan gives every tile its output offset; the emit kernel redoes only the tiles
+// that have triples and writes them in window order. Filters never drop a match, so the emit
+// kernel, which skips the shared-memory filter, finds exactly the counted triples.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -28,13 +36,23 @@
 
 namespace cvk {
 
-constexpr int kFragThreads = 256;
-constexpr int kFragWPT = 33;                                    // windows per thread per tile
-constexpr uint32_t kFragTileWin = kFragThreads * kFragWPT;      // 8448
-constexpr uint32_t kFragTileStep = kFragTileWin * kFragStride;  // bytes between tile starts
-constexpr uint32_t kFragTileBytes = kFragTileStep + 64;         // bytes staged per tile
-constexpr uint32_t kFragSmemCount = 2 * kFragTileBytes;         // two stages
-constexpr uint32_t kFragSmemEmit = kFragTileBytes;
+// Tile geometry per signature (a tile is one warp's work).
+template <int SIG>
+struct FragGeom {
+  static constexpr bool kRolled = SIG == kSigDjb2;
+  static constexpr int kThreads = kRolled ? 512 : 256;  // block size
+  static constexpr int kWarps = kThreads / 32;
+  static constexpr int kWPT = kRolled ? 17 : 33;        // windows per lane per tile (odd)
+  static constexpr uint32_t kTileWin = 32 * kWPT;
+  static constexpr uint32_t kTileStep = kTileWin * kFragStride;  // bytes between tile starts
+  static constexpr uint32_t kTileBytes = kTileStep + 64;         // bytes staged per tile
+  static constexpr bool kL1 = kRolled;                           // shared-memory filter
+  static constexpr uint32_t kL1Off = 2 * kWarps * kTileBytes;    // filter after the warps' buffers
+  static constexpr uint32_t kSmemCount = kL1Off + (kL1 ? kFragL1Bytes : 0);
+  static constexpr uint32_t kSmemEmit = kWarps * kTileBytes;
+  static_assert(kWPT % 2 == 1 && kWPT <= 64 && (!kRolled || kWPT <= 32), "odd window count, masks of 64/32 bits");
+  static_assert(kTileBytes % 16 == 0 && kTileStep % 16 == 0, "bulk copies of whole 16-byte chunks");
+};
 
 __host__ __device__ constexpr uint64_t pow33(int e) {
   uint64_t r = 1;
@@ -71,15 +89,21 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
       : "memory");
 }
 
-// Base-33 Horner value of a little-endian word: byte 0 first (Eq. 1 over four bytes).
+// Base-33 Horner value of a little-endian word, byte 0 first (Eq. 1 over four bytes):
+// b0 33^3 + b1 33^2 + b2 33 + b3, as two 2-way (16-bit weight x 8-bit byte) dot products.
 __device__ __forceinline__ uint32_t horner33(uint32_t w) {
-  return (((w & 0xFFu) * 33u + ((w >> 8) & 0xFFu)) * 33u + ((w >> 16) & 0xFFu)) * 33u + (w >> 24);
+  constexpr uint32_t kW01 = (1089u << 16) | 35937u;  // 33^2 (byte 1), 33^3 (byte 0)
+  constexpr uint32_t kW23 = (1u << 16) | 33u;         // 1 (byte 3), 33 (byte 2)
+  return __dp2a_lo(kW01, w, __dp2a_hi(kW23, w, 0u));
+}
+
+__device__ __forceinline__ uint32_t frag_bloom_bits(uint32_t d2) {
+  return (1u << (d2 & 31)) | (1u << ((d2 >> 5) & 31)) | (1u << ((d2 >> 10) & 31));
 }
 
 __device__ __forceinline__ bool frag_bloom_test(const TableView& tab, uint32_t d2, uint32_t d3) {
-  const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(tab.bloom) + (d3 & tab.bloom_mask));
-  const uint32_t m = (1u << (d2 & 31)) | (1u << ((d2 >> 5) & 31)) | (1u << ((d2 >> 10) & 31));
-  return (w & m) == m;
+  const uint32_t bits = frag_bloom_bits(d2);
+  return (__ldg(reinterpret_cast<const uint32_t*>(tab.bloom) + (d3 & tab.bloom_mask)) & bits) == bits;
 }
 
 // Key words of the window whose first word is ws[w] (shared memory), computed directly.
@@ -110,13 +134,15 @@ __device__ __forceinline__ bool frag_equal(const uint32_t* ws, uint32_t w, const
   return diff == 0;
 }
 
-// Candidate windows of this thread (bit i: window w0 + i passed the Bloom test; every valid
-// window when the table has no filter). n_valid: the thread's windows inside the image.
+// Candidate windows of this thread (bit i: window w0 + i passed the filters; every valid window
+// when the table has no Bloom filter). n_valid: the thread's windows inside the image. l1: the
+// shared-memory filter, or null to skip it (then every window goes to the global Bloom word).
 template <int SIG>
 __device__ __forceinline__ uint64_t frag_candidates(const FragParams& p, const uint32_t* ws, uint32_t w0,
-                                                    uint32_t n_valid) {
+                                                    uint32_t n_valid, const uint32_t* l1) {
+  using G = FragGeom<SIG>;
   uint64_t cand = 0;
-  if constexpr (SIG == kSigDjb2) {
+  if constexpr (G::kRolled) {
     uint32_t P[16];
     uint64_t g = 0;
 #pragma unroll
@@ -124,17 +150,39 @@ __device__ __forceinline__ uint64_t frag_candidates(const FragParams& p, const u
       P[q] = horner33(ws[w0 + q]);
       g = g * kD33x4 + P[q];
     }
+    // Every window's shared-memory test first (its bit comes from h's high word, d1, with no
+    // further mixing); then, for those that passed, the mixed words d2, d3 and the global Bloom
+    // words, all requested before any is tested.
+    uint64_t h[G::kWPT];
+    uint32_t pass = 0;
 #pragma unroll
-    for (int i = 0; i < kFragWPT; i++) {
+    for (int i = 0; i < G::kWPT; i++) {
       if (i > 0) {
         const uint32_t pin = horner33(ws[w0 + i + 15]);
         g = g * kD33x4 - (uint64_t)P[(i - 1) & 15] * kD33x64 + pin;
         P[(i - 1) & 15] = pin;
       }
-      uint32_t d[4];
-      frag64_words(g + kDjbInit, d);
-      if ((uint32_t)i < n_valid && (!p.tab.use_bloom || frag_bloom_test(p.tab, d[2], d[3]))) cand |= 1ull << i;
+      h[i] = g + kDjbInit;
+      const uint32_t b = (uint32_t)(h[i] >> 32) >> (32 - kFragL1Log2Bits);
+      if ((uint32_t)i < n_valid && (!l1 || ((l1[b >> 5] >> (b & 31)) & 1u))) pass |= 1u << i;
     }
+    if (!p.tab.use_bloom) return pass;
+    const uint32_t* bloom = reinterpret_cast<const uint32_t*>(p.tab.bloom);
+    uint32_t wv[G::kWPT], wbits[G::kWPT];
+#pragma unroll
+    for (int i = 0; i < G::kWPT; i++) {
+      wv[i] = 0u;
+      wbits[i] = 1u;
+      if ((pass >> i) & 1u) {
+        uint32_t d[4];
+        frag64_words(h[i], d);
+        wbits[i] = frag_bloom_bits(d[2]);
+        wv[i] = __ldg(bloom + (d[3] & p.tab.bloom_mask));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < G::kWPT; i++)
+      if ((wv[i] & wbits[i]) == wbits[i]) cand |= 1ull << i;
   } else {
 #pragma unroll 1
     for (uint32_t i = 0; i < n_valid; i++) {
@@ -175,125 +223,133 @@ __device__ __forceinline__ uint64_t frag_thread_count(const FragParams& p, const
   return n;
 }
 
-__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src, bool up) {
-  uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
-  lo = up ? __shfl_up_sync(0xFFFFFFFFu, lo, src) : __shfl_sync(0xFFFFFFFFu, lo, src);
-  hi = up ? __shfl_up_sync(0xFFFFFFFFu, hi, src) : __shfl_sync(0xFFFFFFFFu, hi, src);
+__device__ __forceinline__ uint64_t shfl_up_u64(uint64_t v, int d) {
+  const uint32_t lo = __shfl_up_sync(0xFFFFFFFFu, (uint32_t)v, d);
+  const uint32_t hi = __shfl_up_sync(0xFFFFFFFFu, (uint32_t)(v >> 32), d);
   return ((uint64_t)hi << 32) | lo;
 }
 
-// Block-wide exclusive scan of one u64 per thread; *total receives the sum (all threads).
-__device__ __forceinline__ uint64_t block_exclusive_u64(uint64_t v, uint64_t* warp_sums, uint64_t* total) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// Warp-wide exclusive scan of one u64 per lane; *total receives the sum (every lane).
+__device__ __forceinline__ uint64_t warp_exclusive_u64(uint64_t v, uint64_t* total) {
+  const int lane = threadIdx.x & 31;
   uint64_t incl = v;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    const uint64_t x = shfl_u64(incl, d, true);
+    const uint64_t x = shfl_up_u64(incl, d);
     if (lane >= d) incl += x;
   }
-  if (lane == 31) warp_sums[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    constexpr int kWarps = kFragThreads / 32;
-    uint64_t s = lane < kWarps ? warp_sums[lane] : 0, si = s;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint64_t x = shfl_u64(si, d, true);
-      if (lane >= d) si += x;
-    }
-    if (lane < kWarps) warp_sums[lane] = si - s;
-    if (lane == kWarps - 1) warp_sums[kWarps] = si;
-  }
-  __syncthreads();
-  const uint64_t r = warp_sums[warp] + incl - v;
-  *total = warp_sums[kFragThreads / 32];
-  return r;
+  const uint32_t lo = __shfl_sync(0xFFFFFFFFu, (uint32_t)incl, 31);
+  const uint32_t hi = __shfl_sync(0xFFFFFFFFu, (uint32_t)(incl >> 32), 31);
+  *total = ((uint64_t)hi << 32) | lo;
+  return incl - v;
 }
 
-// Thread 0: issue tile `tile` into the stage at smem address dst (completion on bar).
+// Lane 0: issue tile `tile` into the buffer at smem address dst (completion on bar).
+template <int SIG>
 __device__ __forceinline__ void frag_issue(const FragParams& p, uint64_t tile, uint32_t dst, uint32_t bar,
                                            uint64_t policy) {
-  const uint64_t start = tile * kFragTileStep;
+  using G = FragGeom<SIG>;
+  const uint64_t start = tile * G::kTileStep;
   const uint64_t left = p.n_bytes - start;
-  const uint32_t avail = left < kFragTileBytes ? (uint32_t)left : kFragTileBytes;
+  const uint32_t avail = left < G::kTileBytes ? (uint32_t)left : G::kTileBytes;
   const uint32_t bulk = avail & ~15u;
   mbar_arrive_expect_tx(bar, bulk);
   if (bulk) bulk_load(dst, p.image + start, bulk, bar, policy);
 }
 
-// Thread 0: the bytes of the tile past its last whole 16-byte chunk (the bulk copy moves whole
-// chunks only), with plain loads.
+// The bytes of the tile past its last whole 16-byte chunk (the bulk copy moves whole chunks
+// only), with plain loads by the warp's lanes; only the image's last tile has any. Ends with a
+// warp barrier.
+template <int SIG>
 __device__ __forceinline__ void frag_tail(const FragParams& p, uint64_t tile, uint8_t* buf) {
-  const uint64_t start = tile * kFragTileStep;
+  using G = FragGeom<SIG>;
+  const uint64_t start = tile * G::kTileStep;
   const uint64_t left = p.n_bytes - start;
-  const uint32_t avail = left < kFragTileBytes ? (uint32_t)left : kFragTileBytes;
-  for (uint32_t b = avail & ~15u; b < avail; b++) buf[b] = p.image[start + b];
+  const uint32_t avail = left < G::kTileBytes ? (uint32_t)left : G::kTileBytes;
+  const uint32_t b = (avail & ~15u) + (threadIdx.x & 31);
+  if (b < avail) buf[b] = p.image[start + b];
+  __syncwarp();
 }
 
+template <int SIG>
 __device__ __forceinline__ uint32_t frag_valid(const FragParams& p, uint64_t tile, uint32_t w0) {
-  const uint64_t k0 = tile * kFragTileWin + w0;
+  using G = FragGeom<SIG>;
+  const uint64_t k0 = tile * G::kTileWin + w0;
   if (k0 >= p.n_windows) return 0u;
   const uint64_t left = p.n_windows - k0;
-  return left < (uint64_t)kFragWPT ? (uint32_t)left : (uint32_t)kFragWPT;
+  return left < (uint64_t)G::kWPT ? (uint32_t)left : (uint32_t)G::kWPT;
 }
 
 template <int SIG, int LAYOUT>
-__global__ void __launch_bounds__(kFragThreads) frag_count_kernel(const __grid_constant__ FragParams p) {
+__global__ void __launch_bounds__(FragGeom<SIG>::kThreads, 1) frag_count_kernel(const __grid_constant__ FragParams p) {
+  using G = FragGeom<SIG>;
   extern __shared__ __align__(128) uint8_t fsm[];
-  __shared__ __align__(8) uint64_t full[2];
-  __shared__ uint32_t abort_flag;
-  __shared__ uint64_t warp_sums[kFragThreads / 32 + 1];
-  const int tid = threadIdx.x;
+  __shared__ __align__(8) uint64_t bars[2 * G::kWarps + 1];  // two per warp, the shared-memory filter
+  __shared__ uint32_t abort_flag[G::kWarps + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t* l1 = G::kL1 ? reinterpret_cast<const uint32_t*>(fsm + G::kL1Off) : nullptr;
+  uint8_t* mybuf = fsm + 2 * warp * G::kTileBytes;
+  const uint32_t bar0 = smem_addr(&bars[2 * warp]);
   if (tid == 0) {
-    abort_flag = 0;
-    mbar_init(smem_addr(&full[0]), 1);
-    mbar_init(smem_addr(&full[1]), 1);
+    for (int b = 0; b < 2 * G::kWarps + 1; b++) mbar_init(smem_addr(&bars[b]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (tid <= G::kWarps) abort_flag[tid] = 0;
   __syncthreads();
   const uint64_t policy = l2_evict_first_policy();
-  const uint64_t grid = gridDim.x;
-  // Stage s holds the tiles of iterations i with i & 1 == s; the k-th of them completes phase k
-  // of its barrier. Thread 0 issues the first two tiles, then each tile two iterations ahead.
-  if (tid == 0)
+  const uint64_t n_warps = (uint64_t)gridDim.x * G::kWarps;
+  const uint64_t first = (uint64_t)blockIdx.x * G::kWarps + warp;
+  // Buffer s of a warp holds the tiles of its iterations i with i & 1 == s; the k-th of them
+  // completes phase k of the buffer's barrier. Lane 0 issues the first two tiles, then each tile
+  // two iterations ahead.
+  if (tid == 0 && G::kL1) {
+    mbar_arrive_expect_tx(smem_addr(&bars[2 * G::kWarps]), kFragL1Bytes);
+    bulk_load(smem_addr(fsm + G::kL1Off), p.tab.frag_l1, kFragL1Bytes, smem_addr(&bars[2 * G::kWarps]), policy);
+  }
+  if (lane == 0)
     for (int s = 0; s < 2; s++) {
-      const uint64_t t = blockIdx.x + s * grid;
-      if (t < p.n_tiles) frag_issue(p, t, smem_addr(fsm + s * kFragTileBytes), smem_addr(&full[s]), policy);
+      const uint64_t t = first + s * n_warps;
+      if (t < p.n_tiles) frag_issue<SIG>(p, t, smem_addr(mybuf + s * G::kTileBytes), bar0 + 8 * s, policy);
     }
+  bool ok = true;
+  if constexpr (G::kL1) ok = mbar_wait(smem_addr(&bars[2 * G::kWarps]), 0u, &abort_flag[G::kWarps], p.status);
+  bool aborted = !__syncthreads_and(ok);  // the only block-wide barrier: the filter is in place
   uint64_t i = 0;
-  bool aborted = false;
-  for (;; i++) {
-    const uint64_t tile = blockIdx.x + i * grid;
+  for (; !aborted; i++) {
+    const uint64_t tile = first + i * n_warps;
     if (tile >= p.n_tiles) break;
     const int s = (int)(i & 1);
-    uint8_t* buf = fsm + s * kFragTileBytes;
-    const bool ok = mbar_wait(smem_addr(&full[s]), (uint32_t)(i >> 1) & 1u, &abort_flag, p.status);
-    if (!__syncthreads_and(ok)) {
+    uint8_t* buf = mybuf + s * G::kTileBytes;
+    ok = mbar_wait(bar0 + 8 * s, (uint32_t)(i >> 1) & 1u, &abort_flag[warp], p.status);
+    if (!__all_sync(0xFFFFFFFFu, ok)) {
       aborted = true;
       break;
     }
-    if (tid == 0) frag_tail(p, tile, buf);
-    __syncthreads();
+    if ((tile + 1) * G::kTileStep + 64 > p.n_bytes) frag_tail<SIG>(p, tile, buf);  // warp-uniform
     const uint32_t* ws = reinterpret_cast<const uint32_t*>(buf);
-    const uint32_t w0 = (uint32_t)tid * kFragWPT;
-    const uint64_t cand = frag_candidates<SIG>(p, ws, w0, frag_valid(p, tile, w0));
-    const uint64_t n = frag_thread_count<SIG, LAYOUT>(p, ws, w0, cand);
-    uint64_t total;
-    block_exclusive_u64(n, warp_sums, &total);
-    if (tid == 0) p.tile_ntrip[p.tile_base + tile] = total;
-    __syncthreads();  // every thread is done with stage s (and with warp_sums)
-    const uint64_t next = tile + 2 * grid;
-    if (tid == 0 && next < p.n_tiles) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      frag_issue(p, next, smem_addr(buf), smem_addr(&full[s]), policy);
+    const uint32_t w0 = (uint32_t)lane * G::kWPT;
+    const uint64_t cand = frag_candidates<SIG>(p, ws, w0, frag_valid<SIG>(p, tile, w0), l1);
+    uint64_t n = frag_thread_count<SIG, LAYOUT>(p, ws, w0, cand);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) n += __shfl_xor_sync(0xFFFFFFFFu, n, d);
+    __syncwarp();  // every lane is done with the buffer
+    if (lane == 0) {
+      p.tile_ntrip[p.tile_base + tile] = n;
+      const uint64_t next = tile + 2 * n_warps;
+      if (next < p.n_tiles) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        frag_issue<SIG>(p, next, smem_addr(buf), bar0 + 8 * s, policy);
+      }
     }
+    __syncwarp();
   }
-  if (aborted && tid == 0) {
-    // Iterations i and i + 1 had their copies issued (when their tiles exist) and not waited
-    // for: let them land, each wait bounded, before the block's shared memory goes away.
+  if (aborted && lane == 0) {
+    // The filter (lane 0 of warp 0) and this warp's iterations i and i + 1 may have copies issued
+    // and not waited for: let them land, each wait bounded, before shared memory goes away.
     volatile uint32_t never = 0;
-    for (uint64_t j = i; j < i + 2 && blockIdx.x + j * grid < p.n_tiles; j++)
-      if (!mbar_wait(smem_addr(&full[j & 1]), (uint32_t)(j >> 1) & 1u, &never, p.status)) break;
+    if (G::kL1 && tid == 0) mbar_wait(smem_addr(&bars[2 * G::kWarps]), 0u, &never, p.status);
+    for (uint64_t j = i; j < i + 2 && first + j * n_warps < p.n_tiles; j++)
+      if (!mbar_wait(bar0 + 8 * (j & 1), (uint32_t)(j >> 1) & 1u, &never, p.status)) break;
   }
 }
 
@@ -304,44 +360,46 @@ __global__ void frag_hit_list_kernel(const uint64_t* tile_ntrip, uint64_t n_tile
 }
 
 template <int SIG, int LAYOUT>
-__global__ void __launch_bounds__(kFragThreads) frag_emit_kernel(const __grid_constant__ FragParams p) {
+__global__ void __launch_bounds__(FragGeom<SIG>::kThreads, 1) frag_emit_kernel(const __grid_constant__ FragParams p) {
+  using G = FragGeom<SIG>;
   extern __shared__ __align__(128) uint8_t fsm[];
-  __shared__ __align__(8) uint64_t full;
-  __shared__ uint32_t abort_flag;
-  __shared__ uint64_t warp_sums[kFragThreads / 32 + 1];
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    abort_flag = 0;
-    mbar_init(smem_addr(&full), 1);
+  __shared__ __align__(8) uint64_t bars[G::kWarps];
+  __shared__ uint32_t abort_flag[G::kWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint8_t* buf = fsm + warp * G::kTileBytes;
+  const uint32_t bar = smem_addr(&bars[warp]);
+  if (lane == 0) {
+    abort_flag[warp] = 0;
+    mbar_init(bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncthreads();
+  __syncwarp();
   const uint64_t policy = l2_evict_first_policy();
   const uint32_t n_list = *(volatile const uint32_t*)p.n_hit_tiles;
+  const uint32_t n_warps = gridDim.x * G::kWarps;
   uint32_t phase = 0;
-  for (uint32_t j = blockIdx.x; j < n_list; j += gridDim.x) {
+  for (uint32_t j = blockIdx.x * G::kWarps + warp; j < n_list; j += n_warps) {
     const uint64_t tile = p.hit_tiles[j];
-    if (tid == 0) {
+    if (lane == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      frag_issue(p, tile, smem_addr(fsm), smem_addr(&full), policy);
+      frag_issue<SIG>(p, tile, smem_addr(buf), bar, policy);
     }
-    const bool ok = mbar_wait(smem_addr(&full), phase & 1u, &abort_flag, p.status);
-    if (!__syncthreads_and(ok)) {
-      if (tid == 0) {  // the copy may still land: wait for it (bounded) before leaving
+    const bool ok = mbar_wait(bar, phase & 1u, &abort_flag[warp], p.status);
+    if (!__all_sync(0xFFFFFFFFu, ok)) {
+      if (lane == 0) {  // the copy may still land: wait for it (bounded) before leaving
         volatile uint32_t never = 0;
-        mbar_wait(smem_addr(&full), phase & 1u, &never, p.status);
+        mbar_wait(bar, phase & 1u, &never, p.status);
       }
       return;
     }
     phase++;
-    if (tid == 0) frag_tail(p, tile, fsm);
-    __syncthreads();
-    const uint32_t* ws = reinterpret_cast<const uint32_t*>(fsm);
-    const uint32_t w0 = (uint32_t)tid * kFragWPT;
-    const uint64_t cand = frag_candidates<SIG>(p, ws, w0, frag_valid(p, tile, w0));
+    if ((tile + 1) * G::kTileStep + 64 > p.n_bytes) frag_tail<SIG>(p, tile, buf);
+    const uint32_t* ws = reinterpret_cast<const uint32_t*>(buf);
+    const uint32_t w0 = (uint32_t)lane * G::kWPT;
+    const uint64_t cand = frag_candidates<SIG>(p, ws, w0, frag_valid<SIG>(p, tile, w0), nullptr);
     const uint64_t n = frag_thread_count<SIG, LAYOUT>(p, ws, w0, cand);
     uint64_t total;
-    uint64_t pos = p.tile_off[p.tile_base + tile] + block_exclusive_u64(n, warp_sums, &total);
+    uint64_t pos = p.tile_off[p.tile_base + tile] + warp_exclusive_u64(n, &total);
     uint64_t c = cand;
     while (c) {
       const int i = __ffsll((long long)c) - 1;
@@ -349,7 +407,7 @@ __global__ void __launch_bounds__(kFragThreads) frag_emit_kernel(const __grid_co
       const uint32_t w = w0 + (uint32_t)i;
       uint32_t off, cnt;
       if (!frag_resolve<SIG, LAYOUT>(p, ws, w, off, cnt)) continue;
-      const uint64_t k = tile * kFragTileWin + w;
+      const uint64_t k = tile * G::kTileWin + w;
       for (uint32_t q = 0; q < cnt; q++) {
         if (sig_is_weak(SIG) && !frag_equal(ws, w, p.tab.confirm + (uint64_t)(off + q) * 64)) continue;
         if (pos < p.out_cap) {
@@ -361,7 +419,7 @@ __global__ void __launch_bounds__(kFragThreads) frag_emit_kernel(const __grid_co
         pos++;
       }
     }
-    __syncthreads();  // the stage is free again
+    __syncwarp();  // the buffer is free again
   }
 }
 
@@ -398,13 +456,17 @@ __global__ void frag_digest_kernel(const uint8_t* arena, uint64_t n, uint4* dig,
   }
 }
 
-// One-word Bloom filter of a fragment table: every occupied slot sets 3 bits (from d2) of word
-// d3 & mask.
-__global__ void frag_bloom_kernel(const uint4* slots, uint32_t n_slots, uint32_t* words, uint32_t mask) {
+// The filters of a fragment table from its occupied slots: the one-word Bloom filter (3 bits
+// from d2 in word d3 & mask; none when words is null) and the 2^20-bit shared-memory filter
+// (bit: the top 20 bits of d1).
+__global__ void frag_bloom_kernel(const uint4* slots, uint32_t n_slots, uint32_t* words, uint32_t mask,
+                                  uint32_t* l1) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += gridDim.x * blockDim.x) {
     if (slots[2ull * i + 1].y == 0u) continue;
     const uint4 d = slots[2ull * i];
-    atomicOr(words + (d.w & mask), (1u << (d.z & 31)) | (1u << ((d.z >> 5) & 31)) | (1u << ((d.z >> 10) & 31)));
+    if (words) atomicOr(words + (d.w & mask), frag_bloom_bits(d.z));
+    const uint32_t b = d.y >> (32 - kFragL1Log2Bits);
+    atomicOr(l1 + (b >> 5), 1u << (b & 31));
   }
 }
 
@@ -413,25 +475,27 @@ namespace {
 
 using KernelFn = const void*;
 
-KernelFn count_fn(int sig, uint32_t layout) {
+struct Geom {
+  KernelFn count, emit;
+  int threads;
+  uint32_t tile_win, smem_count, smem_emit;
+};
+
+template <int SIG>
+Geom geom_t(uint32_t layout) {
+  using G = FragGeom<SIG>;
   const bool s = layout == kLayoutSorted;
-  switch (sig) {
-    case kSigMd5: return s ? (KernelFn)frag_count_kernel<kSigMd5, kLayoutSorted> : (KernelFn)frag_count_kernel<kSigMd5, kLayoutHash>;
-    case kSigMd5NoPad:
-      return s ? (KernelFn)frag_count_kernel<kSigMd5NoPad, kLayoutSorted> : (KernelFn)frag_count_kernel<kSigMd5NoPad, kLayoutHash>;
-    case kSigDjb2: return s ? (KernelFn)frag_count_kernel<kSigDjb2, kLayoutSorted> : (KernelFn)frag_count_kernel<kSigDjb2, kLayoutHash>;
-    default: return nullptr;
-  }
+  return Geom{s ? (KernelFn)frag_count_kernel<SIG, kLayoutSorted> : (KernelFn)frag_count_kernel<SIG, kLayoutHash>,
+              s ? (KernelFn)frag_emit_kernel<SIG, kLayoutSorted> : (KernelFn)frag_emit_kernel<SIG, kLayoutHash>,
+              G::kThreads, G::kTileWin, G::kSmemCount, G::kSmemEmit};
 }
 
-KernelFn emit_fn(int sig, uint32_t layout) {
-  const bool s = layout == kLayoutSorted;
+bool geom(int sig, uint32_t layout, Geom* g) {
   switch (sig) {
-    case kSigMd5: return s ? (KernelFn)frag_emit_kernel<kSigMd5, kLayoutSorted> : (KernelFn)frag_emit_kernel<kSigMd5, kLayoutHash>;
-    case kSigMd5NoPad:
-      return s ? (KernelFn)frag_emit_kernel<kSigMd5NoPad, kLayoutSorted> : (KernelFn)frag_emit_kernel<kSigMd5NoPad, kLayoutHash>;
-    case kSigDjb2: return s ? (KernelFn)frag_emit_kernel<kSigDjb2, kLayoutSorted> : (KernelFn)frag_emit_kernel<kSigDjb2, kLayoutHash>;
-    default: return nullptr;
+    case kSigMd5: *g = geom_t<kSigMd5>(layout); return true;
+    case kSigMd5NoPad: *g = geom_t<kSigMd5NoPad>(layout); return true;
+    case kSigDjb2: *g = geom_t<kSigDjb2>(layout); return true;
+    default: return false;
   }
 }
 
@@ -453,14 +517,16 @@ int frag_device(FragDev** out) {
   if (!d.ready) {
     for (int sig = 0; sig < 3; sig++)
       for (uint32_t l = 0; l < 2; l++) {
-        if ((e = cudaFuncSetAttribute(count_fn(sig, l), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kFragSmemCount)) != cudaSuccess)
+        Geom g;
+        geom(sig, l, &g);
+        if ((e = cudaFuncSetAttribute(g.count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem_count)) !=
+            cudaSuccess)
           return (int)e;
-        if ((e = cudaFuncSetAttribute(emit_fn(sig, l), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kFragSmemEmit)) != cudaSuccess)
+        if ((e = cudaFuncSetAttribute(g.emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem_emit)) !=
+            cudaSuccess)
           return (int)e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.count_blocks[sig][l], count_fn(sig, l), kFragThreads,
-                                                               kFragSmemCount)) != cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.count_blocks[sig][l], g.count, g.threads,
+                                                               g.smem_count)) != cudaSuccess)
           return (int)e;
         if (d.count_blocks[sig][l] < 1) return (int)cudaErrorInvalidConfiguration;
       }
@@ -478,7 +544,7 @@ FragParams make_params(const TableView& tab, const uint8_t* image, uint64_t n_by
   p.image = image;
   p.n_bytes = n_bytes;
   p.n_windows = frag_windows(n_bytes);
-  p.n_tiles = frag_tiles(n_bytes);
+  p.n_tiles = frag_tiles((int)tab.sig, n_bytes);
   p.tile_base = tile_base;
   p.status = status;
   p.one = 1u;
@@ -489,7 +555,11 @@ FragParams make_params(const TableView& tab, const uint8_t* image, uint64_t n_by
 
 uint64_t frag_windows(uint64_t n_bytes) { return n_bytes >= 64 ? (n_bytes - 64) / kFragStride + 1 : 0; }
 
-uint64_t frag_tiles(uint64_t n_bytes) { return (frag_windows(n_bytes) + kFragTileWin - 1) / kFragTileWin; }
+uint64_t frag_tiles(int sig, uint64_t n_bytes) {
+  Geom g;
+  if (!geom(sig, kLayoutHash, &g)) return 0;
+  return (frag_windows(n_bytes) + g.tile_win - 1) / g.tile_win;
+}
 
 bool frag_sig_supported(int sig) { return sig == kSigMd5 || sig == kSigMd5NoPad || sig == kSigDjb2; }
 
@@ -504,9 +574,10 @@ int frag_digests(int sig, const uint8_t* arena, uint64_t n, uint4* dig, uint8_t*
   return (int)cudaGetLastError();
 }
 
-int frag_bloom(const uint4* slots, uint32_t n_slots, uint32_t* words, uint32_t mask, int sms, void* stream) {
+int frag_bloom(const uint4* slots, uint32_t n_slots, uint32_t* words, uint32_t mask, uint32_t* l1, int sms,
+               void* stream) {
   const unsigned g = (unsigned)std::min<uint64_t>((n_slots + 255) / 256, (uint64_t)sms * 8);
-  frag_bloom_kernel<<<g, 256, 0, (cudaStream_t)stream>>>(slots, n_slots, words, mask);
+  frag_bloom_kernel<<<g, 256, 0, (cudaStream_t)stream>>>(slots, n_slots, words, mask, l1);
   return (int)cudaGetLastError();
 }
 
@@ -517,13 +588,14 @@ int frag_count(const TableView& tab, const uint8_t* image, uint64_t n_bytes, uin
   FragDev* d;
   int rc = frag_device(&d);
   if (rc) return rc;
-  KernelFn fn = count_fn((int)tab.sig, tab.layout);
-  if (!fn) return (int)cudaErrorInvalidValue;
+  Geom g;
+  if (!geom((int)tab.sig, tab.layout, &g)) return (int)cudaErrorInvalidValue;
   p.tile_ntrip = tile_ntrip;
   const uint64_t cap = (uint64_t)sms * (uint64_t)d->count_blocks[tab.sig][tab.layout];
-  const unsigned grid = (unsigned)std::min<uint64_t>(p.n_tiles, cap);
+  const uint64_t warps_per_block = (uint64_t)g.threads / 32;
+  const unsigned grid = (unsigned)std::min<uint64_t>((p.n_tiles + warps_per_block - 1) / warps_per_block, cap);
   void* args[] = {&p};
-  return (int)cudaLaunchKernel(fn, dim3(grid), dim3(kFragThreads), args, kFragSmemCount, (cudaStream_t)stream);
+  return (int)cudaLaunchKernel(g.count, dim3(grid), dim3(g.threads), args, g.smem_count, (cudaStream_t)stream);
 }
 
 int frag_emit(const TableView& tab, const uint8_t* image, uint64_t n_bytes, uint64_t tile_base,
@@ -534,23 +606,25 @@ int frag_emit(const TableView& tab, const uint8_t* image, uint64_t n_bytes, uint
   FragDev* d;
   int rc = frag_device(&d);
   if (rc) return rc;
-  KernelFn fn = emit_fn((int)tab.sig, tab.layout);
-  if (!fn) return (int)cudaErrorInvalidValue;
+  Geom g;
+  if (!geom((int)tab.sig, tab.layout, &g)) return (int)cudaErrorInvalidValue;
   cudaStream_t st = (cudaStream_t)stream;
   uint32_t* count = list + p.n_tiles;
   cudaError_t e = cudaMemsetAsync(count, 0, 4, st);
   if (e != cudaSuccess) return (int)e;
-  const unsigned g = (unsigned)std::min<uint64_t>((p.n_tiles + 255) / 256, (uint64_t)sms * 4);
-  frag_hit_list_kernel<<<g, 256, 0, st>>>(tile_ntrip + tile_base, p.n_tiles, list, count);
+  const unsigned gl = (unsigned)std::min<uint64_t>((p.n_tiles + 255) / 256, (uint64_t)sms * 4);
+  frag_hit_list_kernel<<<gl, 256, 0, st>>>(tile_ntrip + tile_base, p.n_tiles, list, count);
   if ((e = cudaGetLastError()) != cudaSuccess) return (int)e;
   p.tile_off = tile_off;
   p.hit_tiles = list;
   p.n_hit_tiles = count;
   p.out = out;
   p.out_cap = out_cap;
-  const unsigned grid = (unsigned)std::min<uint64_t>(p.n_tiles, (uint64_t)sms * 4);
+  const uint64_t warps_per_block = (uint64_t)g.threads / 32;
+  const unsigned grid = (unsigned)std::min<uint64_t>((p.n_tiles + warps_per_block - 1) / warps_per_block,
+                                                     (uint64_t)sms * 2);
   void* args[] = {&p};
-  e = cudaLaunchKernel(fn, dim3(grid), dim3(kFragThreads), args, kFragSmemEmit, st);
+  e = cudaLaunchKernel(g.emit, dim3(grid), dim3(g.threads), args, g.smem_emit, st);
   if (launches) *launches += 2;
   return (int)e;
 }
