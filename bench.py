@@ -114,15 +114,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
-def setup_workload(torch, cv, synth, name: str, seed_offset: int):
-    plan = synth.config_plan(name)
-    if seed_offset:
-        plan.image_seed += seed_offset
+def image_on_device(torch, synth, plan):
+    """The plan's image generated in device memory."""
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     keep = [dev(plan.plant_file.view(np.uint8)), dev(plan.plant_fcluster.view(np.uint8)), dev(plan.plant_over),
             dev(plan.file_nsect.view(np.uint8)), dev(synth.vocab(plan.image_seed))]
     image = torch.empty(plan.n_bytes, dtype=torch.uint8, device="cuda")
     plan.image_device(image.data_ptr(), dev_plan=tuple(k.data_ptr() for k in keep))
+    torch.cuda.synchronize()
+    return image
+
+
+def setup_workload(torch, cv, synth, name: str, seed_offset: int):
+    plan = synth.config_plan(name)
+    if seed_offset:
+        plan.image_seed += seed_offset
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    image = image_on_device(torch, synth, plan)
+    keep = []
     base = plan.file_base()
     base_d = dev(base.view(np.uint8))
     masters = torch.empty(plan.n_master_sectors * SECTOR, dtype=torch.uint8, device="cuda")
@@ -318,6 +327,54 @@ def run_tables(torch, cv, synth, plan, image, stream, steps):
 # DRAM bytes (read + write) per launch of the default scan kernel, from one ncu capture of the
 # current kernel: 4.436 GB on the 4 GiB mid workload (8,388,608 sectors), scaled by sectors.
 SCAN_TRAFFIC_BYTES = {"mid": 4.4360e9, "scale": 8 * 4.4360e9}
+def run_sweep(torch, cv, synth, stream, steps, sizes=(10**3, 10**5, 10**6, 10**7, 5 * 10**7),
+              densities=(1e-4, 1e-2, 1e-1)):
+    """Table-scaling sweep: an 8 GiB image (16,777,216 sectors, seed 3) against master sets of
+    10^3 .. 5x10^7 sectors, with clusters planted at 0.01%, 1% and 10% of the image sectors
+    (repeats allowed), scanned with and without the Bloom filter. Every result is checked
+    against the plant log in full."""
+    S = 16777216
+    out = {"workload": "sweep: 8 GiB image, seed 3; master sets of the scale workload's size mix"}
+    for M in sizes:
+        file_nsect, mseed = synth.sweep_master_set(M)
+        mplan = synth.Plan(0, mseed, 0, file_nsect, np.zeros(0, np.int32), np.zeros(0, np.uint32),
+                           np.zeros(0, np.uint8))
+        base = mplan.file_base()
+        base_d = torch.from_numpy(base.view(np.uint8).copy()).cuda()
+        masters = torch.empty(M * SECTOR, dtype=torch.uint8, device="cuda")
+        mplan.masters_device(masters.data_ptr(), base_d.data_ptr())
+        torch.cuda.synchronize()
+        files = [(masters.data_ptr() + int(base[f]) * SECTOR, int(file_nsect[f]) * SECTOR)
+                 for f in range(file_nsect.size)]
+        t0 = time.perf_counter()
+        tables = {"bloom": cv.master_build(files)}
+        build_s = time.perf_counter() - t0
+        tables["nobloom"] = cv.master_build(files, bloom_bits_per_key=0)
+        del masters, base_d
+        torch.cuda.synchronize()
+        info = tables["bloom"].info()
+        for dens in densities:
+            plan = synth.make_plan_density(3, S, file_nsect, dens, mseed)
+            image = image_on_device(torch, synth, plan)
+            exp = plan.expected_intact()
+            for name, m in tables.items():
+                wall, kms, matches = time_scans(torch, cv, m, image, stream, steps)
+                r = cv.scan(m, [image], stream=stream)
+                exact = bool(np.array_equal(r.matches(0), exp))
+                r.close()
+                out[f"M{M}_d{dens:g}_{name}"] = {
+                    "master_sectors": M, "files": int(file_nsect.size), "density": dens, "bloom": name == "bloom",
+                    "table_MB": info["n_slots"] * 32 / 1e6, "bloom_MB": info["bloom_bytes"] / 1e6 if name == "bloom" else 0,
+                    "max_probe": info["max_probe"], "build_s": build_s, "GBps": plan.n_bytes / wall / 1e9,
+                    "kernel_GBps": plan.n_bytes / (kms * 1e-3) / 1e9, "kernel_ns_per_sector": kms * 1e6 / S,
+                    "matches": matches, "exact_vs_plant_log": exact}
+            del image
+            torch.cuda.synchronize()
+        for m in tables.values():
+            m.close()
+    return out
+
+
 FRAG_OPS_PER_WINDOW_DJB2 = 31  # rolled djb2 step, key mix and one-word Bloom test (see DESIGN)
 
 
@@ -513,6 +570,9 @@ def main():
     ap.add_argument("--sig-steps", type=int, default=20)
     ap.add_argument("--no-tables", action="store_true")
     ap.add_argument("--no-frag", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-steps", type=int, default=5)
+    ap.add_argument("--sweep-only", action="store_true", help="run only the table-scaling sweep and print its JSON")
     ap.add_argument("--frag-steps", type=int, default=10)
     ap.add_argument("--frag-cpu-mib", type=int, default=256)
     ap.add_argument("--frag-only", action="store_true",
@@ -534,6 +594,16 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args)
+    if args.sweep_only:
+        import torch
+
+        import __graft_entry__
+
+        __graft_entry__.build()
+        from paper_0901_1307_gb300 import cv, synth
+
+        print(json.dumps(run_sweep(torch, cv, synth, torch.cuda.current_stream(), args.sweep_steps)))
+        return 0
     if args.frag_only:
         import torch
 
@@ -625,6 +695,10 @@ def main():
         e2e = {"value": world * nbytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
 
+    sweep = None
+    if not args.no_sweep and rank == 0:
+        sweep = run_sweep(torch, cv, synth, stream, args.sweep_steps)
+
     frags = None
     if not args.no_frag and rank == 0:
         frags = run_fragments(torch, cv, synth, stream, args.frag_steps, args.frag_cpu_mib << 20, args.frag_config,
@@ -671,6 +745,7 @@ def main():
         "signatures": sigs,
         "tables": tables,
         "fragments": frags,
+        "table_sweep": sweep,
         "gpu_launches": launches,
     }
     master.close()

@@ -299,6 +299,16 @@ def master_set(name: str):
     raise KeyError(name)
 
 
+def sweep_master_set(m_sectors: int):
+    """(file_nsect, master_seed) of the table-scaling sweep: the scale workload's file-size
+    distribution (log-uniform 8 KiB-1 MiB, about 210 sectors per file) scaled to m_sectors whole
+    sectors, seed 3."""
+    n_files = max(1, int(round(m_sectors / 210)))
+    rng = np.random.default_rng([3, m_sectors])
+    raw = log_uniform_sizes(rng, n_files, 8 << 10, 1 << 20) / SECTOR
+    return scale_to_total(raw, m_sectors, min(16, m_sectors // n_files)), 3 + 0x5EED + m_sectors
+
+
 def batch_sizes(seed: int, n: int, lo_bytes: int, hi_bytes: int, total_bytes: int) -> np.ndarray:
     """Image sizes in sectors: log-uniform lo..hi, scaled to total_bytes, each at least lo_bytes
     and a whole number of 4 KiB clusters."""
