@@ -73,8 +73,9 @@ def test_small_table_dense_repeats_against_oracle(cv):
     img = plan.image_host()
     files = plan.masters_host()
     want = oracle.match_hash(img, files)
-    assert want.size > 100_000
-    with cv.master_build(files) as m:
-        for bloom in (0, 1):
-            with cv.scan(m, [torch.from_numpy(img).cuda()]) as r:
-                assert np.array_equal(r.matches(0), want)
+    assert want.size > 10_000  # about 10% of the 131,072 sectors, less the overwrites
+    image = torch.from_numpy(img).cuda()
+    for bloom in (0, cv.CV_BLOOM_AUTO):
+        with cv.master_build(files, bloom_bits_per_key=bloom) as m:
+            with cv.scan(m, [image]) as r:
+                assert np.array_equal(r.matches(0), want), bloom
