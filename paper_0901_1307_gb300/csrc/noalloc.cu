@@ -115,8 +115,8 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   int mdev;
   if (master_view(m, &tab, &mdev) != CV_OK || tab.unit != kUnitSector) return CV_EINVAL;
   int dev;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
-    cudaGetLastError();
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev || cudaSetDevice(dev) != cudaSuccess) {
+    cudaGetLastError();  // cudaSetDevice binds the primary context for the driver-API calls below
     return CV_ENODEV;
   }
   if (dev != mdev) return CV_EINVAL;

@@ -43,6 +43,14 @@ int get_ctx(DevCtx** out) {
     return CV_ENODEV;
   }
   if (dev < 0 || dev >= kMaxDevices) return CV_ENODEV;
+  // Bind the device's primary context to the calling thread: the library also makes driver-API
+  // calls (address ranges, tensor maps), which need a current context and do not create one, and
+  // a thread that has made no runtime call yet has none.
+  if ((e = cudaSetDevice(dev)) != cudaSuccess) {
+    g_last_cuda = (int)e;
+    cudaGetLastError();
+    return CV_ENODEV;
+  }
   std::lock_guard<std::mutex> lk(g_ctx_mutex);
   DevCtx& c = g_ctx[dev];
   if (!c.ready) {

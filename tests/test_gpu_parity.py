@@ -352,3 +352,49 @@ def test_server_poll_nonblocking_and_unknown_ticket(cv):
                 break
         assert r is not None and r.count(0) == 64
         r.close()
+
+
+def test_concurrent_scans_on_separate_streams(cv):
+    """Separate scans may run at the same time from several host threads, each on its own
+    stream (the library's shared state is the device context and its memory pool)."""
+    import threading
+
+    plan = synth.config_plan("small:20000:30:77")
+    files = plan.masters_host()
+    img = plan.image_host()
+    want = oracle.match_hash(img, files)
+    with cv.master_build(files) as m:
+        dev = torch.from_numpy(img).cuda()
+        errors, results = [], {}
+
+        def worker(k):
+            try:
+                s = torch.cuda.Stream()
+                got = []
+                for rep in range(5):
+                    src = dev if (k + rep) % 2 == 0 else img  # device and host images alike
+                    with cv.scan(m, [src], stream=s.cuda_stream, chunk_bytes=(3 + k) * 4096) as r:
+                        got.append(r.matches(0))
+                results[k] = got
+            except Exception as e:  # reported below
+                errors.append(e)
+
+        def fresh_thread_noalloc():
+            try:
+                out = torch.empty(16 * (want.size + 8), dtype=torch.uint8, device="cuda")
+                rc, n = cv.scan_noalloc(m, dev, out, want.size + 8)
+                results["noalloc"] = np.frombuffer(out[: n * 16].cpu().numpy().tobytes(), cv.MATCH_DTYPE)
+            except Exception as e:
+                errors.append(e)
+
+        threads = [threading.Thread(target=worker, args=(k,)) for k in range(4)]
+        threads.append(threading.Thread(target=fresh_thread_noalloc))
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        assert not errors, errors
+        for k in range(4):
+            for got in results[k]:
+                assert np.array_equal(got, want)
+        assert np.array_equal(results["noalloc"], want)
