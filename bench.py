@@ -706,6 +706,18 @@ def main():
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
         e2e = {"value": world * nbytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
+        # the host link itself: one plain copy of 8 GiB of the pinned image to the device
+        probe = torch.empty(8 << 30, dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            probe.copy_(host[: 8 << 30], non_blocking=True)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        link = (8 << 30) / (ev0.elapsed_time(ev1) * 1e-3) / 1e9
+        del probe
+        e2e["h2d_link_GBps"] = link
+        e2e["frac_of_h2d_link"] = e2e["value"] / world / link
         if not args.no_streamed:
             # the streamed variant: 128 GiB of host-resident image in 1 GiB chunks, as four
             # 32 GiB images (views of the same pinned buffer) in one call
