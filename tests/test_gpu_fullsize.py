@@ -1,0 +1,62 @@
+"""The headline workload at full size, in the launch configuration the benchmark times: the
+32 GiB image (67,108,864 sectors) generated on the device and scanned against the 4,194,304-sector
+table. The whole result must equal the plan's plant log (master sectors are random, so the
+result is exactly the intact planted sectors), and sampled disk sectors, matching or not, are
+looked up one by one in the oracle's signature database."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0901_1307_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SECTOR = 512
+
+
+@pytest.fixture(scope="module")
+def cv(cuda_device):
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_0901_1307_gb300 import cv as cvmod
+
+    return cvmod
+
+
+def test_scale_workload_full_size(cv):
+    plan = synth.config_plan("scale")
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    keep = [dev(plan.plant_file.view(np.uint8)), dev(plan.plant_fcluster.view(np.uint8)), dev(plan.plant_over),
+            dev(plan.file_nsect.view(np.uint8)), dev(synth.vocab(plan.image_seed))]
+    image = torch.empty(plan.n_bytes, dtype=torch.uint8, device="cuda")
+    plan.image_device(image.data_ptr(), dev_plan=tuple(k.data_ptr() for k in keep))
+    base = plan.file_base()
+    base_d = dev(base.view(np.uint8))
+    masters = torch.empty(plan.n_master_sectors * SECTOR, dtype=torch.uint8, device="cuda")
+    plan.masters_device(masters.data_ptr(), base_d.data_ptr())
+    torch.cuda.synchronize()
+    files = [(masters.data_ptr() + int(base[f]) * SECTOR, int(plan.file_nsect[f]) * SECTOR) for f in range(plan.n_files)]
+    with cv.master_build(files) as m:
+        del masters
+        with cv.scan(m, [image]) as r:
+            got = r.matches(0)
+        exp = plan.expected_intact()
+        assert exp.size > 900_000
+        assert np.array_equal(got, exp)
+        # sampled sectors through the oracle, one by one: every fifth of them a planted one
+        rng = np.random.default_rng(99)
+        hit_rows = np.unique(got["disk_sector"])
+        rows = np.concatenate([rng.choice(hit_rows, 200, replace=False),
+                               rng.integers(0, plan.n_sectors, 800)]).astype(np.int64)
+        secs = image.view(-1, SECTOR)[torch.from_numpy(rows).cuda()].cpu().numpy()
+        db = oracle.OracleDB(plan.masters_host())
+        try:
+            for row, sec in zip(rows.tolist(), secs):
+                want = db.lookup(sec, row)
+                lo = np.searchsorted(got["disk_sector"], row, side="left")
+                hi = np.searchsorted(got["disk_sector"], row, side="right")
+                assert np.array_equal(got[lo:hi], want), row
+        finally:
+            db.close()
