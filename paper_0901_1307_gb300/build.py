@@ -34,7 +34,7 @@ def _sources():
 
 def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + [
-        os.path.join(INCLUDE, "cv.h"), __file__]
+        os.path.join(INCLUDE, "cv.h"), os.path.join(HERE, "cli", "cv_carve.c"), __file__]
 
 
 def stale() -> bool:
@@ -68,7 +68,24 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    build_cli()
     return LIB
+
+
+CLI_SRC = os.path.join(HERE, "cli", "cv_carve.c")
+CLI = os.path.join(HERE, "cv_carve")
+
+
+def build_cli() -> str:
+    """The cv_carve command-line tool (plain C against include/cv.h), linked to libcv.so."""
+    tmp = CLI + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-I" + INCLUDE, CLI_SRC, "-L" + HERE, "-lcv",
+           "-Wl,-rpath,$ORIGIN", "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"cv_carve failed to build:\n{r.stderr}")
+    os.replace(tmp, CLI)
+    return CLI
 
 
 if __name__ == "__main__":

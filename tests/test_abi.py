@@ -115,3 +115,22 @@ def test_master_options_checked_before_the_device(lib):
     assert build(20) == cv.CV_EINVAL
     assert build(full, position_mode=2) == cv.CV_EINVAL
     assert build(full, signature=4) == cv.CV_EINVAL
+
+
+def test_cli_builds_and_refuses_without_gpu(lib, tmp_path):
+    """cv_carve, the C command-line tool, links against libcv.so through include/cv.h alone;
+    without a GPU it reports the library's error (exit 2); a bad command line exits 1."""
+    torch = pytest.importorskip("torch")
+    import subprocess
+
+    from paper_0901_1307_gb300 import build
+
+    exe = build.build_cli()
+    img = tmp_path / "img"
+    img.write_bytes(bytes(4096))
+    r = subprocess.run([exe, str(img)], capture_output=True, text=True)
+    assert r.returncode == 1 and "usage" in r.stderr
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    r = subprocess.run([exe, str(img), "--", str(img)], capture_output=True, text=True)
+    assert r.returncode == 2 and "no usable CUDA device" in r.stderr
