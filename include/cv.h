@@ -51,6 +51,7 @@ extern "C" {
 #define CV_ENODEV -7     /* no usable CUDA device (the library has no CPU path) */
 #define CV_ERANGE -8     /* image_index out of range, or an output buffer too small */
 #define CV_EAGAIN -9     /* not ready yet (cv_poll) */
+#define CV_EIO -10       /* a file could not be opened, read or written */
 
 /* One match: disk sector i of image k equals sector file_sector of master file file_id. */
 typedef struct {
@@ -172,6 +173,18 @@ typedef struct {
 } cv_master_info;
 
 int cv_master_get_info(const cv_master* m, cv_master_info* info);
+
+/*
+ * Save a built table to a file and load it back, so that a master set is hashed once and
+ * reused across runs (the paper has no counterpart: it rebuilds its tables per run). The file
+ * holds the table's device arrays and parameters, little-endian, with a magic tag and a format
+ * version; it is valid on any GPU this library runs on. cv_master_load checks the sizes against
+ * the parameters and every slot's posting range on the device before accepting the table, so a
+ * damaged file yields CV_ECORRUPT rather than out-of-range reads. stream: cudaStream_t or NULL.
+ * Errors: CV_EINVAL, CV_EIO, CV_ENOMEM, CV_ECUDA, CV_ECORRUPT, CV_ENODEV.
+ */
+int cv_master_save(const cv_master* m, const char* path);
+int cv_master_load(const char* path, void* stream, cv_master** out);
 
 /*
  * Scan n_images disk images against the table (paper Section 3.1-3.2: every sector hashed,

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -78,6 +79,7 @@ const char* cv_strerror(int code) {
     case CV_ENODEV: return "no usable CUDA device";
     case CV_ERANGE: return "index or size out of range";
     case CV_EAGAIN: return "not ready yet";
+    case CV_EIO: return "file input/output failed";
     default: return "unknown error";
   }
 }
@@ -564,11 +566,188 @@ int frag_scan(DevCtx* ctx, const cv_master* m, const cv_buf* images, uint32_t n_
 
 }  // namespace
 
+namespace {
+
+// The table file: this header, then the arrays in header order (byte counts in the header).
+struct TableFileHeader {
+  char magic[8];              // "CVTABLE" + '\0'
+  uint32_t version;           // 1
+  uint32_t header_bytes;      // sizeof(TableFileHeader)
+  cv_master_info info;
+  uint32_t slot_mask, bloom_mask, max_probe, use_bloom, sig, tau_mask, layout, n_keys, unit, reserved;
+  uint64_t bytes_slots, bytes_postings, bytes_bloom, bytes_confirm, bytes_keys0, bytes_l1;
+};
+constexpr char kTableMagic[8] = {'C', 'V', 'T', 'A', 'B', 'L', 'E', 0};
+constexpr uint32_t kTableVersion = 1;
+
+uint64_t table_unit_bytes(uint32_t unit) { return unit == kUnitFragment ? kFrag : kSector; }
+
+// Device <-> file in bounded pieces through one host buffer.
+int copy_to_file(FILE* f, const void* dev, uint64_t n) {
+  std::vector<uint8_t> buf(std::min<uint64_t>(n, 64ull << 20));
+  for (uint64_t off = 0; off < n; off += buf.size()) {
+    const uint64_t k = std::min<uint64_t>(buf.size(), n - off);
+    CV_CUDA(cudaMemcpy(buf.data(), (const uint8_t*)dev + off, k, cudaMemcpyDeviceToHost));
+    if (fwrite(buf.data(), 1, k, f) != k) return CV_EIO;
+  }
+  return CV_OK;
+}
+
+int copy_from_file(FILE* f, void* dev, uint64_t n) {
+  std::vector<uint8_t> buf(std::min<uint64_t>(n, 64ull << 20));
+  for (uint64_t off = 0; off < n; off += buf.size()) {
+    const uint64_t k = std::min<uint64_t>(buf.size(), n - off);
+    if (fread(buf.data(), 1, k, f) != k) return CV_EIO;
+    CV_CUDA(cudaMemcpy((uint8_t*)dev + off, buf.data(), k, cudaMemcpyHostToDevice));
+  }
+  return CV_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int cv_master_get_info(const cv_master* m, cv_master_info* info) {
   if (!m || !info || m->magic != kMagicMaster) return CV_EINVAL;
   *info = m->info;
+  return CV_OK;
+}
+
+int cv_master_save(const cv_master* m, const char* path) {
+  if (!m || m->magic != kMagicMaster || !path) return CV_EINVAL;
+  DevCtx* ctx;
+  CV_TRY(get_ctx(&ctx));
+  if (ctx->dev != m->dev) return CV_EINVAL;
+  const cv_master_info& in = m->info;
+  const uint64_t unit = table_unit_bytes(in.unit);
+  TableFileHeader h;
+  memset(&h, 0, sizeof h);
+  memcpy(h.magic, kTableMagic, 8);
+  h.version = kTableVersion;
+  h.header_bytes = sizeof h;
+  h.info = in;
+  h.slot_mask = m->tab.slot_mask;
+  h.bloom_mask = m->tab.bloom_mask;
+  h.max_probe = m->tab.max_probe;
+  h.use_bloom = m->tab.use_bloom;
+  h.sig = m->tab.sig;
+  h.tau_mask = m->tab.tau_mask;
+  h.layout = m->tab.layout;
+  h.n_keys = m->tab.n_keys;
+  h.unit = m->tab.unit;
+  h.bytes_slots = (m->tab.layout == kLayoutSorted ? (uint64_t)m->tab.n_keys : in.n_slots) * 32;
+  h.bytes_postings = in.n_kept * 8;
+  h.bytes_bloom = m->bloom ? in.bloom_bytes : 0;
+  h.bytes_confirm = m->confirm ? in.n_kept * unit : 0;
+  h.bytes_keys0 = m->keys0 ? (uint64_t)m->tab.n_keys * 4 : 0;
+  h.bytes_l1 = m->frag_l1 ? kFragL1Bytes : 0;
+  CV_CUDA(cudaDeviceSynchronize());
+  FILE* f = fopen(path, "wb");
+  if (!f) return CV_EIO;
+  int rc = fwrite(&h, sizeof h, 1, f) == 1 ? CV_OK : CV_EIO;
+  const void* arrays[6] = {m->slots, m->postings, m->bloom, m->confirm, m->keys0, m->frag_l1};
+  const uint64_t sizes[6] = {h.bytes_slots, h.bytes_postings, h.bytes_bloom, h.bytes_confirm, h.bytes_keys0,
+                             h.bytes_l1};
+  for (int k = 0; k < 6 && rc == CV_OK; k++)
+    if (sizes[k]) rc = copy_to_file(f, arrays[k], sizes[k]);
+  if (fclose(f) != 0 && rc == CV_OK) rc = CV_EIO;
+  return rc;
+}
+
+int cv_master_load(const char* path, void* stream_, cv_master** out) {
+  if (!path || !out) return CV_EINVAL;
+  *out = nullptr;
+  DevCtx* ctx;
+  CV_TRY(get_ctx(&ctx));
+  cudaStream_t stream = (cudaStream_t)stream_;
+  FILE* f = fopen(path, "rb");
+  if (!f) return CV_EIO;
+  TableFileHeader h;
+  if (fread(&h, sizeof h, 1, f) != 1) {
+    fclose(f);
+    return CV_EIO;
+  }
+  // the parameters must describe a table this library could have built
+  const cv_master_info& in = h.info;
+  const uint64_t unit = table_unit_bytes(h.unit);
+  const uint64_t n_records = h.layout == kLayoutSorted ? (uint64_t)h.n_keys : in.n_slots;
+  const uint64_t bloom_block = h.unit == kUnitFragment ? 4 : 32;
+  const bool ok = memcmp(h.magic, kTableMagic, 8) == 0 && h.version == kTableVersion &&
+                  h.header_bytes == sizeof h && h.unit <= kUnitFragment && h.layout <= kLayoutSorted &&
+                  h.sig <= (uint32_t)kSigCrc64 && in.unit == h.unit && in.layout == h.layout &&
+                  in.signature == h.sig && (h.tau_mask == 0u || h.tau_mask == 7u) && in.n_kept <= in.n_sectors &&
+                  in.n_sectors < (1ull << 27) && in.n_unique <= in.n_kept && in.n_slots >= 1 &&
+                  in.n_slots <= (1ull << 31) &&
+                  (h.layout == kLayoutSorted ? h.n_keys == in.n_unique && in.n_slots == in.n_unique
+                                             : ((uint64_t)h.slot_mask + 1 == in.n_slots &&
+                                                (in.n_slots & (in.n_slots - 1)) == 0 && h.max_probe <= in.n_slots)) &&
+                  h.bytes_slots == n_records * 32 && h.bytes_postings == in.n_kept * 8 &&
+                  h.bytes_confirm == (sig_is_weak((int)h.sig) ? in.n_kept * unit : 0) &&
+                  h.bytes_keys0 == (h.layout == kLayoutSorted ? (uint64_t)h.n_keys * 4 : 0) &&
+                  h.bytes_l1 == (h.unit == kUnitFragment ? kFragL1Bytes : 0) &&
+                  h.use_bloom == (h.bytes_bloom ? 1u : 0u) && h.bytes_bloom == in.bloom_bytes &&
+                  (!h.use_bloom || ((uint64_t)h.bloom_mask + 1) * bloom_block == h.bytes_bloom) &&
+                  (h.bloom_mask & ((uint64_t)h.bloom_mask + 1)) == 0;
+  if (!ok) {
+    fclose(f);
+    return CV_ECORRUPT;
+  }
+  cv_master* m = (cv_master*)calloc(1, sizeof(cv_master));
+  if (!m) {
+    fclose(f);
+    return CV_ENOMEM;
+  }
+  m->magic = kMagicMaster;
+  m->dev = ctx->dev;
+  auto body = [&]() -> int {
+    void** arrays[6] = {&m->slots, &m->postings, &m->bloom, &m->confirm, &m->keys0, &m->frag_l1};
+    const uint64_t sizes[6] = {h.bytes_slots, h.bytes_postings, h.bytes_bloom, h.bytes_confirm, h.bytes_keys0,
+                               h.bytes_l1};
+    const bool always[6] = {true, true, false, false, false, false};  // the build allocates these even when empty
+    for (int k = 0; k < 6; k++) {
+      if (!sizes[k] && !always[k]) continue;
+      CV_CUDA(cudaMalloc(arrays[k], std::max<uint64_t>(sizes[k], 32)));
+      if (sizes[k]) CV_TRY(copy_from_file(f, *arrays[k], sizes[k]));
+    }
+    uint8_t extra;
+    if (fread(&extra, 1, 1, f) != 0) return CV_ECORRUPT;  // trailing bytes: not this table's file
+    uint32_t* status;
+    CV_CUDA(cudaMallocAsync((void**)&status, 4, stream));
+    CV_CUDA(cudaMemsetAsync(status, 0, 4, stream));
+    validate_slots_kernel<<<grid_for(std::max<uint64_t>(n_records, 1), 256, ctx->sms), 256, 0, stream>>>(
+        (const uint4*)m->slots, n_records, in.n_kept, status);
+    CV_CUDA(cudaGetLastError());
+    uint32_t st = 0;
+    CV_CUDA(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, stream));
+    CV_CUDA(cudaFreeAsync(status, stream));
+    CV_CUDA(cudaStreamSynchronize(stream));
+    if (st) return CV_ECORRUPT;
+    m->tab.slots = (const uint4*)m->slots;
+    m->tab.postings = (const uint2*)m->postings;
+    m->tab.bloom = (const uint4*)m->bloom;
+    m->tab.confirm = (const uint8_t*)m->confirm;
+    m->tab.keys0 = (const uint32_t*)m->keys0;
+    m->tab.frag_l1 = (const uint32_t*)m->frag_l1;
+    m->tab.slot_mask = h.slot_mask;
+    m->tab.bloom_mask = h.bloom_mask;
+    m->tab.max_probe = h.max_probe;
+    m->tab.use_bloom = h.use_bloom;
+    m->tab.sig = h.sig;
+    m->tab.tau_mask = h.tau_mask;
+    m->tab.tau_add = 0;
+    m->tab.layout = h.layout;
+    m->tab.n_keys = h.n_keys;
+    m->tab.unit = h.unit;
+    m->info = in;
+    return CV_OK;
+  };
+  const int rc = body();
+  fclose(f);
+  if (rc != CV_OK) {
+    cv_free(m);
+    return rc;
+  }
+  *out = m;
   return CV_OK;
 }
 

@@ -13,6 +13,7 @@ constexpr uint32_t kStTimeout = 1u;     // an mbarrier wait ran out of time
 constexpr uint32_t kStProbeBound = 2u;  // a lookup ran past the table's recorded probe bound
 constexpr uint32_t kStTableFull = 4u;   // an insert found no free slot
 constexpr uint32_t kStOverflow = 8u;    // an output buffer was too small
+constexpr uint32_t kStBadTable = 16u;   // a loaded table's slot points outside its postings
 
 // A contiguous run of whole sectors in device memory, scanned as one tensor map. An image
 // larger than kMaxSegmentSectors is split into several segments.

@@ -244,6 +244,15 @@ __global__ void gather_slots_kernel(const uint4* slots, const uint32_t* vals, ui
   }
 }
 
+// ------------------------------------------------------------------- loaded tables
+// Every occupied record of a loaded table must name postings inside [0, n_postings).
+__global__ void validate_slots_kernel(const uint4* slots, uint64_t n, uint64_t n_postings, uint32_t* status) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint4 val = slots[2 * i + 1];
+    if (val.y != 0u && (uint64_t)val.x + val.y > n_postings) atomicOr(status, kStBadTable);
+  }
+}
+
 // ----------------------------------------------------------------------------- Bloom
 __global__ void bloom_kernel(const uint4* slots, uint32_t n_slots, uint32_t* bloom, uint32_t bloom_mask) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += gridDim.x * blockDim.x) {

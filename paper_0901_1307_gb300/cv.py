@@ -40,8 +40,9 @@ EXPORTS = ("cv_master_build", "cv_master_get_info", "cv_scan", "cv_matches", "cv
            "cv_strerror", "cv_last_cuda_error", "cv_sector_digests", "cv_kernel_config_count",
            "cv_kernel_config_name", "cv_scan_noalloc", "cv_batch_create", "cv_batch_run", "cv_batch_wait",
            "cv_batch_matches", "cv_batch_get_info", "cv_server_create", "cv_submit", "cv_poll",
-           "cv_server_get_stats", "cv_int_peak", "cv_selftest_wait_timeout")
+           "cv_server_get_stats", "cv_int_peak", "cv_selftest_wait_timeout", "cv_master_save", "cv_master_load")
 CV_EAGAIN = -9
+CV_EIO = -10
 CV_BATCH_BLOOM_AUTO = 0
 CV_BATCH_BLOOM_OFF = 1
 CV_NOALLOC_MAX_SECTORS = 1 << 19
@@ -134,6 +135,10 @@ def load(path: str = LIB_PATH):
         lib.cv_master_build.restype = i32
         lib.cv_master_get_info.argtypes = [vp, ctypes.POINTER(cv_master_info)]
         lib.cv_master_get_info.restype = i32
+        lib.cv_master_save.argtypes = [vp, ctypes.c_char_p]
+        lib.cv_master_save.restype = i32
+        lib.cv_master_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
+        lib.cv_master_load.restype = i32
         lib.cv_scan.argtypes = [vp, ctypes.POINTER(cv_buf), u32, ctypes.POINTER(cv_scan_opts), ctypes.POINTER(vp)]
         lib.cv_scan.restype = i32
         lib.cv_matches.argtypes = [vp, u32, ctypes.POINTER(vp), ctypes.POINTER(u64)]
@@ -337,6 +342,18 @@ def master_build(files, max_load: float = 0.0, bloom_bits_per_key: int = CV_BLOO
     h = ctypes.c_void_p()
     _check(load().cv_master_build(arr, len(files), ctypes.byref(o), ctypes.byref(h)), "cv_master_build")
     del keep
+    return Master(h.value)
+
+
+def master_save(master: Master, path) -> None:
+    """cv_master_save: write the built table to a file."""
+    _check(load().cv_master_save(master.handle, os.fsencode(path)), "cv_master_save")
+
+
+def master_load(path, stream=None) -> Master:
+    """cv_master_load: a table saved by master_save, checked and placed on the current device."""
+    h = ctypes.c_void_p()
+    _check(load().cv_master_load(os.fsencode(path), _stream(stream), ctypes.byref(h)), "cv_master_load")
     return Master(h.value)
 
 
