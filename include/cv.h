@@ -209,7 +209,7 @@ int cv_matches(const cv_result* r, uint32_t image_index, const cv_match** out, u
 typedef struct {
   uint64_t sectors;        /* whole sectors scanned (fragment tables: windows scanned) */
   uint64_t matches;        /* triples over all images */
-  uint64_t hit_sectors;    /* reserved (0) */
+  uint64_t hit_sectors;    /* disk sectors with at least one match (0 for fragment tables) */
   float kernel_ms;         /* device time of the hashing/probe launches */
   float total_ms;          /* device time from the first copy to the last result copy */
   uint32_t kernel_launches; /* kernels the call launched (scan, offsets, expand) */

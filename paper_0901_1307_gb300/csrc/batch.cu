@@ -356,6 +356,7 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
 }
 
 int cv_batch_run(cv_batch* b, void* stream) {
+  NvtxRange nvtx_range("cv.batch_run");
   if (!b || b->magic != kMagicBatch) return CV_EINVAL;
   if (!b->exec) {
     b->ran = true;

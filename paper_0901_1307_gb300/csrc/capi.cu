@@ -170,6 +170,7 @@ static int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* 
 }
 
 int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts* opts, cv_master** out) {
+  NvtxRange nvtx_range("cv.master_build");
   if (!out || (n_files && !files)) return CV_EINVAL;
   *out = nullptr;
   if (opts && opts->struct_size < offsetof(cv_master_opts, position_mode)) return CV_EINVAL;
@@ -434,6 +435,7 @@ namespace {
 // tiles, emit kernel per image over its tiles with triples. Host images are copied whole.
 int frag_scan(DevCtx* ctx, const cv_master* m, const cv_buf* images, uint32_t n_images, uint32_t flags,
               cudaStream_t stream, cv_result** out) {
+  NvtxRange nvtx_range("cv.scan.fragments");
   Temps staging(ctx, stream);
   std::vector<const uint8_t*> dptr(n_images, nullptr);
   std::vector<uint64_t> nbytes(n_images, 0), tile_base(n_images + 1, 0);
@@ -614,6 +616,7 @@ int cv_master_get_info(const cv_master* m, cv_master_info* info) {
 }
 
 int cv_master_save(const cv_master* m, const char* path) {
+  NvtxRange nvtx_range("cv.master_save");
   if (!m || m->magic != kMagicMaster || !path) return CV_EINVAL;
   DevCtx* ctx;
   CV_TRY(get_ctx(&ctx));
@@ -655,6 +658,7 @@ int cv_master_save(const cv_master* m, const char* path) {
 }
 
 int cv_master_load(const char* path, void* stream_, cv_master** out) {
+  NvtxRange nvtx_range("cv.master_load");
   if (!path || !out) return CV_EINVAL;
   *out = nullptr;
   DevCtx* ctx;
@@ -752,6 +756,7 @@ int cv_master_load(const char* path, void* stream_, cv_master** out) {
 }
 
 int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const cv_scan_opts* opts, cv_result** out) {
+  NvtxRange nvtx_range("cv.scan");
   if (!m || m->magic != kMagicMaster || !out || (n_images && !images)) return CV_EINVAL;
   *out = nullptr;
   if (opts && opts->struct_size < offsetof(cv_scan_opts, base_offset)) return CV_EINVAL;
@@ -840,7 +845,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
       const size_t nseg = job.segs.size();
       const uint64_t nt = job.n_tiles;
       uint64_t total = 0;
-      std::vector<uint64_t> seg_off(nseg + 2, 0);
+      std::vector<uint64_t> seg_off(nseg + 3, 0);
       uint32_t* status_keep = nullptr;
       if (nseg) {
         void* ring[2] = {nullptr, nullptr};
@@ -871,10 +876,10 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         CV_TRY(tmp.alloc(&tile_nhit, n_out * 4));
         CV_TRY(tmp.alloc(&tile_ntrip, n_out * 8));
         CV_TRY(tmp.alloc(&tile_off, n_out * 8));
-        CV_TRY(tmp.alloc(&seg_off_d, (nseg + 2) * 8));  // seg_off[nseg], total, status
+        CV_TRY(tmp.alloc(&seg_off_d, (nseg + 3) * 8));  // seg_off[nseg], total, status, hit sectors
         status = (uint32_t*)(seg_off_d + nseg + 1);
         status_keep = status;
-        CV_CUDA(cudaMemsetAsync(status, 0, 8, stream));
+        CV_CUDA(cudaMemsetAsync(status, 0, 16, stream));
         CV_CUDA(cudaMemcpyAsync(segs_d, job.segs.data(), nseg * sizeof(Segment), cudaMemcpyHostToDevice, stream));
         ScanParams p;
         memset(&p, 0, sizeof p);
@@ -884,6 +889,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         p.tile_ntrip = tile_ntrip;
         p.status = status;
         CV_CUDA(cudaEventRecord(ev[1], stream));
+        NvtxRange launches_range("cv.scan.launches");
         // device segments: one launch per run of consecutive device segments
         size_t hk = 0;
         size_t s = 0;
@@ -908,6 +914,8 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
           }
         }
         CV_CUDA(cudaEventRecord(ev[2], stream));
+        launches_range.end();
+        NvtxRange offsets_range("cv.scan.offsets_expand");
         uint64_t* total_d = seg_off_d + nseg;
         uint32_t nseg32 = (uint32_t)nseg;
         uint64_t nt_arg = n_out;
@@ -915,12 +923,15 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         CV_TRY(tmp.alloc(&off_scratch, tile_offsets_scratch_words(n_out) * 8));
         CV_CUDA((cudaError_t)launch_tile_offsets(tile_ntrip, n_out, tile_off, segs_d, nseg32, (uint32_t)(cfg.T / 32),
                                                  seg_off_d, total_d, off_scratch, stream));
-        CV_CUDA(cudaMemcpyAsync(seg_off.data(), seg_off_d, (nseg + 2) * 8, cudaMemcpyDeviceToHost, stream));
+        CV_CUDA((cudaError_t)launch_sum_u32(tile_nhit, n_out, seg_off_d + nseg + 2, ctx->sms, stream));
+        r->launches += 1;
+        CV_CUDA(cudaMemcpyAsync(seg_off.data(), seg_off_d, (nseg + 3) * 8, cudaMemcpyDeviceToHost, stream));
         CV_CUDA(cudaStreamSynchronize(stream));
         const uint32_t st = (uint32_t)seg_off[nseg + 1];
         if (st & kStTimeout) return CV_ETIMEOUT;
         if (st) return CV_ECORRUPT;
         total = seg_off[nseg];
+        r->st.hit_sectors = seg_off[nseg + 2];
         if (total) {
           CV_CUDA(cudaMallocFromPoolAsync((void**)&r->dev_out, total * sizeof(MatchOut), ctx->pool, stream));
           CV_CUDA((cudaError_t)launch_expand(cfg, hit_rec, tile_nhit, tile_off, n_out, segs_d, nseg32, tab,

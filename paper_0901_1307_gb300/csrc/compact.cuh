@@ -102,6 +102,17 @@ __global__ void segment_offsets_kernel(const uint64_t* tile_off, uint64_t n, con
   }
 }
 
+// The sum of n u32 values added to *out: the disk sectors with at least one match, from the
+// per-tile hit counts.
+__global__ void sum_u32_kernel(const uint32_t* v, uint64_t n, unsigned long long* out) {
+  unsigned long long s = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    s += v[i];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, d);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
 // One warp per output tile (32 consecutive sectors) with hits. A hit record is {lane, post_off,
 // post_cnt, n_emit}: the sector emits n_emit triples, all of its postings, or with a 64-bit
 // signature (confirm != null) those whose master sector equals the disk sector byte for byte.

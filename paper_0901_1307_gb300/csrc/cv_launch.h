@@ -36,6 +36,9 @@ int launch_expand(const ScanCfg& cfg, const uint4* hit_rec, const uint32_t* tile
                   uint64_t out_cap, uint32_t* status, int sms, void* stream);
 
 
+// *out += the sum of the n u32 values v (device); *out is device memory. CUDA error code.
+int launch_sum_u32(const uint32_t* v, uint64_t n, uint64_t* out, int sms, void* stream);
+
 // Scratch (u64 words) the offset pass needs for n tiles.
 uint64_t tile_offsets_scratch_words(uint64_t n_tiles);
 

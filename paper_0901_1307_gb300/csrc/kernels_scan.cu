@@ -97,6 +97,13 @@ int launch_wait_selftest(uint32_t* status, uint64_t timeout_ns, void* stream) {
 
 uint64_t tile_offsets_scratch_words(uint64_t n_tiles) { return (n_tiles + kOffChunk - 1) / kOffChunk + 1; }
 
+int launch_sum_u32(const uint32_t* v, uint64_t n, uint64_t* out, int sms, void* stream) {
+  if (!n) return 0;
+  const unsigned g = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 4);
+  sum_u32_kernel<<<g, 256, 0, (cudaStream_t)stream>>>(v, n, reinterpret_cast<unsigned long long*>(out));
+  return (int)cudaGetLastError();
+}
+
 int launch_tile_offsets(const uint64_t* tile_ntrip, uint64_t n_tiles, uint64_t* tile_off, const Segment* segs,
                         uint32_t n_segs, uint32_t scale, uint64_t* seg_off, uint64_t* total, uint64_t* scratch,
                         void* stream_) {

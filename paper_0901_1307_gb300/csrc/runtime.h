@@ -9,11 +9,29 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cv.h"
 #include "cv_internal.h"
 #include "cv_launch.h"
 
 namespace cvk {
+
+// A named range on the host timeline for tools that record NVTX (build, scan phases, engine
+// iterations); without such a tool attached each push and pop is a no-op call.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { end(); }
+  void end() {  // close the range early (once)
+    if (open_) nvtxRangePop();
+    open_ = false;
+  }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+
+ private:
+  bool open_ = true;
+};
 
 // Records the failing CUDA code for cv_last_cuda_error and maps it to a CV_E* code.
 int cuda_fail(cudaError_t e);

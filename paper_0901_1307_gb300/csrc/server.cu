@@ -171,6 +171,7 @@ void cv_server::finish(Request* r) {
 
 // One engine iteration: admit, issue copies, scan every unit that has landed.
 int cv_server::iterate(bool* did_work) {
+  NvtxRange nvtx_range("cv.server.iteration");
   *did_work = false;
   std::vector<Request*> work;
   {

@@ -398,3 +398,23 @@ def test_concurrent_scans_on_separate_streams(cv):
             for got in results[k]:
                 assert np.array_equal(got, want)
         assert np.array_equal(results["noalloc"], want)
+
+
+def test_permuted_master_order_only_relabels(cv):
+    """Metamorphic: permuting the master files permutes file_ids and nothing else; the scan also
+    reports how many disk sectors matched (host and device images alike)."""
+    plan = synth.config_plan("small:30000:40:91")
+    img = plan.image_host()
+    files = plan.masters_host()
+    perm = np.random.default_rng(5).permutation(len(files))
+    dev = torch.from_numpy(img).cuda()
+    with cv.master_build(files) as m, cv.scan(m, [dev, img], chunk_bytes=777 * 512) as r:
+        base = r.matches(0)
+        assert np.array_equal(r.matches(1), base)
+        assert r.stats()["hit_sectors"] == 2 * np.unique(base["disk_sector"]).size
+    with cv.master_build([files[k] for k in perm]) as m, cv.scan(m, [dev]) as r:
+        got = r.matches(0)
+    relabelled = got.copy()
+    relabelled["file_id"] = perm[got["file_id"]]
+    relabelled.sort(order=["disk_sector", "file_id", "file_sector"])
+    assert np.array_equal(relabelled, base)
