@@ -97,6 +97,10 @@ typedef struct cv_result cv_result; /* the results of one scan */
  *   used, and a lookup costs ceil(log2 n_unique) dependent reads whatever the occupancy. */
 #define CV_LAYOUT_HASH 0u
 #define CV_LAYOUT_SORTED 1u
+/* CV_LAYOUT_AUTO: the hash layout, turned into the sorted one when the built table's occupancy
+ * (distinct keys / slots) exceeds 0.8 with a Bloom filter or 0.5 without one, where linear
+ * probing measured slower than bisection on GB300. cv_master_info.layout reports the choice. */
+#define CV_LAYOUT_AUTO 2u
 
 /* What the master files are cut into (cv_master_opts.unit).
  * CV_UNIT_SECTOR: whole 512-byte sectors; disk images are scanned sector by sector.

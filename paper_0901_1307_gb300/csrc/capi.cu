@@ -178,8 +178,8 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
   const uint32_t position_mode = has_v2 ? opts->position_mode : CV_POSITION_ANY;
   if (position_mode > CV_POSITION_CLUSTER) return CV_EINVAL;
   const bool by_tau = position_mode == CV_POSITION_CLUSTER;
-  const uint32_t layout = has_v2 ? opts->layout : CV_LAYOUT_HASH;
-  if (layout > CV_LAYOUT_SORTED) return CV_EINVAL;
+  uint32_t layout = has_v2 ? opts->layout : CV_LAYOUT_HASH;
+  if (layout > CV_LAYOUT_AUTO) return CV_EINVAL;
   const uint32_t unit = (opts && opts->struct_size >= sizeof(cv_master_opts)) ? opts->unit : CV_UNIT_SECTOR;
   if (unit > CV_UNIT_FRAGMENT) return CV_EINVAL;
   const bool frag = unit == CV_UNIT_FRAGMENT;
@@ -309,6 +309,8 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       if (hc[3] & kStTableFull) return CV_ETABLEFULL;
       if (hc[3] & kStTimeout) return CV_ETIMEOUT;
       if (hc[3]) return CV_ECORRUPT;
+      if (layout == CV_LAYOUT_AUTO)  // thresholds from the occupancy sweep (Bloom on / off)
+        layout = (double)hc[2] > (bpk ? 0.8 : 0.5) * (double)n_slots ? CV_LAYOUT_SORTED : CV_LAYOUT_HASH;
       uint32_t steps = 0;  // binary-search steps of the sorted layout
       if (layout == CV_LAYOUT_SORTED) {
         // the occupied slots, compacted in slot order, sorted by h0 (stable: deterministic)

@@ -30,7 +30,7 @@ CV_BLOOM_AUTO = 0xFFFFFFFF
 CV_SIG_MD5, CV_SIG_MD5_NOPAD, CV_SIG_DJB2_64, CV_SIG_CRC64 = 0, 1, 2, 3
 CV_KEEP_ON_DEVICE = 1
 CV_POSITION_ANY, CV_POSITION_CLUSTER = 0, 1
-CV_LAYOUT_HASH, CV_LAYOUT_SORTED = 0, 1
+CV_LAYOUT_HASH, CV_LAYOUT_SORTED, CV_LAYOUT_AUTO = 0, 1, 2
 CV_UNIT_SECTOR, CV_UNIT_FRAGMENT = 0, 1
 SECTOR = 512
 

@@ -115,3 +115,16 @@ def test_sorted_batch_server_noalloc(cv):
         rc, n = cv.scan_noalloc(m, (dev.data_ptr() + a * SECTOR, (bnd - a) * SECTOR), out, wants[1].size + 8)
         assert rc == cv.CV_OK and n == wants[1].size
         assert np.array_equal(np.frombuffer(out[: n * 16].cpu().numpy().tobytes(), cv.MATCH_DTYPE), wants[1])
+
+
+@pytest.mark.parametrize("max_load,bloom", [(0.9, 0), (0.9, 16), (0.5, 0), (0.25, 16)])
+def test_auto_layout_follows_occupancy(cv, max_load, bloom):
+    img, files = layout_workload(140)
+    want = oracle.match_hash(img, files)
+    with cv.master_build(files, max_load=max_load, bloom_bits_per_key=bloom) as mh:
+        occ = mh.info()["n_unique"] / mh.info()["n_slots"]
+    with cv.master_build(files, max_load=max_load, bloom_bits_per_key=bloom, layout=cv.CV_LAYOUT_AUTO) as m:
+        expect = cv.CV_LAYOUT_SORTED if occ > (0.8 if bloom else 0.5) else cv.CV_LAYOUT_HASH
+        assert m.info()["layout"] == expect, occ
+        with cv.scan(m, [torch.from_numpy(img).cuda()]) as r:
+            assert np.array_equal(r.matches(0), want)
