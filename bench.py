@@ -386,10 +386,13 @@ def run_sweep(torch, cv, synth, stream, steps, sizes=(10**3, 10**5, 10**6, 10**7
     return out
 
 
-FRAG_OPS_PER_WINDOW_DJB2 = 31  # rolled djb2 step, key mix and one-word Bloom test (see DESIGN)
+# Algorithmic integer ops per 64-byte window: the rolled djb2 step with its key mix and filter
+# tests; MD5 of one 64-byte message (a data block of 64 five-op steps, the padding block of 64
+# four-op steps, two feed-forwards), or of the data block alone without padding.
+FRAG_OPS_PER_WINDOW = {2: 31, 1: 64 * 5 + 4, 0: 64 * 5 + 64 * 4 + 8}
 
 
-def run_fragments(torch, cv, synth, stream, steps, cpu_sample_bytes, config="frag", sigs=(2, 1, 0)):
+def run_fragments(torch, cv, synth, stream, steps, cpu_sample_bytes, config="frag", sigs=(2, 1, 0), sm_mhz=2070.0):
     """Section 5's fragment scan on the 4 GiB fragment workload: every 64-byte window at a 4-byte
     offset against the 64-byte fragments of 2,000 logos, for djb2-64 (rolled, confirmed), MD5
     without padding and MD5, each checked against the plant log."""
@@ -418,8 +421,14 @@ def run_fragments(torch, cv, synth, stream, steps, cpu_sample_bytes, config="fra
         out[name] = {"GBps": fp.n_bytes / wall / 1e9, "count_kernel_GBps": fp.n_bytes / (kms * 1e-3) / 1e9,
                      "windows_per_s": windows / wall, "matches": matches, "planted_triples": int(exp.size),
                      "all_planted_found": planted_found}
-        if sig == 2:
-            out[name]["achieved_Tops_est"] = windows * FRAG_OPS_PER_WINDOW_DJB2 / (kms * 1e-3) / 1e12
+        ops = FRAG_OPS_PER_WINDOW[sig]
+        peak = SM_COUNT * INT_LANES_PER_SM_CLK * sm_mhz * 1e6
+        achieved = windows * ops / (kms * 1e-3)
+        hbm = measured_peaks().get("hbm_gbs", 6800.0)
+        out[name]["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Top/s",
+                                 "frac": achieved / peak, "ops_per_window": ops,
+                                 "frac_of_hbm": out[name]["count_kernel_GBps"] / hbm,
+                                 "peak_note": f"152 SMs x 128 int ops/clk x {sm_mhz:.0f} MHz"}
         m.close()
     if not cpu_sample_bytes:
         return out
@@ -745,7 +754,7 @@ def main():
     frags = None
     if not args.no_frag and rank == 0:
         frags = run_fragments(torch, cv, synth, stream, args.frag_steps, args.frag_cpu_mib << 20, args.frag_config,
-                              tuple(int(x) for x in args.frag_sigs.split(",")))
+                              tuple(int(x) for x in args.frag_sigs.split(",")), clocks.get("sm_mhz") or 2070.0)
 
     ip = cv.int_peak()
     int_peak = {k: ip[k] / 1e12 for k in ("alu_ops_per_s", "fma_ops_per_s", "mixed_ops_per_s")}
