@@ -319,17 +319,22 @@ def run_tables(torch, cv, synth, plan, image, stream, steps):
         sub = files[:k]
         # the load cap that sizes the table at exactly 2^22 slots for these sectors
         max_load = min(0.9, float(cum[k - 1]) / (slots * 0.9999))
-        for layout, lname in ((0, "hash"), (1, "sorted")):
-            for bloom in (0, 16):
-                m = cv.master_build(sub, max_load=max_load, layout=layout, bloom_bits_per_key=bloom)
-                info = m.info()
-                wall, kms, matches = time_scans(torch, cv, m, image, stream, steps)
-                out[f"occ{occ}_{lname}_{'bloom' if bloom else 'nobloom'}"] = {
-                    "occupancy": info["n_unique"] / max(info["n_slots"], 1), "n_slots": info["n_slots"],
-                    "master_sectors": int(cum[k - 1]),
-                    "max_probe_or_steps": info["max_probe"], "GBps": plan.n_bytes / wall / 1e9,
-                    "kernel_GBps": plan.n_bytes / (kms * 1e-3) / 1e9, "matches": matches}
-                m.close()
+        # MD5 with both layouts, Bloom on and off; the paper's measured signatures (djb2-64, CRC64)
+        # as it ran them, without a Bloom filter, with both layouts
+        variants = [(0, layout, bloom) for layout in (0, 1) for bloom in (0, 16)]
+        variants += [(sig, layout, 0) for sig in (2, 3) for layout in (0, 1)]
+        for sig, layout, bloom in variants:
+            m = cv.master_build(sub, max_load=max_load, layout=layout, bloom_bits_per_key=bloom, signature=sig)
+            info = m.info()
+            wall, kms, matches = time_scans(torch, cv, m, image, stream, steps)
+            sname = {0: "", 2: "djb2_", 3: "crc64_"}[sig]
+            lname = "sorted" if layout else "hash"
+            out[f"occ{occ}_{sname}{lname}_{'bloom' if bloom else 'nobloom'}"] = {
+                "occupancy": info["n_unique"] / max(info["n_slots"], 1), "n_slots": info["n_slots"],
+                "master_sectors": int(cum[k - 1]), "signature": sig,
+                "max_probe_or_steps": info["max_probe"], "GBps": plan.n_bytes / wall / 1e9,
+                "kernel_GBps": plan.n_bytes / (kms * 1e-3) / 1e9, "matches": matches}
+            m.close()
     del masters
     torch.cuda.synchronize()
     return out
@@ -338,6 +343,8 @@ def run_tables(torch, cv, synth, plan, image, stream, steps):
 # DRAM bytes (read + write) per launch of the default scan kernel, from one ncu capture of the
 # current kernel: 4.436 GB on the 4 GiB mid workload (8,388,608 sectors), scaled by sectors.
 SCAN_TRAFFIC_BYTES = {"mid": 4.4360e9, "scale": 8 * 4.4360e9}
+
+
 def run_sweep(torch, cv, synth, stream, steps, sizes=(10**3, 10**5, 10**6, 10**7, 5 * 10**7),
               densities=(1e-4, 1e-2, 1e-1)):
     """Table-scaling sweep: an 8 GiB image (16,777,216 sectors, seed 3) against master sets of
