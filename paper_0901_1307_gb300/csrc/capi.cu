@@ -257,6 +257,12 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
         CV_CUDA(cudaMalloc(&m->bloom, n_blocks * block_bytes));
         CV_CUDA(cudaMemsetAsync(m->bloom, 0, n_blocks * block_bytes, stream));
       }
+      if (frag) {
+        // the shared-memory prefilter of a fragment table exists even when the table is empty
+        // (all zero then: no window passes it)
+        CV_CUDA(cudaMalloc(&m->frag_l1, kFragL1Bytes));
+        CV_CUDA(cudaMemsetAsync(m->frag_l1, 0, kFragL1Bytes, stream));
+      }
       if (M) {
         if (frag) {
           CV_CUDA((cudaError_t)frag_digests(sig, arena, M, dig, trivial, ctx->sms, stream));
@@ -291,8 +297,6 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
           CV_CUDA(cudaGetLastError());
         }
         if (frag) {
-          CV_CUDA(cudaMalloc(&m->frag_l1, kFragL1Bytes));
-          CV_CUDA(cudaMemsetAsync(m->frag_l1, 0, kFragL1Bytes, stream));
           CV_CUDA((cudaError_t)frag_bloom((const uint4*)m->slots, (uint32_t)n_slots, (uint32_t*)m->bloom,
                                           bpk ? (uint32_t)(n_blocks - 1) : 0u, (uint32_t*)m->frag_l1, ctx->sms,
                                           stream));

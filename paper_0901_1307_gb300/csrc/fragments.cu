@@ -590,6 +590,7 @@ int frag_count(const TableView& tab, const uint8_t* image, uint64_t n_bytes, uin
   if (rc) return rc;
   Geom g;
   if (!geom((int)tab.sig, tab.layout, &g)) return (int)cudaErrorInvalidValue;
+  if (tab.sig == kSigDjb2 && !tab.frag_l1) return (int)cudaErrorInvalidValue;  // the kernel copies it in
   p.tile_ntrip = tile_ntrip;
   const uint64_t cap = (uint64_t)sms * (uint64_t)d->count_blocks[tab.sig][tab.layout];
   const uint64_t warps_per_block = (uint64_t)g.threads / 32;

@@ -182,3 +182,19 @@ def test_fragment_rejections(cv):
     o = cv.cv_master_opts(ctypes.sizeof(cv.cv_master_opts), 0.0, 0, 0, None, 0, 0, 2, 0)
     h = ctypes.c_void_p()
     assert lib.cv_master_build(None, 0, ctypes.byref(o), ctypes.byref(h)) == cv.CV_EINVAL
+
+
+@pytest.mark.parametrize("sig", SIGS)
+def test_empty_fragment_tables(cv, sig):
+    """Fragment tables without a single kept fragment (no files, an empty file, a file shorter
+    than a fragment, only all-equal fragments) find nothing, for every layout and filter."""
+    rng = np.random.default_rng(12)
+    img = rng.integers(0, 256, 50_000, dtype=np.uint8)
+    d, keep = dev(img)
+    for files in ([], [np.zeros(0, np.uint8)], [rng.integers(0, 256, 63, dtype=np.uint8)],
+                  [np.zeros(640, np.uint8), np.full(128, 7, np.uint8)]):
+        for layout in (0, 1):
+            for bloom in (0, 16):
+                with frag_master(cv, files, sig, layout=layout, bloom_bits_per_key=bloom) as m:
+                    with cv.scan(m, [d, img]) as r:
+                        assert r.matches(0).size == 0 and r.matches(1).size == 0
