@@ -76,3 +76,27 @@ def test_fuzz_against_oracle(cv, seed):
         with cv.scan(m, [src], chunk_bytes=chunk, base_offset=base) as r:
             got = r.matches(0)
     assert np.array_equal(got, want), (seed, kw, on_device, chunk)
+    if frag or seed % 3 or image.size < SECTOR:
+        return
+    # the same case through the batched, served and allocation-free entry points (sector tables,
+    # clusters counted from each image's sector 0)
+    if kw.get("position_mode"):
+        want = oracle.match_position(image, files, 0)
+    d = torch.from_numpy(image).cuda()
+    with cv.master_build(files, **kw) as m:
+        with cv.batch_create(m, [d, (d.data_ptr(), (image.size // 2) // SECTOR * SECTOR)],
+                             autotune=bool(seed % 2)) as b:
+            b.run()
+            b.wait()
+            assert np.array_equal(cv.device_matches_to_numpy(b.matches(0)), want)
+            half = image[: (image.size // 2) // SECTOR * SECTOR]
+            want_half = oracle.match_position(half, files, 0) if kw.get("position_mode") else oracle.match_hash(half, files)
+            assert np.array_equal(cv.device_matches_to_numpy(b.matches(1)), want_half)
+        with cv.server_create(m, work_unit_bytes=int(rng.integers(1, 9)) * SECTOR, hbm_budget_bytes=1 << 20) as srv:
+            t = srv.submit(np.ascontiguousarray(image))
+            r = srv.poll(t, timeout_ms=60000)
+            assert np.array_equal(r.matches(0), want)
+            r.close()
+        out = torch.empty(16 * (want.size + 4), dtype=torch.uint8, device="cuda")
+        rc, n = cv.scan_noalloc(m, d, out, want.size + 4)
+        assert rc == cv.CV_OK and np.array_equal(np.frombuffer(out[: n * 16].cpu().numpy().tobytes(), cv.MATCH_DTYPE), want)
