@@ -1,13 +1,13 @@
-// Host runtime of libcv.so: the C ABI of include/cv.h.
+// Host runtime of libcv.so: the C ABI of include/cv.h, apart from the master tables (master.cu),
+// batches (batch.cu), the server (server.cu) and the allocation-free scan (noalloc.cu).
 //
-// cv_master_build  master bytes -> device arena -> per-sector MD5 (scan kernel, digest mode)
-//                  -> table insert -> radix sort by slot -> postings + slots -> Bloom filter.
-// cv_scan          images -> segments (tensor maps over device memory, or host chunks copied
-//                  into a double-buffered device ring on a side stream) -> scan launches ->
-//                  tile offsets -> exact-size output -> expand -> per-image sorted matches.
+// cv_scan  images -> segments (tensor maps over device memory, or host chunks copied into a
+//          double-buffered device ring on a side stream) -> scan launches -> tile offsets ->
+//          exact-size output -> expand -> per-image sorted matches; over a fragment table,
+//          count -> offsets -> emit (fragments.cu).
 //
-// Temporaries come from a library-owned stream-ordered memory pool; long-lived objects (the
-// table, results) from cudaMalloc. Every CUDA error is returned as a CV_E* code.
+// Temporaries come from a library-owned stream-ordered memory pool; results from the pool or
+// from host memory. Every CUDA error is returned as a CV_E* code.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -24,45 +24,13 @@
 #include "cv.h"
 #include "cv_internal.h"
 #include "cv_launch.h"
+#include "handles.h"
 #include "runtime.h"
-#include "table_build.cuh"
 
 using namespace cvk;
 
 void cvk_batch_free(void* h);
 void cvk_server_free(void* h);
-
-namespace {
-constexpr uint32_t kMagicMaster = 0xC7A57E01u;
-constexpr uint32_t kMagicResult = 0xC7A57E02u;
-}  // namespace
-
-// ======================================================================== handles
-struct cv_master {
-  uint32_t magic;
-  int dev;
-  TableView tab;
-  void* slots;
-  void* postings;
-  void* bloom;
-  void* confirm;  // kept master sectors in posting order (64-bit signatures)
-  void* keys0;    // sorted layout: h0 of every record
-  void* frag_l1;  // fragment tables: the shared-memory filter
-  cv_master_info info;
-};
-
-struct cv_result {
-  uint32_t magic;
-  int dev;
-  bool on_device;
-  uint32_t n_images;
-  std::vector<uint64_t> off;  // n_images + 1
-  MatchOut* host;
-  MatchOut* dev_out;     // from the library's pool, released on free_stream
-  cudaStream_t free_stream;
-  cv_scan_stats st;
-  int launches;          // kernel launches of the scan
-};
 
 // ======================================================================= C ABI
 extern "C" {
@@ -115,8 +83,10 @@ const char* cv_kernel_config_name(int k) {
   return (k >= 0 && k < n) ? c[k].name : nullptr;
 }
 
-static int digest_job(DevCtx* ctx, int cfg_i, int sig, Job& job, uint4* digests, uint8_t* trivial, uint32_t* status,
-                      cudaStream_t stream, Temps& tmp) {
+}  // extern "C"
+
+int cvk::digest_job(DevCtx* ctx, int cfg_i, int sig, Job& job, uint4* digests, uint8_t* trivial, uint32_t* status,
+                    cudaStream_t stream, Temps& tmp) {
   Segment* segs_d;
   CV_TRY(tmp.alloc(&segs_d, job.segs.size() * sizeof(Segment)));
   CV_CUDA(cudaMemcpyAsync(segs_d, job.segs.data(), job.segs.size() * sizeof(Segment), cudaMemcpyHostToDevice, stream));
@@ -129,6 +99,8 @@ static int digest_job(DevCtx* ctx, int cfg_i, int sig, Job& job, uint4* digests,
   CV_TRY(launch_range(ctx, cfg_i, true, job, segs_d, 0, job.segs.size(), p, stream));
   return CV_OK;
 }
+
+extern "C" {
 
 int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t* trivial, void* stream_) {
   if (n_sectors == 0) return CV_OK;
@@ -148,255 +120,8 @@ int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t
   return digest_job(ctx, cfg_i, kSigMd5, job, (uint4*)digests, trivial, status, stream, tmp);
 }
 
-// Stable LSD radix sort of n (key, value) pairs by the low `bits` bits of the key, 8 bits per
-// pass, ping-ponging between (k0, v0) and (k1, v1); *kres/*vres receive the pair holding the
-// result.
-static int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint64_t n, int bits, Temps& tmp,
-                            cudaStream_t stream, uint32_t** kres, uint32_t** vres) {
-  const uint32_t nb = (uint32_t)((n + kRsChunk - 1) / kRsChunk);
-  uint32_t* hist;
-  CV_TRY(tmp.alloc(&hist, (uint64_t)std::max<uint32_t>(nb, 1) * 256 * 4));
-  for (int shift = 0; shift < bits && n; shift += 8) {
-    rs_hist_kernel<<<nb, kRsThreads, 0, stream>>>(k0, n, shift, hist, nb);
-    exclusive_scan_u32_kernel<<<1, 1024, 0, stream>>>(hist, (uint64_t)nb * 256);
-    rs_scatter_kernel<<<nb, kRsThreads, 0, stream>>>(k0, v0, k1, v1, n, shift, hist, nb);
-    CV_CUDA(cudaGetLastError());
-    std::swap(k0, k1);
-    std::swap(v0, v1);
-  }
-  *kres = k0;
-  *vres = v0;
-  return CV_OK;
-}
-
-int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts* opts, cv_master** out) {
-  NvtxRange nvtx_range("cv.master_build");
-  if (!out || (n_files && !files)) return CV_EINVAL;
-  *out = nullptr;
-  if (opts && opts->struct_size < offsetof(cv_master_opts, position_mode)) return CV_EINVAL;
-  const bool has_v2 = opts && opts->struct_size >= offsetof(cv_master_opts, unit);
-  const uint32_t position_mode = has_v2 ? opts->position_mode : CV_POSITION_ANY;
-  if (position_mode > CV_POSITION_CLUSTER) return CV_EINVAL;
-  const bool by_tau = position_mode == CV_POSITION_CLUSTER;
-  uint32_t layout = has_v2 ? opts->layout : CV_LAYOUT_HASH;
-  if (layout > CV_LAYOUT_AUTO) return CV_EINVAL;
-  const uint32_t unit = (opts && opts->struct_size >= sizeof(cv_master_opts)) ? opts->unit : CV_UNIT_SECTOR;
-  if (unit > CV_UNIT_FRAGMENT) return CV_EINVAL;
-  const bool frag = unit == CV_UNIT_FRAGMENT;
-  const uint64_t U = frag ? kFrag : kSector;  // bytes per master unit
-  float max_load = (opts && opts->max_load > 0.f) ? opts->max_load : 0.5f;
-  if (!(max_load > 0.f && max_load <= 0.9f)) return CV_EINVAL;
-  uint32_t bpk = opts ? opts->bloom_bits_per_key : CV_BLOOM_AUTO;
-  if (bpk == CV_BLOOM_AUTO) bpk = 16;
-  if (bpk > 64) return CV_EINVAL;
-  const int sig = opts ? (int)opts->signature : kSigMd5;
-  if (sig < 0 || sig > kSigCrc64) return CV_EINVAL;
-  if (frag && (!frag_sig_supported(sig) || by_tau)) return CV_EINVAL;
-  cudaStream_t stream = opts ? (cudaStream_t)opts->stream : nullptr;
-  DevCtx* ctx;
-  CV_TRY(get_ctx(&ctx));
-  int cfg_i;
-  const ScanCfg& cfg = scan_config_for(ctx->cfg_index, sig, &cfg_i);
-
-  // whole units (sectors or fragments) of every file, concatenated
-  std::vector<uint64_t> file_base(n_files + 1, 0);
-  for (uint32_t f = 0; f < n_files; f++) {
-    if (files[f].n_bytes && !files[f].data) return CV_EINVAL;
-    file_base[f + 1] = file_base[f] + files[f].n_bytes / U;
-  }
-  const uint64_t M = file_base[n_files];
-  if (M >= (1ull << 27)) return CV_EINVAL;
-
-  cv_master* m = (cv_master*)calloc(1, sizeof(cv_master));
-  if (!m) return CV_ENOMEM;
-  m->magic = kMagicMaster;
-  m->dev = ctx->dev;
-  int rc = CV_OK;
-  {
-    Temps tmp(ctx, stream);
-    auto body = [&]() -> int {
-      const uint64_t n_slots = std::max<uint64_t>(next_pow2((uint64_t)((double)M / max_load) + 1), 2);
-      if (n_slots > (1ull << 31)) return CV_EINVAL;
-      const uint32_t mask = (uint32_t)(n_slots - 1);
-      uint8_t* arena;
-      uint4* dig;
-      uint8_t* trivial;
-      uint32_t *owner, *cnt, *slot_of, *keys2, *vals, *vals2, *counters;
-      uint64_t* file_base_d;
-      CV_TRY(tmp.alloc(&arena, M * U));
-      CV_TRY(tmp.alloc(&dig, M * sizeof(uint4)));
-      CV_TRY(tmp.alloc(&trivial, M));
-      CV_TRY(tmp.alloc(&owner, n_slots * 4));
-      CV_TRY(tmp.alloc(&cnt, n_slots * 4));
-      CV_TRY(tmp.alloc(&slot_of, M * 4));
-      CV_TRY(tmp.alloc(&keys2, M * 4));
-      CV_TRY(tmp.alloc(&vals, M * 4));
-      CV_TRY(tmp.alloc(&vals2, M * 4));
-      CV_TRY(tmp.alloc(&counters, 16));  // max_disp, n_kept, n_unique, status
-      CV_TRY(tmp.alloc(&file_base_d, (n_files + 1) * 8));
-      uint8_t* tau = nullptr;  // per master sector cluster position (position-keyed tables)
-      if (by_tau) CV_TRY(tmp.alloc(&tau, std::max<uint64_t>(M, 1)));
-      CV_CUDA(cudaMemsetAsync(owner, 0, n_slots * 4, stream));
-      CV_CUDA(cudaMemsetAsync(cnt, 0, n_slots * 4, stream));
-      CV_CUDA(cudaMemsetAsync(counters, 0, 16, stream));
-      CV_CUDA(cudaMemcpyAsync(file_base_d, file_base.data(), (n_files + 1) * 8, cudaMemcpyHostToDevice, stream));
-      for (uint32_t f = 0; f < n_files; f++) {
-        const uint64_t ns = file_base[f + 1] - file_base[f];
-        if (ns)
-          CV_CUDA(cudaMemcpyAsync(arena + file_base[f] * U, files[f].data, ns * U, cudaMemcpyDefault, stream));
-      }
-      // long-lived table memory
-      CV_CUDA(cudaMalloc(&m->slots, n_slots * 32));
-      CV_CUDA(cudaMalloc(&m->postings, std::max<uint64_t>(M, 1) * 8));
-      CV_CUDA(cudaMemsetAsync(m->slots, 0, n_slots * 32, stream));
-      // Bloom blocks: 32 bytes for sector tables, one 32-bit word for fragment tables
-      const uint64_t block_bytes = frag ? 4 : 32;
-      uint64_t n_blocks = 0;
-      if (bpk) {
-        n_blocks = std::max<uint64_t>(next_pow2((M * bpk + block_bytes * 8 - 1) / (block_bytes * 8)), frag ? 8 : 1);
-        CV_CUDA(cudaMalloc(&m->bloom, n_blocks * block_bytes));
-        CV_CUDA(cudaMemsetAsync(m->bloom, 0, n_blocks * block_bytes, stream));
-      }
-      if (frag) {
-        // the shared-memory prefilter of a fragment table exists even when the table is empty
-        // (all zero then: no window passes it)
-        CV_CUDA(cudaMalloc(&m->frag_l1, kFragL1Bytes));
-        CV_CUDA(cudaMemsetAsync(m->frag_l1, 0, kFragL1Bytes, stream));
-      }
-      if (M) {
-        if (frag) {
-          CV_CUDA((cudaError_t)frag_digests(sig, arena, M, dig, trivial, ctx->sms, stream));
-        } else {
-          Job job;
-          CV_TRY(job.add(ctx, cfg, arena, M, 0, 0, false));
-          CV_TRY(digest_job(ctx, cfg_i, sig, job, dig, trivial, counters + 3, stream, tmp));
-        }
-        const unsigned g = grid_for(M, 256, ctx->sms);
-        if (tau) {
-          tau_kernel<<<g, 256, 0, stream>>>(file_base_d, n_files, M, tau);
-          CV_CUDA(cudaGetLastError());
-        }
-        insert_kernel<<<g, 256, 0, stream>>>(dig, trivial, tau, M, owner, cnt, slot_of, mask, counters, counters + 1,
-                                            counters + 3);
-        CV_CUDA(cudaGetLastError());
-        iota_kernel<<<g, 256, 0, stream>>>(vals, M);
-        CV_CUDA(cudaGetLastError());
-        // stable LSD radix sort of (slot_of, m) by slot_of; keys <= n_slots
-        int bits = 1;
-        while ((1ull << bits) <= n_slots) bits++;
-        uint32_t *kin, *vin;
-        CV_TRY(radix_sort_pairs(slot_of, vals, keys2, vals2, M, bits, tmp, stream, &kin, &vin));
-        fill_kernel<<<g, 256, 0, stream>>>(kin, vin, M, (uint32_t)n_slots, owner, cnt, dig, tau, file_base_d,
-                                          n_files, (uint4*)m->slots, (uint2*)m->postings, counters + 2);
-        CV_CUDA(cudaGetLastError());
-        if (sig_is_weak(sig)) {
-          // a copy of the kept master units in posting order, to confirm matches byte for byte
-          CV_CUDA(cudaMalloc(&m->confirm, M * U));
-          gather_units_kernel<<<grid_for(M * (U / 16), 256, ctx->sms), 256, 0, stream>>>(
-              (const uint4*)arena, kin, vin, M, (uint32_t)n_slots, (uint32_t)(U / 16), (uint4*)m->confirm);
-          CV_CUDA(cudaGetLastError());
-        }
-        if (frag) {
-          CV_CUDA((cudaError_t)frag_bloom((const uint4*)m->slots, (uint32_t)n_slots, (uint32_t*)m->bloom,
-                                          bpk ? (uint32_t)(n_blocks - 1) : 0u, (uint32_t*)m->frag_l1, ctx->sms,
-                                          stream));
-        } else if (bpk) {
-          bloom_kernel<<<grid_for(n_slots, 256, ctx->sms), 256, 0, stream>>>((const uint4*)m->slots,
-                                                                             (uint32_t)n_slots, (uint32_t*)m->bloom,
-                                                                             (uint32_t)(n_blocks - 1));
-          CV_CUDA(cudaGetLastError());
-        }
-      }
-      uint32_t hc[4];
-      CV_CUDA(cudaMemcpyAsync(hc, counters, 16, cudaMemcpyDeviceToHost, stream));
-      CV_CUDA(cudaStreamSynchronize(stream));
-      if (hc[3] & kStTableFull) return CV_ETABLEFULL;
-      if (hc[3] & kStTimeout) return CV_ETIMEOUT;
-      if (hc[3]) return CV_ECORRUPT;
-      if (layout == CV_LAYOUT_AUTO)  // thresholds from the occupancy sweep (Bloom on / off)
-        layout = (double)hc[2] > (bpk ? 0.8 : 0.5) * (double)n_slots ? CV_LAYOUT_SORTED : CV_LAYOUT_HASH;
-      uint32_t steps = 0;  // binary-search steps of the sorted layout
-      if (layout == CV_LAYOUT_SORTED) {
-        // the occupied slots, compacted in slot order, sorted by h0 (stable: deterministic)
-        const uint32_t nu = hc[2];
-        uint32_t *ck, *cv, *ck2, *cv2, *kr, *vr;
-        CV_TRY(tmp.alloc(&ck, n_slots * 4));
-        CV_TRY(tmp.alloc(&cv, n_slots * 4));
-        CV_TRY(tmp.alloc(&ck2, n_slots * 4));
-        CV_TRY(tmp.alloc(&cv2, n_slots * 4));
-        const unsigned gs = grid_for(n_slots, 256, ctx->sms);
-        occupied_keys_kernel<<<gs, 256, 0, stream>>>((const uint4*)m->slots, (uint32_t)n_slots, ck, cv);
-        CV_CUDA(cudaGetLastError());
-        CV_TRY(radix_sort_pairs(ck, cv, ck2, cv2, n_slots, 1, tmp, stream, &kr, &vr));
-        uint32_t* kfree = kr == ck ? ck2 : ck;  // the other key buffer is free for the h0 keys
-        uint32_t* vfree = vr == cv ? cv2 : cv;
-        const unsigned gu = grid_for(std::max<uint32_t>(nu, 1), 256, ctx->sms);
-        h0_keys_kernel<<<gu, 256, 0, stream>>>((const uint4*)m->slots, vr, nu, kfree);
-        CV_CUDA(cudaGetLastError());
-        uint32_t *hk, *hv;
-        CV_TRY(radix_sort_pairs(kfree, vr, kr, vfree, nu, 32, tmp, stream, &hk, &hv));
-        void* sorted_slots = nullptr;
-        CV_CUDA(cudaMalloc(&sorted_slots, std::max<uint64_t>(nu, 1) * 32));
-        CV_CUDA(cudaMalloc(&m->keys0, std::max<uint64_t>(nu, 1) * 4));
-        gather_slots_kernel<<<gu, 256, 0, stream>>>((const uint4*)m->slots, hv, nu, (uint4*)sorted_slots);
-        CV_CUDA(cudaGetLastError());
-        if (nu) CV_CUDA(cudaMemcpyAsync(m->keys0, hk, (uint64_t)nu * 4, cudaMemcpyDeviceToDevice, stream));
-        CV_CUDA(cudaStreamSynchronize(stream));
-        cudaFree(m->slots);
-        m->slots = sorted_slots;
-        while ((1ull << steps) < nu) steps++;
-      }
-      m->tab.slots = (const uint4*)m->slots;
-      m->tab.keys0 = (const uint32_t*)m->keys0;
-      m->tab.layout = layout;
-      m->tab.n_keys = hc[2];
-      m->tab.postings = (const uint2*)m->postings;
-      m->tab.bloom = (const uint4*)m->bloom;
-      m->tab.slot_mask = mask;
-      m->tab.bloom_mask = bpk ? (uint32_t)(n_blocks - 1) : 0u;
-      m->tab.max_probe = hc[0] + 1;
-      m->tab.use_bloom = bpk ? 1u : 0u;
-      m->tab.sig = (uint32_t)sig;
-      m->tab.confirm = (const uint8_t*)m->confirm;
-      m->tab.tau_mask = by_tau ? 7u : 0u;
-      m->tab.unit = unit;
-      m->tab.frag_l1 = (const uint32_t*)m->frag_l1;
-      m->info.unit = unit;
-      m->tab.tau_add = 0u;
-      m->info.signature = (uint32_t)sig;
-      m->info.position_mode = position_mode;
-      m->info.n_files = n_files;
-      m->info.n_sectors = M;
-      m->info.n_kept = hc[1];
-      m->info.n_unique = hc[2];
-      m->info.n_slots = n_slots;
-      m->info.bloom_bytes = n_blocks * block_bytes;
-      m->info.max_probe = layout == CV_LAYOUT_SORTED ? steps : hc[0] + 1;
-      m->info.layout = layout;
-      const uint64_t table_bytes =
-          layout == CV_LAYOUT_SORTED ? std::max<uint64_t>(hc[2], 1) * 36 : n_slots * 32;
-      if (layout == CV_LAYOUT_SORTED) m->info.n_slots = hc[2];
-      m->info.device_bytes = table_bytes + std::max<uint64_t>(M, 1) * 8 + n_blocks * block_bytes +
-                             (m->confirm ? M * U : 0) + (m->frag_l1 ? kFragL1Bytes : 0);
-      return CV_OK;
-    };
-    rc = body();
-  }
-  if (rc == CV_OK) {
-    cudaError_t e = cudaStreamSynchronize(stream);  // temporaries returned
-    if (e != cudaSuccess) rc = cuda_fail(e);
-  }
-  if (rc != CV_OK) {
-    cv_free(m);
-    return rc;
-  }
-  *out = m;
-  return CV_OK;
-}
-
 }  // extern "C"
 
-// Device view of a master table for other translation units of the library.
 namespace cvk {
 // A one-image result holding a copy of n host triples (used by the serving loop).
 cv_result* make_host_result(int dev, const MatchOut* data, uint64_t n, uint64_t sectors, float total_ms) {
@@ -427,12 +152,6 @@ cv_result* make_host_result(int dev, const MatchOut* data, uint64_t n, uint64_t 
   return r;
 }
 
-int master_view(const cv_master* m, TableView* tab, int* dev) {
-  if (!m || m->magic != kMagicMaster) return CV_EINVAL;
-  *tab = m->tab;
-  *dev = m->dev;
-  return CV_OK;
-}
 }  // namespace cvk
 
 namespace {
@@ -574,192 +293,8 @@ int frag_scan(DevCtx* ctx, const cv_master* m, const cv_buf* images, uint32_t n_
 
 }  // namespace
 
-namespace {
-
-// The table file: this header, then the arrays in header order (byte counts in the header).
-struct TableFileHeader {
-  char magic[8];              // "CVTABLE" + '\0'
-  uint32_t version;           // 1
-  uint32_t header_bytes;      // sizeof(TableFileHeader)
-  cv_master_info info;
-  uint32_t slot_mask, bloom_mask, max_probe, use_bloom, sig, tau_mask, layout, n_keys, unit, reserved;
-  uint64_t bytes_slots, bytes_postings, bytes_bloom, bytes_confirm, bytes_keys0, bytes_l1;
-};
-constexpr char kTableMagic[8] = {'C', 'V', 'T', 'A', 'B', 'L', 'E', 0};
-constexpr uint32_t kTableVersion = 1;
-
-uint64_t table_unit_bytes(uint32_t unit) { return unit == kUnitFragment ? kFrag : kSector; }
-
-// Device <-> file in bounded pieces through one host buffer.
-int copy_to_file(FILE* f, const void* dev, uint64_t n) {
-  std::vector<uint8_t> buf(std::min<uint64_t>(n, 64ull << 20));
-  for (uint64_t off = 0; off < n; off += buf.size()) {
-    const uint64_t k = std::min<uint64_t>(buf.size(), n - off);
-    CV_CUDA(cudaMemcpy(buf.data(), (const uint8_t*)dev + off, k, cudaMemcpyDeviceToHost));
-    if (fwrite(buf.data(), 1, k, f) != k) return CV_EIO;
-  }
-  return CV_OK;
-}
-
-int copy_from_file(FILE* f, void* dev, uint64_t n) {
-  std::vector<uint8_t> buf(std::min<uint64_t>(n, 64ull << 20));
-  for (uint64_t off = 0; off < n; off += buf.size()) {
-    const uint64_t k = std::min<uint64_t>(buf.size(), n - off);
-    if (fread(buf.data(), 1, k, f) != k) return CV_EIO;
-    CV_CUDA(cudaMemcpy((uint8_t*)dev + off, buf.data(), k, cudaMemcpyHostToDevice));
-  }
-  return CV_OK;
-}
-
-}  // namespace
-
 extern "C" {
 
-int cv_master_get_info(const cv_master* m, cv_master_info* info) {
-  if (!m || !info || m->magic != kMagicMaster) return CV_EINVAL;
-  *info = m->info;
-  return CV_OK;
-}
-
-int cv_master_save(const cv_master* m, const char* path) {
-  NvtxRange nvtx_range("cv.master_save");
-  if (!m || m->magic != kMagicMaster || !path) return CV_EINVAL;
-  DevCtx* ctx;
-  CV_TRY(get_ctx(&ctx));
-  if (ctx->dev != m->dev) return CV_EINVAL;
-  const cv_master_info& in = m->info;
-  const uint64_t unit = table_unit_bytes(in.unit);
-  TableFileHeader h;
-  memset(&h, 0, sizeof h);
-  memcpy(h.magic, kTableMagic, 8);
-  h.version = kTableVersion;
-  h.header_bytes = sizeof h;
-  h.info = in;
-  h.slot_mask = m->tab.slot_mask;
-  h.bloom_mask = m->tab.bloom_mask;
-  h.max_probe = m->tab.max_probe;
-  h.use_bloom = m->tab.use_bloom;
-  h.sig = m->tab.sig;
-  h.tau_mask = m->tab.tau_mask;
-  h.layout = m->tab.layout;
-  h.n_keys = m->tab.n_keys;
-  h.unit = m->tab.unit;
-  h.bytes_slots = (m->tab.layout == kLayoutSorted ? (uint64_t)m->tab.n_keys : in.n_slots) * 32;
-  h.bytes_postings = in.n_kept * 8;
-  h.bytes_bloom = m->bloom ? in.bloom_bytes : 0;
-  h.bytes_confirm = m->confirm ? in.n_kept * unit : 0;
-  h.bytes_keys0 = m->keys0 ? (uint64_t)m->tab.n_keys * 4 : 0;
-  h.bytes_l1 = m->frag_l1 ? kFragL1Bytes : 0;
-  CV_CUDA(cudaDeviceSynchronize());
-  FILE* f = fopen(path, "wb");
-  if (!f) return CV_EIO;
-  int rc = fwrite(&h, sizeof h, 1, f) == 1 ? CV_OK : CV_EIO;
-  const void* arrays[6] = {m->slots, m->postings, m->bloom, m->confirm, m->keys0, m->frag_l1};
-  const uint64_t sizes[6] = {h.bytes_slots, h.bytes_postings, h.bytes_bloom, h.bytes_confirm, h.bytes_keys0,
-                             h.bytes_l1};
-  for (int k = 0; k < 6 && rc == CV_OK; k++)
-    if (sizes[k]) rc = copy_to_file(f, arrays[k], sizes[k]);
-  if (fclose(f) != 0 && rc == CV_OK) rc = CV_EIO;
-  return rc;
-}
-
-int cv_master_load(const char* path, void* stream_, cv_master** out) {
-  NvtxRange nvtx_range("cv.master_load");
-  if (!path || !out) return CV_EINVAL;
-  *out = nullptr;
-  DevCtx* ctx;
-  CV_TRY(get_ctx(&ctx));
-  cudaStream_t stream = (cudaStream_t)stream_;
-  FILE* f = fopen(path, "rb");
-  if (!f) return CV_EIO;
-  TableFileHeader h;
-  if (fread(&h, sizeof h, 1, f) != 1) {
-    fclose(f);
-    return CV_EIO;
-  }
-  // the parameters must describe a table this library could have built
-  const cv_master_info& in = h.info;
-  const uint64_t unit = table_unit_bytes(h.unit);
-  const uint64_t n_records = h.layout == kLayoutSorted ? (uint64_t)h.n_keys : in.n_slots;
-  const uint64_t bloom_block = h.unit == kUnitFragment ? 4 : 32;
-  const bool ok = memcmp(h.magic, kTableMagic, 8) == 0 && h.version == kTableVersion &&
-                  h.header_bytes == sizeof h && h.unit <= kUnitFragment && h.layout <= kLayoutSorted &&
-                  h.sig <= (uint32_t)kSigCrc64 && in.unit == h.unit && in.layout == h.layout &&
-                  in.signature == h.sig && (h.tau_mask == 0u || h.tau_mask == 7u) && in.n_kept <= in.n_sectors &&
-                  in.n_sectors < (1ull << 27) && in.n_unique <= in.n_kept && in.n_slots >= 1 &&
-                  in.n_slots <= (1ull << 31) &&
-                  (h.layout == kLayoutSorted ? h.n_keys == in.n_unique && in.n_slots == in.n_unique
-                                             : ((uint64_t)h.slot_mask + 1 == in.n_slots &&
-                                                (in.n_slots & (in.n_slots - 1)) == 0 && h.max_probe <= in.n_slots)) &&
-                  h.bytes_slots == n_records * 32 && h.bytes_postings == in.n_kept * 8 &&
-                  h.bytes_confirm == (sig_is_weak((int)h.sig) ? in.n_kept * unit : 0) &&
-                  h.bytes_keys0 == (h.layout == kLayoutSorted ? (uint64_t)h.n_keys * 4 : 0) &&
-                  h.bytes_l1 == (h.unit == kUnitFragment ? kFragL1Bytes : 0) &&
-                  h.use_bloom == (h.bytes_bloom ? 1u : 0u) && h.bytes_bloom == in.bloom_bytes &&
-                  (!h.use_bloom || ((uint64_t)h.bloom_mask + 1) * bloom_block == h.bytes_bloom) &&
-                  (h.bloom_mask & ((uint64_t)h.bloom_mask + 1)) == 0;
-  if (!ok) {
-    fclose(f);
-    return CV_ECORRUPT;
-  }
-  cv_master* m = (cv_master*)calloc(1, sizeof(cv_master));
-  if (!m) {
-    fclose(f);
-    return CV_ENOMEM;
-  }
-  m->magic = kMagicMaster;
-  m->dev = ctx->dev;
-  auto body = [&]() -> int {
-    void** arrays[6] = {&m->slots, &m->postings, &m->bloom, &m->confirm, &m->keys0, &m->frag_l1};
-    const uint64_t sizes[6] = {h.bytes_slots, h.bytes_postings, h.bytes_bloom, h.bytes_confirm, h.bytes_keys0,
-                               h.bytes_l1};
-    const bool always[6] = {true, true, false, false, false, false};  // the build allocates these even when empty
-    for (int k = 0; k < 6; k++) {
-      if (!sizes[k] && !always[k]) continue;
-      CV_CUDA(cudaMalloc(arrays[k], std::max<uint64_t>(sizes[k], 32)));
-      if (sizes[k]) CV_TRY(copy_from_file(f, *arrays[k], sizes[k]));
-    }
-    uint8_t extra;
-    if (fread(&extra, 1, 1, f) != 0) return CV_ECORRUPT;  // trailing bytes: not this table's file
-    uint32_t* status;
-    CV_CUDA(cudaMallocAsync((void**)&status, 4, stream));
-    CV_CUDA(cudaMemsetAsync(status, 0, 4, stream));
-    validate_slots_kernel<<<grid_for(std::max<uint64_t>(n_records, 1), 256, ctx->sms), 256, 0, stream>>>(
-        (const uint4*)m->slots, n_records, in.n_kept, status);
-    CV_CUDA(cudaGetLastError());
-    uint32_t st = 0;
-    CV_CUDA(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, stream));
-    CV_CUDA(cudaFreeAsync(status, stream));
-    CV_CUDA(cudaStreamSynchronize(stream));
-    if (st) return CV_ECORRUPT;
-    m->tab.slots = (const uint4*)m->slots;
-    m->tab.postings = (const uint2*)m->postings;
-    m->tab.bloom = (const uint4*)m->bloom;
-    m->tab.confirm = (const uint8_t*)m->confirm;
-    m->tab.keys0 = (const uint32_t*)m->keys0;
-    m->tab.frag_l1 = (const uint32_t*)m->frag_l1;
-    m->tab.slot_mask = h.slot_mask;
-    m->tab.bloom_mask = h.bloom_mask;
-    m->tab.max_probe = h.max_probe;
-    m->tab.use_bloom = h.use_bloom;
-    m->tab.sig = h.sig;
-    m->tab.tau_mask = h.tau_mask;
-    m->tab.tau_add = 0;
-    m->tab.layout = h.layout;
-    m->tab.n_keys = h.n_keys;
-    m->tab.unit = h.unit;
-    m->info = in;
-    return CV_OK;
-  };
-  const int rc = body();
-  fclose(f);
-  if (rc != CV_OK) {
-    cv_free(m);
-    return rc;
-  }
-  *out = m;
-  return CV_OK;
-}
 
 int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const cv_scan_opts* opts, cv_result** out) {
   NvtxRange nvtx_range("cv.scan");
