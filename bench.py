@@ -613,7 +613,7 @@ def main():
     ap.add_argument("--batch-density", type=float, default=0.01)
     ap.add_argument("--batch-runs", type=int, default=10)
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-density", type=float, default=0.02)
     ap.add_argument("--serve-budget-gb", type=int, default=120)
