@@ -537,7 +537,7 @@ def run_served(torch, cv, synth, args, host):
     size_s = np.minimum(size_s, pool_sectors // 8 * 8)
     start = (rng.integers(0, (pool_sectors - size_s) // 8 + 1) * 8).astype(np.int64)
     srv = cv.server_create(m, hbm_budget_bytes=args.serve_budget_gb * 10**9, work_unit_bytes=64 << 20, max_live=64,
-                           copy_streams=4)
+                           copy_streams=4, max_copy_bytes=int(args.serve_copy_gib * 2**30) if args.serve_copy_gib else 0)
     base = host.data_ptr()
     tickets = [None] * n
     arrivals = np.cumsum(gaps)
@@ -554,11 +554,13 @@ def run_served(torch, cv, synth, args, host):
     t0 = time.perf_counter()
     th.start()
     exact = True
+    lat = np.zeros(n)
     for k in range(n):
         while tickets[k] is None:
             time.sleep(0.0005)
         r = srv.poll(tickets[k], timeout_ms=-1)
         got = r.matches(0)
+        lat[k] = r.stats()["total_ms"]
         r.close()
         if not np.array_equal(got, expected_window(expect, int(start[k]), int(size_s[k]))):
             exact = False
@@ -572,6 +574,11 @@ def run_served(torch, cv, synth, args, host):
                         f"windows of a {pool_sectors * SECTOR / 2**30:.0f} GiB pinned pool, "
                         f"{int(file_nsect.sum())}-sector table, HBM budget {args.serve_budget_gb} GB",
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
+            "chunks_p50_ms": float(np.percentile(lat[~drive], 50)), "chunks_p99_ms": float(np.percentile(lat[~drive], 99)),
+            "drives_p50_ms": float(np.percentile(lat[drive], 50)), "drives_p99_ms": float(np.percentile(lat[drive], 99)),
+            "drives_copy_floor_p99_ms": float(np.percentile(size_s[drive] * SECTOR / (args.h2d_link_gbps * 1e9) * 1e3,
+                                                            99)),
+            "host_memory": "cv_host_alloc (private anonymous mapping registered with the CUDA driver)",
             "throughput_GBps": total_b / st["wall_s"] / 1e9 if st["wall_s"] else None, "wall_s": wall,
             "bytes": total_b, "iterations": st["iterations"], "units": st["units"],
             "mean_live_per_iteration": st["mean_live_per_iteration"],
@@ -617,11 +624,28 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--serve-density", type=float, default=0.02)
     ap.add_argument("--serve-budget-gb", type=int, default=120)
+    ap.add_argument("--serve-copy-gib", type=float, default=0.0, help="copy bytes queued at once (0: the library's)")
+    ap.add_argument("--h2d-link-gbps", type=float, default=211.0, help="host link rate for the drives' copy floor")
+    ap.add_argument("--serve-only", action="store_true", help="run only the served section and print its JSON")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve_only:
+        import torch
+
+        import __graft_entry__
+
+        __graft_entry__.build()
+        from paper_0901_1307_gb300 import cv, synth
+
+        hostbuf = cv.host_alloc(32 << 30)
+        host = torch.from_numpy(hostbuf.array())
+        print(json.dumps(run_served(torch, cv, synth, args, host)))
+        del host
+        hostbuf.close()
+        return 0
     if args.sweep_only:
         import torch
 
@@ -705,11 +729,12 @@ def main():
     if not args.no_tables:
         tables = run_tables(torch, cv, synth, plan, image, stream, args.table_steps)
 
-    # end to end through the C ABI from pinned host memory
+    # end to end through the C ABI from pinned host memory (cv_host_alloc)
     e2e = None
-    host = None
+    host = hostbuf = None
     if not args.no_e2e or not args.no_serve:
-        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        hostbuf = cv.host_alloc(nbytes)
+        host = torch.from_numpy(hostbuf.array())
         host.copy_(image)
     del image
     torch.cuda.synchronize()
@@ -724,7 +749,7 @@ def main():
             r.close()
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-        e2e = {"value": world * nbytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nbytes,
+        e2e = {"value": world * nbytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nbytes, "host_memory": "cv_host_alloc",
                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
         # the host link itself: one plain copy of 8 GiB of the pinned image to the device
         probe = torch.empty(8 << 30, dtype=torch.uint8, device="cuda")
@@ -814,6 +839,8 @@ def main():
         line["served"] = run_served(torch, cv, synth, args, host)
         line["p99_served_ms"] = line["served"]["p99_ms"]
     del host
+    if hostbuf is not None:
+        hostbuf.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(plan, args.cpu_sample_pieces)
     if rank == 0:

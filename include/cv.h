@@ -332,6 +332,10 @@ typedef struct {
   uint64_t work_unit_bytes;  /* request data per work unit (multiple of 512); 0 = 64 MiB */
   uint32_t kernel_config;    /* 0 = default; k + 1 = configuration k */
   uint32_t copy_streams;     /* host-to-device copy streams; 0 = 2 */
+  uint64_t max_copy_bytes;   /* request data queued on the copy streams at once (more is issued as
+                                copies land, so later requests are not stuck behind a large one);
+                                0 = 2 GiB, UINT64_MAX = no limit. The size without this field (32
+                                bytes) is accepted and means 0. */
 } cv_server_opts;
 
 typedef struct {
@@ -383,6 +387,29 @@ int cv_server_get_stats(cv_server* s, cv_server_stats* st);
 #define CV_NOALLOC_MAX_SECTORS (1u << 19)
 int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n_bytes, cv_match* out, uint64_t out_capacity,
                     uint64_t* n_out, void* stream);
+
+/*
+ * Host memory to read images into before they are scanned (the host buffers of the paper's
+ * Section 3.1 and Figure 7), mapped so that host-to-device copies from it run at the link
+ * rate for as long as the kernel keeps it in huge pages. On a GB300 the GPU reads host memory
+ * through the CPU's page tables; measured on its Grace host, copies from memory in 64 KiB
+ * base pages (cudaHostAlloc memory, registered memory, locked or not) fell from 210 GB/s to
+ * 3-20 GB/s within a minute of a serving loop running, with host page faults on every pass,
+ * while memory in 512 MiB huge pages kept 210 GB/s unless the kernel split its huge pages
+ * (seen in two of four processes), after which the split part behaved as base pages do.
+ * A block is a private anonymous mapping aligned to the kernel's transparent huge page size,
+ * advised for huge pages, populated, locked where RLIMIT_MEMLOCK allows, and registered with
+ * the CUDA driver (pinned). Where the kernel grants no huge pages it still works, as base
+ * pages.
+ *   cv_host_alloc  *out = the block (aligned to the huge page size, contents zero; the mapping
+ *                  is rounded up to a whole number of huge pages). Errors: CV_EINVAL (n_bytes
+ *                  0 or out NULL), CV_ENOMEM, CV_ECUDA, CV_ENODEV.
+ *   cv_host_free   releases a block from cv_host_alloc; the caller ensures no copy from it is
+ *                  still in flight. NULL is a no-op; any other pointer: CV_EINVAL.
+ * Any host memory can still be passed to the scan calls; this is only the fast kind.
+ */
+int cv_host_alloc(uint64_t n_bytes, void** out);
+int cv_host_free(void* p);
 
 #ifdef __cplusplus
 }

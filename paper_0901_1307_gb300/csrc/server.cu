@@ -6,7 +6,8 @@
 //   - Requests are cut into work units (default 64 MiB of whole sectors).
 //   - A device arena of hbm_budget_bytes holds units in flight, one slot per unit. Units are
 //     copied host-to-device on side streams as slots free up, round robin over the live
-//     requests so large drives do not starve small network chunks.
+//     requests, fewest bytes left first, with at most max_copy_bytes queued on the streams at
+//     once, so a small network chunk is not stuck behind the queued copies of a large drive.
 //   - Every engine iteration takes, for each live request, its units that have landed on the
 //     device (in order) and scans all of them in one launch (continuous batching). The whole
 //     arena is one allocation, so one tensor map covers every unit.
@@ -14,6 +15,7 @@
 //     unit has been scanned. Units of one request are always scanned in order, so its matches
 //     stay sorted and equal a solo cv_scan of the image.
 // One engine thread per server; cv_submit and cv_poll may be called from any thread.
+#include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -111,6 +113,8 @@ struct cv_server {
   bool any_submit = false;
   double live_sum = 0;
   uint64_t bytes_in_flight = 0;
+  uint64_t copy_cap = 0;      // bytes queued on the copy streams at most (at least one unit)
+  uint64_t copy_queued = 0;   // bytes issued and not yet seen landed
 
   void run();
   int iterate(bool* did_work);
@@ -183,14 +187,22 @@ int cv_server::iterate(bool* did_work) {
     work = live;
   }
   if (work.empty()) return CV_OK;
-  // copies: round robin over live requests, one unit per request per pass, while slots last
+  // copies: round robin over live requests, one unit per request per pass, while slots and the
+  // copy cap last; the request with the fewest bytes left to copy goes first, so a small request
+  // is not queued behind the rest of a large one
+  std::vector<Request*> order;
+  for (Request* r : work)
+    if (!r->device && r->next_copy < r->units.size()) order.push_back(r);
+  const auto left = [](const Request* r) { return r->n_sectors - r->units[r->next_copy].first_sector; };
+  std::stable_sort(order.begin(), order.end(), [&](const Request* a, const Request* b) { return left(a) < left(b); });
   bool issued = true;
   while (issued && !free_slots.empty()) {
     issued = false;
-    for (Request* r : work) {
+    for (Request* r : order) {
       if (free_slots.empty()) break;
-      if (r->device || r->next_copy >= r->units.size()) continue;
+      if (r->next_copy >= r->units.size()) continue;
       Unit& u = r->units[r->next_copy];
+      if (copy_queued && copy_queued + u.n_sectors * kSector > copy_cap) continue;
       u.slot = free_slots.back();
       free_slots.pop_back();
       u.copy_stream = (int)(r->next_copy % copy_streams.size());
@@ -200,6 +212,7 @@ int cv_server::iterate(bool* did_work) {
       CV_CUDA(cudaEventRecord(slot_event[u.slot], cs));
       u.copied = true;
       bytes_in_flight += u.n_sectors * kSector;
+      copy_queued += u.n_sectors * kSector;
       st.peak_bytes_in_flight = std::max(st.peak_bytes_in_flight, bytes_in_flight);
       r->next_copy++;
       issued = true;
@@ -226,6 +239,7 @@ int cv_server::iterate(bool* did_work) {
         cudaError_t q = cudaEventQuery(slot_event[u.slot]);
         if (q == cudaErrorNotReady) break;
         if (q != cudaSuccess) return cuda_fail(q);
+        copy_queued -= u.n_sectors * kSector;  // each unit is gathered once
         Segment s;
         s.n_sectors = u.n_sectors;
         s.tile_base = job.n_tiles;
@@ -354,7 +368,8 @@ extern "C" {
 int cv_server_create(const cv_master* m, const cv_server_opts* opts, cv_server** out) {
   if (!m || !out) return CV_EINVAL;
   *out = nullptr;
-  if (opts && opts->struct_size < sizeof(cv_server_opts)) return CV_EINVAL;
+  if (opts && opts->struct_size < offsetof(cv_server_opts, max_copy_bytes)) return CV_EINVAL;
+  const uint64_t copy_cap_opt = (opts && opts->struct_size >= sizeof(cv_server_opts)) ? opts->max_copy_bytes : 0u;
   TableView tab;
   int mdev;
   if (master_view(m, &tab, &mdev) != CV_OK || tab.unit != kUnitSector) return CV_EINVAL;
@@ -385,6 +400,7 @@ int cv_server_create(const cv_master* m, const cv_server_opts* opts, cv_server**
   s->cfg_i = cfg_i;
   s->tab = tab;
   s->unit_bytes = unit;
+  s->copy_cap = copy_cap_opt ? copy_cap_opt : (2ull << 30);
   s->unit_sectors = unit / kSector;
   s->max_live = (opts && opts->max_live) ? opts->max_live : 64u;
   s->n_slots = (int)slots;

@@ -40,7 +40,8 @@ EXPORTS = ("cv_master_build", "cv_master_get_info", "cv_scan", "cv_matches", "cv
            "cv_strerror", "cv_last_cuda_error", "cv_sector_digests", "cv_kernel_config_count",
            "cv_kernel_config_name", "cv_scan_noalloc", "cv_batch_create", "cv_batch_run", "cv_batch_wait",
            "cv_batch_matches", "cv_batch_get_info", "cv_server_create", "cv_submit", "cv_poll",
-           "cv_server_get_stats", "cv_int_peak", "cv_selftest_wait_timeout", "cv_master_save", "cv_master_load")
+           "cv_server_get_stats", "cv_int_peak", "cv_selftest_wait_timeout", "cv_master_save", "cv_master_load",
+           "cv_host_alloc", "cv_host_free")
 CV_EAGAIN = -9
 CV_EIO = -10
 CV_BATCH_BLOOM_AUTO = 0
@@ -100,7 +101,7 @@ class cv_batch_info(ctypes.Structure):
 class cv_server_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("max_live", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64),
                 ("work_unit_bytes", ctypes.c_uint64), ("kernel_config", ctypes.c_uint32),
-                ("copy_streams", ctypes.c_uint32)]
+                ("copy_streams", ctypes.c_uint32), ("max_copy_bytes", ctypes.c_uint64)]
 
 
 class cv_server_stats(ctypes.Structure):
@@ -182,6 +183,10 @@ def load(path: str = LIB_PATH):
         lib.cv_int_peak.restype = i32
         lib.cv_selftest_wait_timeout.argtypes = [u32, vp]
         lib.cv_selftest_wait_timeout.restype = i32
+        lib.cv_host_alloc.argtypes = [u64, ctypes.POINTER(vp)]
+        lib.cv_host_alloc.restype = i32
+        lib.cv_host_free.argtypes = [vp]
+        lib.cv_host_free.restype = i32
         _lib = lib
         return lib
 
@@ -519,10 +524,10 @@ class Server:
 
 
 def server_create(master: Master, max_live: int = 0, hbm_budget_bytes: int = 0, work_unit_bytes: int = 0,
-                  kernel_config: int = 0, copy_streams: int = 0) -> Server:
+                  kernel_config: int = 0, copy_streams: int = 0, max_copy_bytes: int = 0) -> Server:
     """cv_server_create: a serving loop over one resident master table."""
     o = cv_server_opts(ctypes.sizeof(cv_server_opts), max_live, hbm_budget_bytes, work_unit_bytes, kernel_config,
-                       copy_streams)
+                       copy_streams, max_copy_bytes)
     h = ctypes.c_void_p()
     _check(load().cv_server_create(master.handle, ctypes.byref(o), ctypes.byref(h)), "cv_server_create")
     return Server(h.value)
@@ -538,3 +543,44 @@ def int_peak() -> dict:
 def selftest_wait_timeout(timeout_us: int, stream=None) -> int:
     """cv_selftest_wait_timeout: return code of a bounded wait that runs out (CV_ETIMEOUT)."""
     return int(load().cv_selftest_wait_timeout(timeout_us, _stream(stream)))
+
+
+class HostBuffer:
+    """Host memory from cv_host_alloc: huge pages, registered with the driver (pinned); copies
+    from it keep the full link rate.
+
+    ``array()`` is a numpy uint8 view of it (``torch.from_numpy`` gives a CPU tensor over the
+    same memory); the view must not outlive ``close()``."""
+
+    def __init__(self, n_bytes: int):
+        p = ctypes.c_void_p()
+        _check(load().cv_host_alloc(n_bytes, ctypes.byref(p)), "cv_host_alloc")
+        self.ptr = int(p.value)
+        self.nbytes = int(n_bytes)
+
+    def array(self) -> np.ndarray:
+        if not self.ptr:
+            raise ValueError("host buffer is closed")
+        return np.ctypeslib.as_array((ctypes.c_uint8 * self.nbytes).from_address(self.ptr))
+
+    def close(self) -> None:
+        if self.ptr:
+            _check(load().cv_host_free(self.ptr), "cv_host_free")
+            self.ptr = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def host_alloc(n_bytes: int) -> HostBuffer:
+    """cv_host_alloc: n_bytes of pinned, huge-page host memory for images."""
+    return HostBuffer(n_bytes)

@@ -3,6 +3,8 @@
 Everything here is integer work, so the bar is bit-exact: identical digests, identical trivial
 flags, identical sorted match lists.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -337,6 +339,45 @@ def test_server_results_equal_solo_scans(cv):
         a, n = cuts[0]
         with cv.scan(m, [np.ascontiguousarray(full[a * SECTOR:(a + n) * SECTOR])]) as r:
             assert_same(r.matches(0), oracle.match_hash(full[a * SECTOR:(a + n) * SECTOR], files), "solo")
+
+
+@pytest.mark.parametrize("cap", [1, 3 << 20, 2**64 - 1])
+def test_server_copy_cap(cv, cap):
+    """However many copy bytes may be queued at once (one unit, a few, no limit), every request,
+    large and small, submitted together, gets the oracle's matches."""
+    plan = synth.config_plan("small:60000:60:52")
+    files = plan.masters_host()
+    full = plan.image_host()
+    pinned = torch.from_numpy(full).pin_memory()
+    cuts = [(0, 60000), (100, 7), (30000, 25000), (5, 1), (59000, 1000), (7000, 33)]
+    with cv.master_build(files) as m:
+        with cv.server_create(m, work_unit_bytes=1 << 20, copy_streams=3, max_copy_bytes=cap) as srv:
+            tickets = [srv.submit(pinned[a * SECTOR:(a + n) * SECTOR], tag=k) for k, (a, n) in enumerate(cuts)]
+            for k, t in enumerate(tickets):
+                r = srv.poll(t, timeout_ms=60000)
+                a, n = cuts[k]
+                assert_same(r.matches(0), oracle.match_hash(full[a * SECTOR:(a + n) * SECTOR], files), f"request {k}")
+                r.close()
+
+
+def test_server_opts_without_copy_cap_field(cv):
+    """Options of the size before max_copy_bytes existed are accepted (the cap takes its
+    default); anything shorter is refused."""
+    files = [synth.random_sectors(4, 64)]
+    lib = cv.load()
+    with cv.master_build(files) as m:
+        for size, ok in [(ctypes.sizeof(cv.cv_server_opts) - 8, True), (ctypes.sizeof(cv.cv_server_opts) - 12, False)]:
+            o = cv.cv_server_opts(size, 0, 0, 0, 0, 0, 123)
+            h = ctypes.c_void_p()
+            rc = lib.cv_server_create(m.handle, ctypes.byref(o), ctypes.byref(h))
+            assert (rc == cv.CV_OK) == ok, (size, rc)
+            if h.value:
+                srv = cv.Server(h.value)
+                t = srv.submit(np.ascontiguousarray(files[0]))
+                r = srv.poll(t, timeout_ms=60000)
+                assert r.count(0) == 64
+                r.close()
+                srv.close()
 
 
 def test_server_poll_nonblocking_and_unknown_ticket(cv):
