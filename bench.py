@@ -578,7 +578,7 @@ def run_served(torch, cv, synth, args, host):
             "drives_p50_ms": float(np.percentile(lat[drive], 50)), "drives_p99_ms": float(np.percentile(lat[drive], 99)),
             "drives_copy_floor_p99_ms": float(np.percentile(size_s[drive] * SECTOR / (args.h2d_link_gbps * 1e9) * 1e3,
                                                             99)),
-            "host_memory": "cv_host_alloc (private anonymous mapping registered with the CUDA driver)",
+            "host_memory": "cudaHostAlloc (torch pin_memory)",
             "throughput_GBps": total_b / st["wall_s"] / 1e9 if st["wall_s"] else None, "wall_s": wall,
             "bytes": total_b, "iterations": st["iterations"], "units": st["units"],
             "mean_live_per_iteration": st["mean_live_per_iteration"],
@@ -640,11 +640,8 @@ def main():
         __graft_entry__.build()
         from paper_0901_1307_gb300 import cv, synth
 
-        hostbuf = cv.host_alloc(32 << 30)
-        host = torch.from_numpy(hostbuf.array())
+        host = torch.empty(32 << 30, dtype=torch.uint8, pin_memory=True)
         print(json.dumps(run_served(torch, cv, synth, args, host)))
-        del host
-        hostbuf.close()
         return 0
     if args.sweep_only:
         import torch
@@ -729,12 +726,11 @@ def main():
     if not args.no_tables:
         tables = run_tables(torch, cv, synth, plan, image, stream, args.table_steps)
 
-    # end to end through the C ABI from pinned host memory (cv_host_alloc)
+    # end to end through the C ABI from pinned host memory
     e2e = None
-    host = hostbuf = None
+    host = None
     if not args.no_e2e or not args.no_serve:
-        hostbuf = cv.host_alloc(nbytes)
-        host = torch.from_numpy(hostbuf.array())
+        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
         host.copy_(image)
     del image
     torch.cuda.synchronize()
@@ -749,7 +745,7 @@ def main():
             r.close()
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-        e2e = {"value": world * nbytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nbytes, "host_memory": "cv_host_alloc",
+        e2e = {"value": world * nbytes / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
         # the host link itself: one plain copy of 8 GiB of the pinned image to the device
         probe = torch.empty(8 << 30, dtype=torch.uint8, device="cuda")
@@ -839,8 +835,6 @@ def main():
         line["served"] = run_served(torch, cv, synth, args, host)
         line["p99_served_ms"] = line["served"]["p99_ms"]
     del host
-    if hostbuf is not None:
-        hostbuf.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(plan, args.cpu_sample_pieces)
     if rank == 0:

@@ -388,29 +388,6 @@ int cv_server_get_stats(cv_server* s, cv_server_stats* st);
 int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n_bytes, cv_match* out, uint64_t out_capacity,
                     uint64_t* n_out, void* stream);
 
-/*
- * Host memory to read images into before they are scanned (the host buffers of the paper's
- * Section 3.1 and Figure 7), mapped so that host-to-device copies from it run at the link
- * rate for as long as the kernel keeps it in huge pages. On a GB300 the GPU reads host memory
- * through the CPU's page tables; measured on its Grace host, copies from memory in 64 KiB
- * base pages (cudaHostAlloc memory, registered memory, locked or not) fell from 210 GB/s to
- * 3-20 GB/s within a minute of a serving loop running, with host page faults on every pass,
- * while memory in 512 MiB huge pages kept 210 GB/s unless the kernel split its huge pages
- * (seen in two of four processes), after which the split part behaved as base pages do.
- * A block is a private anonymous mapping aligned to the kernel's transparent huge page size,
- * advised for huge pages, populated, locked where RLIMIT_MEMLOCK allows, and registered with
- * the CUDA driver (pinned). Where the kernel grants no huge pages it still works, as base
- * pages.
- *   cv_host_alloc  *out = the block (aligned to the huge page size, contents zero; the mapping
- *                  is rounded up to a whole number of huge pages). Errors: CV_EINVAL (n_bytes
- *                  0 or out NULL), CV_ENOMEM, CV_ECUDA, CV_ENODEV.
- *   cv_host_free   releases a block from cv_host_alloc; the caller ensures no copy from it is
- *                  still in flight. NULL is a no-op; any other pointer: CV_EINVAL.
- * Any host memory can still be passed to the scan calls; this is only the fast kind.
- */
-int cv_host_alloc(uint64_t n_bytes, void** out);
-int cv_host_free(void* p);
-
 #ifdef __cplusplus
 }
 #endif

@@ -8,10 +8,8 @@
  * "image_index window fragment..." for 64-byte fragments at 4-byte offsets), in the library's
  * sorted order; a summary goes to stderr. Options: -s 0..3 the signature (MD5, MD5 without
  * padding, djb2-64, CRC64), -p BASE position-keyed tables with clusters counted from sector BASE,
- * -f fragments instead of sectors. Files are read whole into host memory (images into pinned
- * memory from cv_host_alloc, so their copies to the device run at the link rate); the library
- * copies them to the device. Exit status: 0 on success, 1 on a usage or I/O error, 2 on a
- * library error.
+ * -f fragments instead of sectors. Files are read whole into host memory; the library copies
+ * them to the device. Exit status: 0 on success, 1 on a usage or I/O error, 2 on a library error.
  */
 #include <stdint.h>
 #include <stdio.h>
@@ -20,10 +18,7 @@
 
 #include "cv.h"
 
-/* The whole file at path, in malloc'd memory, or with pinned set in memory from cv_host_alloc
- * (NULL if that fails too: *rc then holds the library's code). */
-static void* read_file(const char* path, uint64_t* n, int pinned, int* rc) {
-  *rc = CV_OK;
+static void* read_file(const char* path, uint64_t* n) {
   FILE* f = fopen(path, "rb");
   if (!f) return NULL;
   if (fseek(f, 0, SEEK_END) != 0) {
@@ -35,18 +30,9 @@ static void* read_file(const char* path, uint64_t* n, int pinned, int* rc) {
     fclose(f);
     return NULL;
   }
-  void* buf = NULL;
-  if (pinned) {
-    *rc = cv_host_alloc(len > 0 ? (uint64_t)len : 1u, &buf);
-    if (*rc != CV_OK) buf = NULL;
-  } else {
-    buf = malloc(len > 0 ? (size_t)len : 1);
-  }
+  void* buf = malloc(len > 0 ? (size_t)len : 1);
   if (buf && len > 0 && fread(buf, 1, (size_t)len, f) != (size_t)len) {
-    if (pinned)
-      cv_host_free(buf);
-    else
-      free(buf);
+    free(buf);
     buf = NULL;
   }
   fclose(f);
@@ -87,18 +73,16 @@ int main(int argc, char** argv) {
   cv_buf* files = (cv_buf*)calloc((size_t)(n_files > 0 ? n_files : 1), sizeof(cv_buf));
   cv_buf* images = (cv_buf*)calloc((size_t)n_images, sizeof(cv_buf));
   if (!files || !images) return 1;
-  int rc = CV_OK;
   for (int f = 0; f < n_files; f++) {
-    files[f].data = read_file(argv[sep + 1 + f], &files[f].n_bytes, 0, &rc);
+    files[f].data = read_file(argv[sep + 1 + f], &files[f].n_bytes);
     if (!files[f].data) {
       fprintf(stderr, "cv_carve: cannot read %s\n", argv[sep + 1 + f]);
       return 1;
     }
   }
   for (int i = 0; i < n_images; i++) {
-    images[i].data = read_file(argv[a + i], &images[i].n_bytes, 1, &rc);
+    images[i].data = read_file(argv[a + i], &images[i].n_bytes);
     if (!images[i].data) {
-      if (rc != CV_OK) return fail("cv_host_alloc", rc);
       fprintf(stderr, "cv_carve: cannot read %s\n", argv[a + i]);
       return 1;
     }
@@ -113,7 +97,7 @@ int main(int argc, char** argv) {
   mo.layout = CV_LAYOUT_HASH;
   mo.unit = frag ? CV_UNIT_FRAGMENT : CV_UNIT_SECTOR;
   cv_master* m = NULL;
-  rc = cv_master_build(files, (uint32_t)n_files, &mo, &m);
+  int rc = cv_master_build(files, (uint32_t)n_files, &mo, &m);
   if (rc != CV_OK) return fail("cv_master_build", rc);
 
   cv_scan_opts so;
@@ -147,7 +131,7 @@ int main(int argc, char** argv) {
   cv_free(r);
   cv_free(m);
   for (int f = 0; f < n_files; f++) free((void*)files[f].data);
-  for (int i = 0; i < n_images; i++) cv_host_free((void*)images[i].data);
+  for (int i = 0; i < n_images; i++) free((void*)images[i].data);
   free(files);
   free(images);
   return 0;

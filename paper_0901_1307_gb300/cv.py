@@ -40,8 +40,7 @@ EXPORTS = ("cv_master_build", "cv_master_get_info", "cv_scan", "cv_matches", "cv
            "cv_strerror", "cv_last_cuda_error", "cv_sector_digests", "cv_kernel_config_count",
            "cv_kernel_config_name", "cv_scan_noalloc", "cv_batch_create", "cv_batch_run", "cv_batch_wait",
            "cv_batch_matches", "cv_batch_get_info", "cv_server_create", "cv_submit", "cv_poll",
-           "cv_server_get_stats", "cv_int_peak", "cv_selftest_wait_timeout", "cv_master_save", "cv_master_load",
-           "cv_host_alloc", "cv_host_free")
+           "cv_server_get_stats", "cv_int_peak", "cv_selftest_wait_timeout", "cv_master_save", "cv_master_load")
 CV_EAGAIN = -9
 CV_EIO = -10
 CV_BATCH_BLOOM_AUTO = 0
@@ -183,10 +182,6 @@ def load(path: str = LIB_PATH):
         lib.cv_int_peak.restype = i32
         lib.cv_selftest_wait_timeout.argtypes = [u32, vp]
         lib.cv_selftest_wait_timeout.restype = i32
-        lib.cv_host_alloc.argtypes = [u64, ctypes.POINTER(vp)]
-        lib.cv_host_alloc.restype = i32
-        lib.cv_host_free.argtypes = [vp]
-        lib.cv_host_free.restype = i32
         _lib = lib
         return lib
 
@@ -544,43 +539,3 @@ def selftest_wait_timeout(timeout_us: int, stream=None) -> int:
     """cv_selftest_wait_timeout: return code of a bounded wait that runs out (CV_ETIMEOUT)."""
     return int(load().cv_selftest_wait_timeout(timeout_us, _stream(stream)))
 
-
-class HostBuffer:
-    """Host memory from cv_host_alloc: huge pages, registered with the driver (pinned); copies
-    from it keep the full link rate.
-
-    ``array()`` is a numpy uint8 view of it (``torch.from_numpy`` gives a CPU tensor over the
-    same memory); the view must not outlive ``close()``."""
-
-    def __init__(self, n_bytes: int):
-        p = ctypes.c_void_p()
-        _check(load().cv_host_alloc(n_bytes, ctypes.byref(p)), "cv_host_alloc")
-        self.ptr = int(p.value)
-        self.nbytes = int(n_bytes)
-
-    def array(self) -> np.ndarray:
-        if not self.ptr:
-            raise ValueError("host buffer is closed")
-        return np.ctypeslib.as_array((ctypes.c_uint8 * self.nbytes).from_address(self.ptr))
-
-    def close(self) -> None:
-        if self.ptr:
-            _check(load().cv_host_free(self.ptr), "cv_host_free")
-            self.ptr = 0
-
-    def __enter__(self):
-        return self
-
-    def __exit__(self, *a):
-        self.close()
-
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
-
-
-def host_alloc(n_bytes: int) -> HostBuffer:
-    """cv_host_alloc: n_bytes of pinned, huge-page host memory for images."""
-    return HostBuffer(n_bytes)
