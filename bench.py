@@ -327,13 +327,20 @@ def run_tables(torch, cv, synth, plan, image, stream, steps):
             m = cv.master_build(sub, max_load=max_load, layout=layout, bloom_bits_per_key=bloom, signature=sig)
             info = m.info()
             wall, kms, matches = time_scans(torch, cv, m, image, stream, steps)
+            # exact table reads of the lookups, on the image's first 2 GiB (4,194,304 sectors)
+            prof = image[: 1 << 31]
+            pr = cv.probe_profile(m, prof, stream=stream)
+            ns = prof.numel() // SECTOR
             sname = {0: "", 2: "djb2_", 3: "crc64_"}[sig]
             lname = "sorted" if layout else "hash"
             out[f"occ{occ}_{sname}{lname}_{'bloom' if bloom else 'nobloom'}"] = {
                 "occupancy": info["n_unique"] / max(info["n_slots"], 1), "n_slots": info["n_slots"],
                 "master_sectors": int(cum[k - 1]), "signature": sig,
                 "max_probe_or_steps": info["max_probe"], "GBps": plan.n_bytes / wall / 1e9,
-                "kernel_GBps": plan.n_bytes / (kms * 1e-3) / 1e9, "matches": matches}
+                "kernel_GBps": plan.n_bytes / (kms * 1e-3) / 1e9, "matches": matches,
+                "bloom_pass_per_sector": pr["bloom_passed"] / ns, "slot_reads_per_sector": pr["slot_reads"] / ns,
+                "key_reads_per_sector": pr["key_reads"] / ns,
+                "slot_reads_per_lookup": pr["slot_reads"] / max(pr["bloom_passed"], 1)}
             m.close()
     del masters
     torch.cuda.synchronize()
@@ -380,12 +387,16 @@ def run_sweep(torch, cv, synth, stream, steps, sizes=(10**3, 10**5, 10**6, 10**7
                 r = cv.scan(m, [image], stream=stream)
                 exact = bool(np.array_equal(r.matches(0), exp))
                 r.close()
+                pr = cv.probe_profile(m, image, stream=stream)
                 out[f"M{M}_d{dens:g}_{name}"] = {
                     "master_sectors": M, "files": int(file_nsect.size), "density": dens, "bloom": name == "bloom",
                     "table_MB": info["n_slots"] * 32 / 1e6, "bloom_MB": info["bloom_bytes"] / 1e6 if name == "bloom" else 0,
                     "max_probe": info["max_probe"], "build_s": build_s, "GBps": plan.n_bytes / wall / 1e9,
                     "kernel_GBps": plan.n_bytes / (kms * 1e-3) / 1e9, "kernel_ns_per_sector": kms * 1e6 / S,
-                    "matches": matches, "exact_vs_plant_log": exact}
+                    "matches": matches, "exact_vs_plant_log": exact,
+                    "bloom_pass_per_sector": pr["bloom_passed"] / S, "slot_reads_per_sector": pr["slot_reads"] / S,
+                    "slot_reads_per_lookup": pr["slot_reads"] / max(pr["bloom_passed"], 1),
+                    "found_sectors": pr["found"]}
             del image
             torch.cuda.synchronize()
         for m in tables.values():

@@ -222,6 +222,34 @@ typedef struct {
 
 int cv_scan_get_stats(const cv_result* r, cv_scan_stats* st);
 
+/*
+ * Lookup cost, counted exactly: what the scan of an image reads from the table (the paper's
+ * occupancy study, Section 4, Figures 10-12). The scan's own lookups are replayed outside the
+ * scan kernel (which keeps no counters): the Bloom test when the table has a filter, then
+ * the linear-probing walk from the home slot of Eq. 3 up to the table's probe bound (hash
+ * layout), or the bisection over the sorted key words and the comparison of the records that
+ * share the sector's key word (sorted layout).
+ *   image        device pointer, 16-byte aligned; n_bytes / 512 whole sectors are looked up.
+ *   base_offset  as cv_scan_opts.base_offset (position-keyed tables).
+ *   st           st->struct_size = sizeof(cv_probe_stats); filled on success.
+ * Sector tables only (a fragment table: CV_EINVAL). Runs on stream and returns after the work
+ * has finished. Errors: CV_EINVAL, CV_ENOMEM, CV_ECUDA, CV_ETIMEOUT, CV_ENODEV.
+ */
+typedef struct {
+  uint32_t struct_size;    /* sizeof(cv_probe_stats) */
+  uint32_t layout;         /* the table's layout: CV_LAYOUT_HASH or CV_LAYOUT_SORTED */
+  uint64_t sectors;        /* sectors looked up */
+  uint64_t bloom_passed;   /* of them, those the Bloom filter let through (all, without one) */
+  uint64_t slot_reads;     /* 32-byte table records read: the probe walks' slots (hash layout),
+                              the records compared after the bisection (sorted layout) */
+  uint64_t key_reads;      /* sorted layout: 4-byte key words read by the bisections and the
+                              scans over equal key words; 0 for the hash layout */
+  uint64_t found;          /* sectors whose key (signature, and position in S_tau tables) is in
+                              the table; for 64-bit signatures before byte confirmation */
+} cv_probe_stats;
+int cv_probe_profile(const cv_master* m, const void* image, uint64_t n_bytes, uint64_t base_offset,
+                     cv_probe_stats* st, void* stream);
+
 /* Free a cv_master, cv_result, cv_batch or cv_server handle (NULL is ignored). A server first
  * finishes its admitted requests and stops its engine thread. */
 void cv_free(void* handle);

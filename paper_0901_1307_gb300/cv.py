@@ -40,7 +40,8 @@ EXPORTS = ("cv_master_build", "cv_master_get_info", "cv_scan", "cv_matches", "cv
            "cv_strerror", "cv_last_cuda_error", "cv_sector_digests", "cv_kernel_config_count",
            "cv_kernel_config_name", "cv_scan_noalloc", "cv_batch_create", "cv_batch_run", "cv_batch_wait",
            "cv_batch_matches", "cv_batch_get_info", "cv_server_create", "cv_submit", "cv_poll",
-           "cv_server_get_stats", "cv_int_peak", "cv_selftest_wait_timeout", "cv_master_save", "cv_master_load")
+           "cv_server_get_stats", "cv_int_peak", "cv_selftest_wait_timeout", "cv_master_save", "cv_master_load",
+           "cv_probe_profile")
 CV_EAGAIN = -9
 CV_EIO = -10
 CV_BATCH_BLOOM_AUTO = 0
@@ -82,6 +83,12 @@ class cv_scan_stats(ctypes.Structure):
     _fields_ = [("sectors", ctypes.c_uint64), ("matches", ctypes.c_uint64), ("hit_sectors", ctypes.c_uint64),
                 ("kernel_ms", ctypes.c_float), ("total_ms", ctypes.c_float), ("kernel_launches", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
+
+
+class cv_probe_stats(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("layout", ctypes.c_uint32), ("sectors", ctypes.c_uint64),
+                ("bloom_passed", ctypes.c_uint64), ("slot_reads", ctypes.c_uint64), ("key_reads", ctypes.c_uint64),
+                ("found", ctypes.c_uint64)]
 
 
 class cv_batch_opts(ctypes.Structure):
@@ -182,6 +189,8 @@ def load(path: str = LIB_PATH):
         lib.cv_int_peak.restype = i32
         lib.cv_selftest_wait_timeout.argtypes = [u32, vp]
         lib.cv_selftest_wait_timeout.restype = i32
+        lib.cv_probe_profile.argtypes = [vp, vp, u64, u64, ctypes.POINTER(cv_probe_stats), vp]
+        lib.cv_probe_profile.restype = i32
         _lib = lib
         return lib
 
@@ -539,3 +548,13 @@ def selftest_wait_timeout(timeout_us: int, stream=None) -> int:
     """cv_selftest_wait_timeout: return code of a bounded wait that runs out (CV_ETIMEOUT)."""
     return int(load().cv_selftest_wait_timeout(timeout_us, _stream(stream)))
 
+
+
+def probe_profile(master: Master, image, base_offset: int = 0, stream=None) -> dict:
+    """cv_probe_profile: exact table reads of the scan's lookups over one device image."""
+    ip, nb, _k = _buf(image)
+    st = cv_probe_stats()
+    st.struct_size = ctypes.sizeof(cv_probe_stats)
+    _check(load().cv_probe_profile(master.handle, ip, nb, base_offset, ctypes.byref(st), _stream(stream)),
+           "cv_probe_profile")
+    return {k: getattr(st, k) for k, _ in cv_probe_stats._fields_ if k != "struct_size"}
