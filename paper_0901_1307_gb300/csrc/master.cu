@@ -43,6 +43,145 @@ int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uin
   return CV_OK;
 }
 
+// One copy of the gather stage: bytes from src to dst_base + dst.
+struct CopyPiece {
+  const uint8_t* src;
+  uint64_t dst;
+  uint64_t bytes;
+};
+
+constexpr uint64_t kPieceBytes = 4ull << 20;   // device runs are cut into pieces of this size
+constexpr uint64_t kHostDirect = 4ull << 20;   // host runs this long are copied by the driver
+constexpr uint64_t kStageBytes = 64ull << 20;  // pinned staging chunk for shorter host runs
+
+// Each block copies whole pieces (grid-stride over them), 16 bytes at a time when the source,
+// the destination and the length allow it, else byte by byte.
+__global__ void gather_pieces_kernel(const CopyPiece* pieces, uint32_t n, uint8_t* dst_base) {
+  for (uint32_t r = blockIdx.x; r < n; r += gridDim.x) {
+    const CopyPiece c = pieces[r];
+    uint8_t* d = dst_base + c.dst;
+    if ((((uintptr_t)c.src | (uintptr_t)d | c.bytes) & 15u) == 0) {
+      const uint4* s4 = reinterpret_cast<const uint4*>(c.src);
+      uint4* d4 = reinterpret_cast<uint4*>(d);
+      for (uint64_t i = threadIdx.x; i < c.bytes / 16; i += blockDim.x) d4[i] = s4[i];
+    } else {
+      for (uint64_t i = threadIdx.x; i < c.bytes; i += blockDim.x) d[i] = c.src[i];
+    }
+  }
+}
+
+int launch_gather(const std::vector<CopyPiece>& pieces, uint8_t* dst_base, int sms, Temps& tmp, cudaStream_t stream) {
+  if (pieces.empty()) return CV_OK;
+  CopyPiece* d;
+  CV_TRY(tmp.alloc(&d, pieces.size() * sizeof(CopyPiece)));
+  CV_CUDA(cudaMemcpyAsync(d, pieces.data(), pieces.size() * sizeof(CopyPiece), cudaMemcpyHostToDevice, stream));
+  const uint64_t g = std::min<uint64_t>(pieces.size(), (uint64_t)sms * 8);
+  gather_pieces_kernel<<<(unsigned)g, 256, 0, stream>>>(d, (uint32_t)pieces.size(), dst_base);
+  CV_CUDA(cudaGetLastError());
+  return CV_OK;
+}
+
+// The whole units of every file into the arena (file f's at arena + file_base[f] * U). One
+// copy call per file costs microseconds of host time each, which dominated the build of master
+// sets of many small files. So: files contiguous in memory are merged into runs; runs in this
+// GPU's memory are copied by one gather launch; host runs of kHostDirect bytes or more by the
+// driver, one call each; shorter host runs are packed by the host into a pinned staging chunk,
+// copied to the device in one call per chunk and scattered by a gather launch; anything else
+// (managed memory, another GPU's) by the driver. Memory is classified once per CUDA allocation
+// (cuMemGetAddressRange), not once per file.
+int gather_master_units(DevCtx* ctx, const cv_buf* files, uint32_t n_files, const std::vector<uint64_t>& file_base,
+                        uint64_t U, uint8_t* arena, Temps& tmp, cudaStream_t stream) {
+  std::vector<CopyPiece> runs;
+  for (uint32_t f = 0; f < n_files; f++) {
+    const uint64_t bytes = (file_base[f + 1] - file_base[f]) * U;
+    if (!bytes) continue;
+    const uint8_t* src = (const uint8_t*)files[f].data;
+    const uint64_t dst = file_base[f] * U;
+    if (!runs.empty() && runs.back().src + runs.back().bytes == src && runs.back().dst + runs.back().bytes == dst)
+      runs.back().bytes += bytes;
+    else
+      runs.push_back(CopyPiece{src, dst, bytes});
+  }
+  // Where a run lives: this GPU's memory (gathered by a kernel), host memory the CPU may read
+  // (pageable, pinned or registered: staged, or copied by the driver when long), or anything
+  // else (managed memory, another GPU's memory: copied by the driver).
+  enum RunKind { kThisGpu, kHostMem, kByDriver };
+  std::vector<CopyPiece> dev_pieces, host_short;
+  uintptr_t lo = 0, hi = 0;  // the last CUDA allocation classified, and its kind
+  RunKind lo_kind = kHostMem;
+  for (size_t q = 0; q < runs.size(); q++) {
+    CopyPiece r = runs[q];
+    const uintptr_t a = (uintptr_t)r.src;
+    RunKind kind = kHostMem;  // not inside a CUDA allocation: ordinary host memory
+    if (a >= lo && a < hi) {
+      kind = lo_kind;
+    } else {
+      CUdeviceptr ab = 0;
+      size_t asz = 0;
+      if (ctx->address_range && ctx->address_range(&ab, &asz, (CUdeviceptr)a) == CUDA_SUCCESS) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, r.src) != cudaSuccess) {
+          cudaGetLastError();
+          kind = kByDriver;
+        } else if (at.type == cudaMemoryTypeDevice && at.device == ctx->dev) {
+          kind = kThisGpu;
+        } else {
+          kind = at.type == cudaMemoryTypeHost ? kHostMem : kByDriver;
+        }
+        lo = (uintptr_t)ab;
+        hi = lo + asz;
+        lo_kind = kind;
+      }
+    }
+    if (a >= lo && a < hi && a + r.bytes > hi) {
+      // files merged across the end of an allocation: the rest is classified on its own
+      const uint64_t head = hi - a;
+      runs.push_back(CopyPiece{r.src + head, r.dst + head, r.bytes - head});
+      r.bytes = head;
+    }
+    if (kind == kThisGpu) {
+      for (uint64_t o = 0; o < r.bytes; o += kPieceBytes)
+        dev_pieces.push_back(CopyPiece{r.src + o, r.dst + o, std::min(kPieceBytes, r.bytes - o)});
+    } else if (kind == kByDriver || r.bytes >= kHostDirect) {
+      CV_CUDA(cudaMemcpyAsync(arena + r.dst, r.src, r.bytes, cudaMemcpyDefault, stream));
+    } else {
+      host_short.push_back(r);
+    }
+  }
+  CV_TRY(launch_gather(dev_pieces, arena, ctx->sms, tmp, stream));
+  if (host_short.empty()) return CV_OK;
+  // short host runs: pinned chunk -> device staging -> scattered into the arena
+  uint64_t total = 0;
+  for (const CopyPiece& r : host_short) total += r.bytes;
+  const uint64_t chunk = std::min(total, kStageBytes);
+  uint8_t* staged;
+  CV_TRY(tmp.alloc(&staged, chunk));
+  uint8_t* pinned = nullptr;
+  CV_CUDA(cudaMallocHost((void**)&pinned, chunk));
+  int rc = CV_OK;
+  size_t i = 0;
+  while (i < host_short.size() && rc == CV_OK) {
+    std::vector<CopyPiece> pieces;
+    uint64_t used = 0;
+    for (; i < host_short.size() && used + host_short[i].bytes <= chunk; i++) {
+      memcpy(pinned + used, host_short[i].src, host_short[i].bytes);
+      pieces.push_back(CopyPiece{staged + used, host_short[i].dst, host_short[i].bytes});
+      used += host_short[i].bytes;
+    }
+    cudaError_t e = cudaMemcpyAsync(staged, pinned, used, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e);
+      break;
+    }
+    rc = launch_gather(pieces, arena, ctx->sms, tmp, stream);
+    // the pinned chunk and the device staging are reused: wait before refilling them, and
+    // before the pinned chunk is freed
+    if (rc == CV_OK && (e = cudaStreamSynchronize(stream)) != cudaSuccess) rc = cuda_fail(e);
+  }
+  cudaFreeHost(pinned);
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -118,11 +257,7 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       CV_CUDA(cudaMemsetAsync(cnt, 0, n_slots * 4, stream));
       CV_CUDA(cudaMemsetAsync(counters, 0, 16, stream));
       CV_CUDA(cudaMemcpyAsync(file_base_d, file_base.data(), (n_files + 1) * 8, cudaMemcpyHostToDevice, stream));
-      for (uint32_t f = 0; f < n_files; f++) {
-        const uint64_t ns = file_base[f + 1] - file_base[f];
-        if (ns)
-          CV_CUDA(cudaMemcpyAsync(arena + file_base[f] * U, files[f].data, ns * U, cudaMemcpyDefault, stream));
-      }
+      CV_TRY(gather_master_units(ctx, files, n_files, file_base, U, arena, tmp, stream));
       // long-lived table memory
       CV_CUDA(cudaMalloc(&m->slots, n_slots * 32));
       CV_CUDA(cudaMalloc(&m->postings, std::max<uint64_t>(M, 1) * 8));
