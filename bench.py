@@ -352,6 +352,33 @@ def run_tables(torch, cv, synth, plan, image, stream, steps):
 SCAN_TRAFFIC_BYTES = {"mid": 4.4360e9, "scale": 8 * 4.4360e9}
 
 
+def run_build(torch, cv, synth, M, reps=3):
+    """Table builds (cv_master_build, MD5, Bloom filter) of the sweep's master set of M sectors,
+    device-resident, as many files as that set has; the first build is a warm-up."""
+    file_nsect, mseed = synth.sweep_master_set(M)
+    mplan = synth.Plan(0, mseed, 0, file_nsect, np.zeros(0, np.int32), np.zeros(0, np.uint32), np.zeros(0, np.uint8))
+    base = mplan.file_base()
+    base_d = torch.from_numpy(base.view(np.uint8).copy()).cuda()
+    masters = torch.empty(M * SECTOR, dtype=torch.uint8, device="cuda")
+    mplan.masters_device(masters.data_ptr(), base_d.data_ptr())
+    torch.cuda.synchronize()
+    files = [(masters.data_ptr() + int(base[f]) * SECTOR, int(file_nsect[f]) * SECTOR) for f in range(file_nsect.size)]
+    times = []
+    for k in range(reps + 1):
+        t0 = time.perf_counter()
+        m = cv.master_build(files)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        info = m.info()
+        m.close()
+        if k:
+            times.append(dt)
+    best = min(times)
+    return {"workload": f"sweep master set: {M} sectors in {file_nsect.size} device-resident files", "build_s": times,
+            "sectors_per_s": M / best, "master_GBps": M * SECTOR / best / 1e9, "n_slots": info["n_slots"],
+            "max_probe": info["max_probe"]}
+
+
 def run_sweep(torch, cv, synth, stream, steps, sizes=(10**3, 10**5, 10**6, 10**7, 5 * 10**7),
               densities=(1e-4, 1e-2, 1e-1)):
     """Table-scaling sweep: an 8 GiB image (16,777,216 sectors, seed 3) against master sets of
@@ -619,6 +646,8 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=5)
     ap.add_argument("--sweep-only", action="store_true", help="run only the table-scaling sweep and print its JSON")
+    ap.add_argument("--build-only", type=int, default=0, metavar="M",
+                    help="time only table builds of the sweep's master set of M sectors and print their JSON")
     ap.add_argument("--frag-steps", type=int, default=10)
     ap.add_argument("--frag-cpu-mib", type=int, default=256)
     ap.add_argument("--frag-only", action="store_true",
@@ -653,6 +682,16 @@ def main():
 
         host = torch.empty(32 << 30, dtype=torch.uint8, pin_memory=True)
         print(json.dumps(run_served(torch, cv, synth, args, host)))
+        return 0
+    if args.build_only:
+        import torch
+
+        import __graft_entry__
+
+        __graft_entry__.build()
+        from paper_0901_1307_gb300 import cv, synth
+
+        print(json.dumps(run_build(torch, cv, synth, args.build_only)))
         return 0
     if args.sweep_only:
         import torch

@@ -28,11 +28,16 @@ namespace {
 int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint64_t n, int bits, Temps& tmp,
                      cudaStream_t stream, uint32_t** kres, uint32_t** vres) {
   const uint32_t nb = (uint32_t)((n + kRsChunk - 1) / kRsChunk);
-  uint32_t* hist;
-  CV_TRY(tmp.alloc(&hist, (uint64_t)std::max<uint32_t>(nb, 1) * 256 * 4));
+  const uint64_t nh = (uint64_t)std::max<uint32_t>(nb, 1) * 256;
+  const uint32_t nc = (uint32_t)((nh + kScanChunk - 1) / kScanChunk);
+  uint32_t *hist, *sums;
+  CV_TRY(tmp.alloc(&hist, nh * 4));
+  CV_TRY(tmp.alloc(&sums, (uint64_t)nc * 4));
   for (int shift = 0; shift < bits && n; shift += 8) {
     rs_hist_kernel<<<nb, kRsThreads, 0, stream>>>(k0, n, shift, hist, nb);
-    exclusive_scan_u32_kernel<<<1, 1024, 0, stream>>>(hist, (uint64_t)nb * 256);
+    scan_chunk_sums_u32_kernel<<<nc, kScanThreads, 0, stream>>>(hist, (uint64_t)nb * 256, sums);
+    scan_sums_u32_kernel<<<1, 1024, 0, stream>>>(sums, nc);
+    scan_chunks_u32_kernel<<<nc, kScanThreads, 0, stream>>>(hist, (uint64_t)nb * 256, sums);
     rs_scatter_kernel<<<nb, kRsThreads, 0, stream>>>(k0, v0, k1, v1, n, shift, hist, nb);
     CV_CUDA(cudaGetLastError());
     std::swap(k0, k1);

@@ -43,6 +43,7 @@ __global__ void insert_kernel(const uint4* dig, const uint8_t* trivial, const ui
                               uint32_t* owner, uint32_t* cnt, uint32_t* slot_of, uint32_t mask, uint32_t* max_disp,
                               uint32_t* n_kept, uint32_t* status) {
   const uint32_t none = mask + 1u;
+  uint32_t kept = 0, longest = 0;  // this thread's, added to the shared counters once per warp
   for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < n; m += (uint64_t)gridDim.x * blockDim.x) {
     if (trivial[m]) {
       slot_of[m] = none;
@@ -74,8 +75,15 @@ __global__ void insert_kernel(const uint4* dig, const uint8_t* trivial, const ui
     }
     slot_of[m] = idx;
     atomicAdd(cnt + idx, 1u);
-    atomicMax(max_disp, c);
-    atomicAdd(n_kept, 1u);
+    longest = c > longest ? c : longest;
+    kept++;
+  }
+  // one update per warp: a per-key atomic on one address serialises the whole build
+  kept = __reduce_add_sync(0xFFFFFFFFu, kept);
+  longest = __reduce_max_sync(0xFFFFFFFFu, longest);
+  if ((threadIdx.x & 31) == 0 && kept) {
+    atomicAdd(n_kept, kept);
+    atomicMax(max_disp, longest);
   }
 }
 
@@ -104,38 +112,104 @@ __global__ void __launch_bounds__(kRsThreads) rs_hist_kernel(const uint32_t* key
   hist[(uint64_t)threadIdx.x * n_blocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// In-place exclusive scan of n u32 values whose total fits in 32 bits (one block).
-__global__ void __launch_bounds__(1024) exclusive_scan_u32_kernel(uint32_t* v, uint64_t n) {
-  __shared__ uint32_t warp_sum[32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint64_t per = (n + 1023) / 1024;
-  const uint64_t lo = per * tid < n ? per * tid : n;
-  const uint64_t hi = lo + per < n ? lo + per : n;
-  uint32_t sum = 0;
-  for (uint64_t i = lo; i < hi; i++) sum += v[i];
-  uint32_t incl = sum;
+// In-place exclusive scan of n u32 values whose total fits in 32 bits, over the whole GPU in
+// three launches: the sum of every 4096-value chunk; an exclusive scan of those sums (one
+// block); each chunk's own scan, offset by its sum's prefix. Loads and stores are coalesced;
+// the per-thread runs are read from a padded shared tile without bank conflicts.
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr uint32_t kScanChunk = kScanThreads * kScanItems;
+
+// Exclusive scan of x over the B threads of a block; *total gets the sum (every thread).
+template <int B>
+__device__ __forceinline__ uint32_t block_exclusive_u32(uint32_t x, uint32_t* total) {
+  __shared__ uint32_t ws[B / 32 + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = x;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    uint32_t x = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-    if (lane >= d) incl += x;
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if (lane >= d) incl += y;
   }
-  if (lane == 31) warp_sum[warp] = incl;
+  if (lane == 31) ws[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    uint32_t w = warp_sum[lane], wi = w;
+    const uint32_t w = lane < B / 32 ? ws[lane] : 0u;
+    uint32_t wi = w;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      uint32_t x = __shfl_up_sync(0xFFFFFFFFu, wi, d);
-      if (lane >= d) wi += x;
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, d);
+      if (lane >= d) wi += y;
     }
-    warp_sum[lane] = wi - w;
+    if (lane < B / 32) ws[lane] = wi - w;
+    if (lane == B / 32 - 1) ws[B / 32] = wi;
   }
   __syncthreads();
-  uint32_t run = warp_sum[warp] + incl - sum;
-  for (uint64_t i = lo; i < hi; i++) {
-    const uint32_t x = v[i];
-    v[i] = run;
-    run += x;
+  const uint32_t r = ws[warp] + incl - x;
+  *total = ws[B / 32];
+  __syncthreads();  // ws may be reused by the next call
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_chunk_sums_u32_kernel(const uint32_t* v, uint64_t n,
+                                                                           uint32_t* sums) {
+  const uint64_t base = (uint64_t)blockIdx.x * kScanChunk;
+  uint32_t s = 0;
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++) {
+    const uint64_t i = base + (uint64_t)r * kScanThreads + threadIdx.x;
+    if (i < n) s += v[i];
+  }
+  uint32_t total;
+  block_exclusive_u32<kScanThreads>(s, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) scan_sums_u32_kernel(uint32_t* sums, uint32_t nb) {
+  uint32_t carry = 0;
+  for (uint32_t t0 = 0; t0 < nb; t0 += 1024) {
+    const uint32_t i = t0 + threadIdx.x;
+    const uint32_t x = i < nb ? sums[i] : 0u;
+    uint32_t total;
+    const uint32_t e = block_exclusive_u32<1024>(x, &total);
+    if (i < nb) sums[i] = carry + e;
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_chunks_u32_kernel(uint32_t* v, uint64_t n, const uint32_t* sums) {
+  __shared__ uint32_t tile[kScanChunk + kScanChunk / 32];  // element e at e + e / 32
+  const uint64_t base = (uint64_t)blockIdx.x * kScanChunk;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++) {
+    const uint32_t e = r * kScanThreads + tid;
+    const uint64_t i = base + e;
+    tile[e + e / 32] = i < n ? v[i] : 0u;
+  }
+  __syncthreads();
+  uint32_t loc[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; j++) {
+    const uint32_t e = tid * kScanItems + j;
+    loc[j] = tile[e + e / 32];
+    s += loc[j];
+  }
+  uint32_t total;
+  uint32_t run = block_exclusive_u32<kScanThreads>(s, &total) + sums[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < kScanItems; j++) {
+    const uint32_t e = tid * kScanItems + j;
+    tile[e + e / 32] = run;
+    run += loc[j];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++) {
+    const uint32_t e = r * kScanThreads + tid;
+    const uint64_t i = base + e;
+    if (i < n) v[i] = tile[e + e / 32];
   }
 }
 
@@ -185,6 +259,7 @@ __global__ void fill_kernel(const uint32_t* keys, const uint32_t* vals, uint64_t
                             const uint32_t* owner, const uint32_t* cnt, const uint4* dig, const uint8_t* tau,
                             const uint64_t* file_base, uint32_t n_files, uint4* slots, uint2* postings,
                             uint32_t* n_unique) {
+  uint32_t uniq = 0;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t key = keys[q];
     if (key >= n_slots) continue;
@@ -199,9 +274,11 @@ __global__ void fill_kernel(const uint32_t* keys, const uint32_t* vals, uint64_t
       const uint32_t o = owner[key] - 1u;
       slots[2ull * key] = dig[o];
       slots[2ull * key + 1] = make_uint4((uint32_t)q, cnt[key], tau ? (uint32_t)tau[o] : 0u, 0u);
-      atomicAdd(n_unique, 1u);
+      uniq++;
     }
   }
+  uniq = __reduce_add_sync(0xFFFFFFFFu, uniq);
+  if ((threadIdx.x & 31) == 0 && uniq) atomicAdd(n_unique, uniq);
 }
 
 // Kept master units (sectors or fragments of wpu 16-byte words) in posting order: posting q
