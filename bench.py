@@ -137,8 +137,7 @@ def setup_workload(torch, cv, synth, name: str, seed_offset: int):
     masters = torch.empty(plan.n_master_sectors * SECTOR, dtype=torch.uint8, device="cuda")
     plan.masters_device(masters.data_ptr(), base_d.data_ptr())
     torch.cuda.synchronize()
-    files = [(masters.data_ptr() + int(base[f]) * SECTOR, int(plan.file_nsect[f]) * SECTOR)
-             for f in range(plan.n_files)]
+    files = file_descriptors(masters.data_ptr(), base, plan.file_nsect)
     t0 = time.perf_counter()
     master = cv.master_build(files)
     build_s = time.perf_counter() - t0
@@ -225,6 +224,12 @@ def device_plan(torch, synth, plan):
     return tuple(k.data_ptr() for k in keep), keep
 
 
+def file_descriptors(ptr, base, file_nsect):
+    """(pointer, bytes) rows of files laid out from ptr at sector offsets base (a cv_buf array)."""
+    n = file_nsect.size
+    return np.stack([ptr + base[:n].astype(np.uint64) * SECTOR, file_nsect.astype(np.uint64) * SECTOR], axis=1)
+
+
 def build_master_set(torch, cv, synth, name):
     """The named master set generated on the device and built into a table."""
     file_nsect, mseed = synth.master_set(name)
@@ -234,7 +239,7 @@ def build_master_set(torch, cv, synth, name):
     masters = torch.empty(mplan.n_master_sectors * SECTOR, dtype=torch.uint8, device="cuda")
     mplan.masters_device(masters.data_ptr(), base_d.data_ptr())
     torch.cuda.synchronize()
-    files = [(masters.data_ptr() + int(base[f]) * SECTOR, int(file_nsect[f]) * SECTOR) for f in range(file_nsect.size)]
+    files = file_descriptors(masters.data_ptr(), base, file_nsect)
     t0 = time.perf_counter()
     m = cv.master_build(files)
     build_s = time.perf_counter() - t0
@@ -283,8 +288,7 @@ def device_masters(torch, plan):
     masters = torch.empty(plan.n_master_sectors * SECTOR, dtype=torch.uint8, device="cuda")
     plan.masters_device(masters.data_ptr(), base_d.data_ptr())
     torch.cuda.synchronize()
-    files = [(masters.data_ptr() + int(base[f]) * SECTOR, int(plan.file_nsect[f]) * SECTOR)
-             for f in range(plan.n_files)]
+    files = file_descriptors(masters.data_ptr(), base, plan.file_nsect)
     return masters, files
 
 
@@ -362,7 +366,7 @@ def run_build(torch, cv, synth, M, reps=3):
     masters = torch.empty(M * SECTOR, dtype=torch.uint8, device="cuda")
     mplan.masters_device(masters.data_ptr(), base_d.data_ptr())
     torch.cuda.synchronize()
-    files = [(masters.data_ptr() + int(base[f]) * SECTOR, int(file_nsect[f]) * SECTOR) for f in range(file_nsect.size)]
+    files = file_descriptors(masters.data_ptr(), base, file_nsect)
     times = []
     for k in range(reps + 1):
         t0 = time.perf_counter()
@@ -396,8 +400,7 @@ def run_sweep(torch, cv, synth, stream, steps, sizes=(10**3, 10**5, 10**6, 10**7
         masters = torch.empty(M * SECTOR, dtype=torch.uint8, device="cuda")
         mplan.masters_device(masters.data_ptr(), base_d.data_ptr())
         torch.cuda.synchronize()
-        files = [(masters.data_ptr() + int(base[f]) * SECTOR, int(file_nsect[f]) * SECTOR)
-                 for f in range(file_nsect.size)]
+        files = file_descriptors(masters.data_ptr(), base, file_nsect)
         t0 = time.perf_counter()
         tables = {"bloom": cv.master_build(files)}
         build_s = time.perf_counter() - t0

@@ -231,6 +231,20 @@ def _buf(x):
 
 
 def _bufs(xs):
+    """A cv_buf array for a list of buffers. An (n, 2) uint64 array of (pointer, bytes) rows is
+    passed as it is (it has cv_buf's layout), and a list made only of (pointer, bytes) tuples is
+    converted in one step: with hundreds of thousands of master files the element-by-element
+    path costs more than the build itself."""
+    if isinstance(xs, np.ndarray):
+        a = np.ascontiguousarray(xs, dtype=np.uint64)
+        if a.ndim != 2 or a.shape[1] != 2:
+            raise ValueError("a buffer descriptor array has shape (n, 2): pointer, bytes")
+        return a.ctypes.data_as(ctypes.POINTER(cv_buf)), [a]
+    if xs and all(type(x) is tuple for x in xs):
+        a = np.array(xs, dtype=np.uint64)
+        if a.ndim != 2 or a.shape[1] != 2:
+            raise ValueError("buffer tuples are (pointer, bytes)")
+        return a.ctypes.data_as(ctypes.POINTER(cv_buf)), [a]
     keep = []
     arr = (cv_buf * max(1, len(xs)))()
     for i, x in enumerate(xs):
@@ -344,8 +358,11 @@ def master_build(files, max_load: float = 0.0, bloom_bits_per_key: int = CV_BLOO
     positions, or with position_mode=CV_POSITION_CLUSTER the tables S_tau of Section 3.1), as a
     linear-probing hash table or (layout=CV_LAYOUT_SORTED) a sorted array searched by bisection.
     unit=CV_UNIT_FRAGMENT cuts the files into 64-byte fragments instead of 512-byte sectors, and
-    scans then look up every 64-byte window at a 4-byte offset (Section 5)."""
-    arr, keep = _bufs(list(files))
+    scans then look up every 64-byte window at a 4-byte offset (Section 5). files: a list of
+    buffers (arrays, tensors, (pointer, bytes) tuples) or an (n, 2) uint64 array of
+    (pointer, bytes) rows."""
+    files = files if isinstance(files, np.ndarray) else list(files)
+    arr, keep = _bufs(files)
     o = cv_master_opts(ctypes.sizeof(cv_master_opts), max_load, bloom_bits_per_key, signature, _stream(stream),
                        position_mode, layout, unit, 0)
     h = ctypes.c_void_p()

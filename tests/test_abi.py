@@ -134,3 +134,32 @@ def test_cli_builds_and_refuses_without_gpu(lib, tmp_path):
         pytest.skip("a GPU is present")
     r = subprocess.run([exe, str(img), "--", str(img)], capture_output=True, text=True)
     assert r.returncode == 2 and "no usable CUDA device" in r.stderr
+
+
+def test_buffer_lists_marshal_to_cv_buf_arrays():
+    """The binding's three ways of passing buffer lists give the same cv_buf array: elements one
+    by one, (pointer, bytes) tuples converted at once, and an (n, 2) uint64 descriptor array."""
+    import ctypes
+
+    import numpy as np
+
+    from paper_0901_1307_gb300 import cv
+
+    a = np.arange(3000, dtype=np.uint8)
+    b = np.zeros(0, np.uint8)
+    rows = [(a.ctypes.data, a.nbytes), (0, 0), (a.ctypes.data + 512, 1024)]
+
+    def as_pairs(arr, n):
+        return [(arr[i].data or 0, arr[i].n_bytes) for i in range(n)]
+
+    one_by_one, keep1 = cv._bufs([a, b, (a.ctypes.data + 512, 1024)])
+    tuples, keep2 = cv._bufs(rows)
+    desc, keep3 = cv._bufs(np.array(rows, dtype=np.uint64))
+    assert ctypes.sizeof(cv.cv_buf) == 16
+    assert as_pairs(one_by_one, 3)[0] == rows[0] and as_pairs(one_by_one, 3)[2] == rows[2]
+    assert as_pairs(tuples, 3) == rows == as_pairs(desc, 3)
+    for bad in (np.zeros((3, 3), np.uint64), np.zeros(4, np.uint64)):
+        with pytest.raises(ValueError):
+            cv._bufs(bad)
+    with pytest.raises(ValueError):
+        cv._bufs([(1, 2, 3), (4, 5, 6)])
