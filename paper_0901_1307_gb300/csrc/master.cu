@@ -94,8 +94,12 @@ int launch_gather(const std::vector<CopyPiece>& pieces, uint8_t* dst_base, int s
 // copied to the device in one call per chunk and scattered by a gather launch; anything else
 // (managed memory, another GPU's) by the driver. Memory is classified once per CUDA allocation
 // (cuMemGetAddressRange), not once per file.
+//
+// *units receives where the build reads the units from: the arena (allocated here), or, when
+// every unit already lies in one 16-byte-aligned run of this GPU's memory in file order, that
+// memory itself, with no copy and no arena.
 int gather_master_units(DevCtx* ctx, const cv_buf* files, uint32_t n_files, const std::vector<uint64_t>& file_base,
-                        uint64_t U, uint8_t* arena, Temps& tmp, cudaStream_t stream) {
+                        uint64_t U, Temps& tmp, cudaStream_t stream, const uint8_t** units) {
   std::vector<CopyPiece> runs;
   for (uint32_t f = 0; f < n_files; f++) {
     const uint64_t bytes = (file_base[f + 1] - file_base[f]) * U;
@@ -107,6 +111,29 @@ int gather_master_units(DevCtx* ctx, const cv_buf* files, uint32_t n_files, cons
     else
       runs.push_back(CopyPiece{src, dst, bytes});
   }
+  const uint64_t total_bytes = file_base[n_files] * U;
+  *units = nullptr;
+  if (total_bytes == 0) return CV_OK;
+  if (runs.size() == 1 && runs[0].dst == 0 && runs[0].bytes == total_bytes && ((uintptr_t)runs[0].src & 15u) == 0) {
+    CUdeviceptr ab = 0;
+    size_t asz = 0;
+    cudaPointerAttributes at;
+    const uintptr_t a = (uintptr_t)runs[0].src;
+    if (ctx->address_range && ctx->address_range(&ab, &asz, (CUdeviceptr)a) == CUDA_SUCCESS &&
+        a + total_bytes <= (uintptr_t)ab + asz) {
+      if (cudaPointerGetAttributes(&at, runs[0].src) == cudaSuccess) {
+        if (at.type == cudaMemoryTypeDevice && at.device == ctx->dev) {
+          *units = runs[0].src;
+          return CV_OK;
+        }
+      } else {
+        cudaGetLastError();
+      }
+    }
+  }
+  uint8_t* arena;
+  CV_TRY(tmp.alloc(&arena, total_bytes));
+  *units = arena;
   // Where a run lives: this GPU's memory (gathered by a kernel), host memory the CPU may read
   // (pageable, pinned or registered: staged, or copied by the driver when long), or anything
   // else (managed memory, another GPU's memory: copied by the driver).
@@ -240,12 +267,11 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       const uint64_t n_slots = std::max<uint64_t>(next_pow2((uint64_t)((double)M / max_load) + 1), 2);
       if (n_slots > (1ull << 31)) return CV_EINVAL;
       const uint32_t mask = (uint32_t)(n_slots - 1);
-      uint8_t* arena;
+      const uint8_t* arena;  // the master units, back to back in file order (device memory)
       uint4* dig;
       uint8_t* trivial;
       uint32_t *owner, *cnt, *slot_of, *keys2, *vals, *vals2, *counters;
       uint64_t* file_base_d;
-      CV_TRY(tmp.alloc(&arena, M * U));
       CV_TRY(tmp.alloc(&dig, M * sizeof(uint4)));
       CV_TRY(tmp.alloc(&trivial, M));
       CV_TRY(tmp.alloc(&owner, n_slots * 4));
@@ -262,7 +288,7 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
       CV_CUDA(cudaMemsetAsync(cnt, 0, n_slots * 4, stream));
       CV_CUDA(cudaMemsetAsync(counters, 0, 16, stream));
       CV_CUDA(cudaMemcpyAsync(file_base_d, file_base.data(), (n_files + 1) * 8, cudaMemcpyHostToDevice, stream));
-      CV_TRY(gather_master_units(ctx, files, n_files, file_base, U, arena, tmp, stream));
+      CV_TRY(gather_master_units(ctx, files, n_files, file_base, U, tmp, stream, &arena));
       // long-lived table memory
       CV_CUDA(cudaMalloc(&m->slots, n_slots * 32));
       CV_CUDA(cudaMalloc(&m->postings, std::max<uint64_t>(M, 1) * 8));
