@@ -4,11 +4,10 @@
 // its remark that probing costs more at high occupancy). The scan kernel does not count its
 // reads, since a counter there would cost every scan; this entry point replays the same
 // lookups outside it. It computes the key words of every sector with the scan's own digest
-// pass, then a counting kernel repeats the scan's lookup for each sector: the Bloom test
-// (when the table has a filter), then either the linear-probing walk from the home slot of
-// Eq. 3 (hash layout) or the bisection over the sorted keys and the comparison of the records
-// that share the key word (sorted layout), in the same order and with the same bound as the
-// scan kernel's, adding up what it reads.
+// pass, then a counting kernel runs the scan's own lookup functions for each sector with a
+// counter attached: the Bloom test (when the table has a filter), then either the
+// linear-probing walk from the home slot of Eq. 3 (hash layout) or the bisection over the
+// sorted keys and the comparison of the records that share the key word (sorted layout).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -25,55 +24,29 @@ namespace {
 
 constexpr uint64_t kProfileChunk = 1ull << 22;  // sectors per digest pass (64 MiB of key words)
 
+// Adds up the reads of the scan's own probe loops (table_probe, sorted_probe).
+struct ProbeCount {
+  uint64_t* slots;
+  uint64_t* keys;
+  __device__ __forceinline__ void slot() const { ++*slots; }
+  __device__ __forceinline__ void key() const { ++*keys; }
+};
+
 // acc: [0] sectors past the Bloom filter, [1] slot records read, [2] sorted keys read,
 // [3] sectors whose key is in the table.
 __global__ void probe_profile_kernel(const uint4* dig, uint64_t n, uint64_t sector0, TableView tab,
                                      unsigned long long* acc) {
   uint64_t passed = 0, slots = 0, keys = 0, found = 0;
+  const ProbeCount cnt{&slots, &keys};
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint4 d = dig[i];
     const uint32_t tau = (uint32_t)((sector0 + i + tab.tau_add) & tab.tau_mask);
     if (tab.use_bloom && !bloom_test(tab, d.y, d.z, d.w, tau)) continue;
     passed++;
-    if (tab.layout == kLayoutSorted) {
-      // sorted_probe, counted
-      const uint32_t h0 = tau_home(d.x, tau);
-      uint32_t m = tab.n_keys, base = 0;
-      if (m == 0u) continue;
-      while (m > 1u) {
-        const uint32_t half = m >> 1;
-        keys++;
-        base = tab.keys0[base + half] < h0 ? base + half : base;
-        m -= half;
-      }
-      keys++;
-      uint32_t j = base + (tab.keys0[base] < h0 ? 1u : 0u);
-      for (; j < tab.n_keys; j++) {
-        keys++;
-        if (tab.keys0[j] != h0) break;
-        slots++;
-        const uint4 key = tab.slots[2ull * j];
-        const uint4 val = tab.slots[2ull * j + 1];
-        if (key.x == d.x && key.y == d.y && key.z == d.z && key.w == d.w && val.z == tau) {
-          found++;
-          break;
-        }
-      }
-    } else {
-      // table_probe, counted
-      uint32_t idx = tau_home(d.x, tau) & tab.slot_mask;
-      for (uint32_t c = 0; c < tab.max_probe; c++) {
-        slots++;
-        const uint4 key = tab.slots[2ull * idx];
-        const uint4 val = tab.slots[2ull * idx + 1];
-        if (val.y == 0u) break;
-        if (key.x == d.x && key.y == d.y && key.z == d.z && key.w == d.w && val.z == tau) {
-          found++;
-          break;
-        }
-        idx = (idx + 1u) & tab.slot_mask;
-      }
-    }
+    uint32_t post_off = 0;
+    const uint32_t c = tab.layout == kLayoutSorted ? sorted_probe(tab, d.x, d.y, d.z, d.w, tau, post_off, cnt)
+                                                   : table_probe(tab, d.x, d.y, d.z, d.w, tau, post_off, cnt);
+    if (c) found++;
   }
   uint64_t v[4] = {passed, slots, keys, found};
 #pragma unroll

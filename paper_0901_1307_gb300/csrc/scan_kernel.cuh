@@ -108,12 +108,22 @@ __device__ __forceinline__ bool bloom_test(const TableView& tab, uint32_t d1, ui
   return (m & 1u) != 0;
 }
 
+// What a lookup reads from the table: a slot record (32 bytes) or a sorted key word (4 bytes).
+// The scan passes this no-op counter; cv_probe_profile passes one that adds them up, so its
+// counts are those of the very loops below.
+struct ProbeNoCount {
+  __device__ __forceinline__ void slot() const {}
+  __device__ __forceinline__ void key() const {}
+};
+
 // Linear probing from the home slot (Eq. 3) until the key (digest, tau) or an empty slot is
 // found, never beyond the table's probe bound. Returns post_cnt (0: not present) and post_off.
+template <class Count = ProbeNoCount>
 __device__ __forceinline__ uint32_t table_probe(const TableView& tab, uint32_t d0, uint32_t d1, uint32_t d2,
-                                                uint32_t d3, uint32_t tau, uint32_t& post_off) {
+                                                uint32_t d3, uint32_t tau, uint32_t& post_off, Count cnt = Count()) {
   uint32_t idx = tau_home(d0, tau) & tab.slot_mask;
   for (uint32_t c = 0; c < tab.max_probe; c++) {
+    cnt.slot();
     const uint4* s = tab.slots + 2ull * idx;
     uint4 key = __ldg(s);
     uint4 val = __ldg(s + 1);
@@ -130,8 +140,9 @@ __device__ __forceinline__ uint32_t table_probe(const TableView& tab, uint32_t d
 // Sorted layout: branch-free lower bound of h0 = tau_home(d0, tau) in keys0 (ceil(log2 n_keys)
 // dependent loads; the first levels are shared by every thread and stay in L1), then the
 // records with that h0 are compared in full. Returns post_cnt (0: not present) and post_off.
+template <class Count = ProbeNoCount>
 __device__ __forceinline__ uint32_t sorted_probe(const TableView& tab, uint32_t d0, uint32_t d1, uint32_t d2,
-                                                 uint32_t d3, uint32_t tau, uint32_t& post_off) {
+                                                 uint32_t d3, uint32_t tau, uint32_t& post_off, Count cnt = Count()) {
   const uint32_t h0 = tau_home(d0, tau);
   const uint32_t* k = tab.keys0;
   uint32_t n = tab.n_keys;
@@ -139,10 +150,14 @@ __device__ __forceinline__ uint32_t sorted_probe(const TableView& tab, uint32_t 
   uint32_t base = 0;
   while (n > 1u) {
     const uint32_t half = n >> 1;
+    cnt.key();
     base = __ldg(k + base + half) < h0 ? base + half : base;
     n -= half;
   }
-  for (uint32_t i = base + (__ldg(k + base) < h0 ? 1u : 0u); i < tab.n_keys && __ldg(k + i) == h0; i++) {
+  cnt.key();
+  for (uint32_t i = base + (__ldg(k + base) < h0 ? 1u : 0u); i < tab.n_keys && (cnt.key(), __ldg(k + i) == h0);
+       i++) {
+    cnt.slot();
     const uint4* s = tab.slots + 2ull * i;
     const uint4 key = __ldg(s);
     const uint4 val = __ldg(s + 1);
