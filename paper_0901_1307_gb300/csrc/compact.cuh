@@ -124,32 +124,41 @@ __global__ void expand_kernel(const uint4* hit_rec, const uint32_t* tile_nhit, c
   constexpr uint32_t kW = T / 32;
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t u = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < n_out_tiles; u += warps) {
-    const uint32_t n = tile_nhit[u];
-    if (n == 0) continue;
-    const uint64_t ctile = u / kW;
-    const uint32_t sg = find_segment(segs, n_segs, ctile);
-    const uint64_t row_first = (ctile - segs[sg].tile_base) * T + (u % kW) * 32;  // within the segment
-    const uint64_t first_sector = segs[sg].sector_base + row_first;
-    uint4 rec = make_uint4(0, 0, 0, 0);
-    if ((uint32_t)lane < n) rec = hit_rec[u * 32 + lane];
-    uint32_t incl = rec.w;
+  // A warp reads the hit counts of 32 output tiles at once and expands only those with hits:
+  // most tiles have none, and one dependent count load per tile made the pass latency-bound.
+  for (uint64_t u0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; u0 < n_out_tiles;
+       u0 += warps * 32) {
+    const uint32_t mine_n = u0 + lane < n_out_tiles ? tile_nhit[u0 + lane] : 0u;
+    uint32_t busy = __ballot_sync(0xFFFFFFFFu, mine_n != 0u);
+    while (busy) {
+      const int b = __ffs(busy) - 1;
+      busy &= busy - 1;
+      const uint64_t u = u0 + (uint64_t)b;
+      const uint32_t n = __shfl_sync(0xFFFFFFFFu, mine_n, b);
+      const uint64_t ctile = u / kW;
+      const uint32_t sg = find_segment(segs, n_segs, ctile);
+      const uint64_t row_first = (ctile - segs[sg].tile_base) * T + (u % kW) * 32;  // within the segment
+      const uint64_t first_sector = segs[sg].sector_base + row_first;
+      uint4 rec = make_uint4(0, 0, 0, 0);
+      if ((uint32_t)lane < n) rec = hit_rec[u * 32 + lane];
+      uint32_t incl = rec.w;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-      if (lane >= d) incl += v;
-    }
-    uint64_t o = tile_off[u] + (incl - rec.w);
-    const uint8_t* mine = confirm ? segs[sg].bytes + (row_first + rec.x) * kSector : nullptr;
-    for (uint32_t k = 0; k < rec.z; k++) {
-      if (confirm && !sectors_equal(mine, confirm + (uint64_t)(rec.y + k) * kSector)) continue;
-      if (o < out_cap) {
-        const uint2 pf = postings[rec.y + k];
-        out[o] = MatchOut{first_sector + rec.x, pf.x, pf.y};
-      } else {
-        atomicOr(status, kStOverflow);
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += v;
       }
-      o++;
+      uint64_t o = tile_off[u] + (incl - rec.w);
+      const uint8_t* mine = confirm ? segs[sg].bytes + (row_first + rec.x) * kSector : nullptr;
+      for (uint32_t k = 0; k < rec.z; k++) {
+        if (confirm && !sectors_equal(mine, confirm + (uint64_t)(rec.y + k) * kSector)) continue;
+        if (o < out_cap) {
+          const uint2 pf = postings[rec.y + k];
+          out[o] = MatchOut{first_sector + rec.x, pf.x, pf.y};
+        } else {
+          atomicOr(status, kStOverflow);
+        }
+        o++;
+      }
     }
   }
 }
