@@ -352,8 +352,9 @@ def run_tables(torch, cv, synth, plan, image, stream, steps):
 
 
 # DRAM bytes (read + write) per launch of the default scan kernel, from one ncu capture of the
-# current kernel: 4.436 GB on the 4 GiB mid workload (8,388,608 sectors), scaled by sectors.
-SCAN_TRAFFIC_BYTES = {"mid": 4.4360e9, "scale": 8 * 4.4360e9}
+# current kernel: 4.427 GB on the 4 GiB mid workload (8,388,608 sectors; the mean of four
+# launches), scaled by sectors.
+SCAN_TRAFFIC_BYTES = {"mid": 4.4274e9, "scale": 8 * 4.4274e9}
 
 
 def run_build(torch, cv, synth, M, reps=3):
@@ -863,7 +864,7 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Top/s",
                      "frac": achieved_ops / peak_ops,
                      "traffic": SCAN_TRAFFIC_BYTES.get(args.config) if args.kernel_config == 0 else None,
-                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch: 4.436 GB measured "
+                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch: 4.427 GB measured "
                                      "on the 4 GiB mid workload, x8 by sectors for the 32 GiB image",
                      "kernel": "scan_kernel (MD5 + Bloom + probe + tile compaction)",
                      "kernel_ms": kms, "kernel_GBps": nbytes / (kms * 1e-3) / 1e9,
