@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 from paper_0901_1307_gb300 import synth
+from probe_model import linear_probing_model, miss_reads
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -36,32 +37,6 @@ def cv(cuda_device):
 def d0_of(sector: bytes) -> int:
     """Word 0 of the MD5 digest (bytes 0-3, little-endian): the home-slot key of Eq. 3."""
     return struct.unpack("<I", hashlib.md5(sector).digest()[:4])[0]
-
-
-def linear_probing_model(homes, n_slots):
-    """Occupied slots and total displacement of linear probing over the given home slots,
-    inserted in list order (both are the same for every order), and the longest displacement
-    (which is not)."""
-    occ = np.zeros(n_slots, bool)
-    total = 0
-    longest = 0
-    for h in homes:
-        i, d = h, 0
-        while occ[i]:
-            i = (i + 1) % n_slots
-            d += 1
-        occ[i] = True
-        total += d + 1
-        longest = max(longest, d)
-    return occ, total, longest
-
-
-def miss_reads(occ, home, bound):
-    n = occ.size
-    run = 0
-    while run < n and occ[(home + run) % n]:
-        run += 1
-    return min(run + 1, bound)
 
 
 def sectors_of(a: np.ndarray):
