@@ -50,6 +50,10 @@ def test_strerror_and_null_arguments(lib):
     assert lib.cv_master_build(None, 1, None, ctypes.byref(out)) == cv.CV_EINVAL
     assert lib.cv_scan(None, None, 0, None, ctypes.byref(out)) == cv.CV_EINVAL
     assert lib.cv_matches(None, 0, None, None) == cv.CV_EINVAL
+    st = cv.cv_probe_stats()
+    st.struct_size = ctypes.sizeof(st)
+    assert lib.cv_probe_profile(None, None, 0, 0, ctypes.byref(st), None) == cv.CV_EINVAL
+    assert lib.cv_probe_profile(None, None, 0, 0, None, None) == cv.CV_EINVAL
     lib.cv_free(None)
 
 
