@@ -360,10 +360,11 @@ typedef struct {
   uint64_t work_unit_bytes;  /* request data per work unit (multiple of 512); 0 = 64 MiB */
   uint32_t kernel_config;    /* 0 = default; k + 1 = configuration k */
   uint32_t copy_streams;     /* host-to-device copy streams; 0 = 2 */
-  uint64_t max_copy_bytes;   /* request data queued on the copy streams at once (more is issued as
-                                copies land, so later requests are not stuck behind a large one);
-                                0 = 2 GiB, UINT64_MAX = no limit. The size without this field (32
-                                bytes) is accepted and means 0. */
+  uint64_t max_copy_bytes;   /* request data queued on the copy streams at once, at least one work
+                                unit; more is issued as copies land, first to the live request with
+                                the fewest bytes left, so a small request is not stuck behind a
+                                large one's copies. 0 = 2 GiB, UINT64_MAX = no limit. The size
+                                without this field (32 bytes) is accepted and means 0. */
 } cv_server_opts;
 
 typedef struct {
