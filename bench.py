@@ -202,7 +202,7 @@ def run_reference(args):
             times.append(dt)
     tot = sum(times)
     v = args.steps * n * SECTOR / tot / 1e9
-    line = {"metric": "disk-image GB/s scanned", "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+    line = {"metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "impl": "reference",
@@ -628,6 +628,91 @@ def run_served(torch, cv, synth, args, host):
             "bit_exact_vs_plant_log": bool(exact)}
 
 
+METRIC = "disk-image GB/s scanned on 1 GB300 (% of hash/HBM roofline); p99 scan latency served"
+
+
+def emit_section(args, name, obj):
+    """One section of the results as its own JSON line on stdout (rank 0), ahead of the headline
+    line, which comes last and stays short; also appended to --sections-out when given."""
+    if int(os.environ.get("RANK", "0")) != 0 or obj is None:
+        return
+    text = json.dumps({"section": name, **obj}, separators=(",", ":"))
+    print(text, flush=True)
+    if args.sections_out:
+        with open(args.sections_out, "a") as fh:
+            fh.write(text + "\n")
+
+
+def scan_roofline(kms, sectors, hit_sectors, clocks, int_peak, args):
+    """The scan kernel against the lower of its two ceilings.
+
+    Algorithmic bytes per launch: the image read once (512 B per sector), one 16-byte hit record
+    per sector with a match, and the per-tile counts (4 + 8 B per 32-sector output tile). The
+    integer ceiling is 152 SMs x 128 lanes x the sampled SM clock, at 2,852 algorithmic MD5 ops
+    per sector (5.57 per byte); the HBM ceiling is the measured copy bandwidth. The lower one is
+    the bound reported."""
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    hbm = measured_peaks().get("hbm_gbs")
+    hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)"
+    if not hbm:
+        hbm, hbm_src = 6800.0, "fallback"
+    peak_ops = SM_COUNT * INT_LANES_PER_SM_CLK * sm_mhz * 1e6
+    int_roof_gbs = peak_ops / (MD5_OPS_PER_SECTOR / SECTOR) / 1e9
+    alg_bytes = sectors * SECTOR + hit_sectors * 16 + (sectors + 31) // 32 * 12
+    achieved_gbs = alg_bytes / (kms * 1e-3) / 1e9
+    achieved_ops = sectors * MD5_OPS_PER_SECTOR / (kms * 1e-3)
+    traffic = SCAN_TRAFFIC_BYTES.get(args.config) if args.kernel_config == 0 else None
+    if hbm <= int_roof_gbs:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s", "frac": achieved_gbs / hbm}
+    else:
+        roof = {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Top/s",
+                "frac": achieved_ops / peak_ops}
+    roof.update({
+        "traffic": traffic, "kernel": "scan_kernel (MD5 + Bloom + probe + tile compaction)", "kernel_ms": kms,
+        "peak_source": hbm_src, "int_roof_GBps": int_roof_gbs,
+        "alu_frac_of_issue_ceiling": achieved_ops / peak_ops,
+        "alu_frac_of_measured_int_peak": achieved_ops / (int_peak["mixed_ops_per_s"] * 1e12),
+        "detail": {
+            "algorithmic_bytes_per_launch": alg_bytes, "kernel_GBps_image": sectors * SECTOR / (kms * 1e-3) / 1e9,
+            "achieved_int_Tops": achieved_ops / 1e12, "issue_ceiling_Tops": peak_ops / 1e12,
+            "int_peak_measured": int_peak, "hash_hbm_roofline_GBps": min(hbm, int_roof_gbs),
+            "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch, from one ncu capture of the "
+                            "same kernel on the 4 GiB mid workload, scaled by sectors to the 32 GiB image",
+            "peak_note": f"{SM_COUNT} SMs x {INT_LANES_PER_SM_CLK} int ops/clk x median SM clock {sm_mhz:.0f} MHz "
+                         f"sampled in the timed region; {MD5_OPS_PER_SECTOR} algorithmic ops per sector"}})
+    return roof
+
+
+def headline(*, value, world, args, ms, nbytes, sectors, plan, kernel_config, matches, exact, roof, clocks, e2e,
+             cpu, launches, batched, served):
+    """The last stdout line: the headline figures only (the sections went out on earlier lines)."""
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic (seeded generator, the paper's random-file workload mix)",
+        "config": {"workload": f"{args.config}: {nbytes / 2**30:.0f} GiB image ({sectors} sectors), "
+                               f"{plan.n_master_sectors} master sectors in {plan.n_files} files, MD5, device-resident",
+                   "l2": "inputs larger than L2 (no flush)", "kernel_config": kernel_config,
+                   "matches_per_step": matches, "bit_exact_vs_plant_log": exact},
+        "sectors_per_s": world * sectors / (ms * 1e-3),
+        "roofline": roof,
+        "clocks": {k: clocks.get(k) for k in ("sm_mhz", "sm_max_mhz", "reasons", "samples")},
+        "e2e": None if e2e is None else {k: e2e[k] for k in ("value", "unit", "h2d_bytes_per_step",
+                                                              "d2h_bytes_per_step", "frac_of_h2d_link")},
+        "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "gpu_launches": launches,
+    }
+    if batched:
+        line["batched"] = {"GBps": batched["graph_GBps"], "speedup_vs_sequential": batched["speedup_vs_sequential"],
+                           "bit_exact": batched["bit_exact_vs_plant_log"]}
+    if served:
+        line["served"] = {"p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"],
+                          "GBps": served["throughput_GBps"], "bit_exact": served["bit_exact_vs_plant_log"]}
+        line["p99_served_ms"] = served["p99_ms"]
+    line["sections"] = "earlier stdout lines, one JSON object each, keyed by 'section'"
+    return line
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -671,6 +756,7 @@ def main():
     ap.add_argument("--serve-copy-gib", type=float, default=0.0, help="copy bytes queued at once (0: the library's)")
     ap.add_argument("--h2d-link-gbps", type=float, default=211.0, help="host link rate for the drives' copy floor")
     ap.add_argument("--serve-only", action="store_true", help="run only the served section and print its JSON")
+    ap.add_argument("--sections-out", default="", help="also append every section's JSON line to this file")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -749,7 +835,7 @@ def main():
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    kernel_ms, matches, launches = [], 0, 0
+    kernel_ms, matches, launches, hit_sectors = [], 0, 0, 0
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -760,6 +846,7 @@ def main():
             st = r.stats()
             kernel_ms.append(st["kernel_ms"])
             matches = st["matches"]
+            hit_sectors = st["hit_sectors"]
             launches += st["kernel_launches"]
             r.close()
         e1.record(stream)
@@ -773,12 +860,10 @@ def main():
     exact = bool(np.array_equal(r.matches(0), plan.expected_intact()))
     r.close()
 
-    sigs = None
     if not args.no_sigs:
-        sigs = run_signatures(torch, cv, synth, plan, image, stream, args.sig_steps)
-    tables = None
+        emit_section(args, "signatures", run_signatures(torch, cv, synth, plan, image, stream, args.sig_steps))
     if not args.no_tables:
-        tables = run_tables(torch, cv, synth, plan, image, stream, args.table_steps)
+        emit_section(args, "tables", run_tables(torch, cv, synth, plan, image, stream, args.table_steps))
 
     # end to end through the C ABI from pinned host memory
     e2e = None
@@ -829,14 +914,16 @@ def main():
                                       "kernel_GBps": 4 * nbytes / (st["kernel_ms"] * 1e-3) / 1e9,
                                       "matches": st["matches"], "bound": "host-to-device copies"}
 
-    sweep = None
-    if not args.no_sweep and rank == 0:
-        sweep = run_sweep(torch, cv, synth, stream, args.sweep_steps)
+    if e2e is not None:
+        emit_section(args, "e2e", e2e)
 
-    frags = None
+    if not args.no_sweep and rank == 0:
+        emit_section(args, "table_sweep", run_sweep(torch, cv, synth, stream, args.sweep_steps))
+
     if not args.no_frag and rank == 0:
-        frags = run_fragments(torch, cv, synth, stream, args.frag_steps, args.frag_cpu_mib << 20, args.frag_config,
-                              tuple(int(x) for x in args.frag_sigs.split(",")), clocks.get("sm_mhz") or 2070.0)
+        emit_section(args, "fragments", run_fragments(
+            torch, cv, synth, stream, args.frag_steps, args.frag_cpu_mib << 20, args.frag_config,
+            tuple(int(x) for x in args.frag_sigs.split(",")), clocks.get("sm_mhz") or 2070.0))
 
     ip = cv.int_peak()
     int_peak = {k: ip[k] / 1e12 for k in ("alu_ops_per_s", "fma_ops_per_s", "mixed_ops_per_s")}
@@ -845,54 +932,27 @@ def main():
                      "how": "cv_int_peak: independent lop3 / mad.lo chains, 8 blocks of 256 threads per SM"})
     kms = statistics.mean(kernel_ms)
     sectors = plan.n_sectors
-    achieved_ops = sectors * MD5_OPS_PER_SECTOR / (kms * 1e-3)
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
-    peak_ops = SM_COUNT * INT_LANES_PER_SM_CLK * sm_mhz * 1e6
-    peaks = measured_peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    roof_gbs = min(hbm, peak_ops / (MD5_OPS_PER_SECTOR / SECTOR) / 1e9)
-    line = {
-        "metric": "disk-image GB/s scanned", "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u32", "data": "synthetic",
-        "config": {"workload": f"{args.config}: {nbytes / 2**30:.0f} GiB image ({sectors} sectors), "
-                               f"{plan.n_master_sectors} master sectors in {plan.n_files} files, device-resident",
-                   "l2": "inputs larger than L2 (no flush)", "kernel_config": cv.kernel_configs()[
-                       args.kernel_config - 1] if args.kernel_config else "default",
-                   "matches_per_step": matches, "bit_exact_vs_plant_log": exact, "table_build_s": build_s},
-        "sectors_per_s": world * sectors / (ms * 1e-3),
-        "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12, "unit": "Top/s",
-                     "frac": achieved_ops / peak_ops,
-                     "traffic": SCAN_TRAFFIC_BYTES.get(args.config) if args.kernel_config == 0 else None,
-                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum per launch: 4.427 GB measured "
-                                     "on the 4 GiB mid workload, x8 by sectors for the 32 GiB image",
-                     "kernel": "scan_kernel (MD5 + Bloom + probe + tile compaction)",
-                     "kernel_ms": kms, "kernel_GBps": nbytes / (kms * 1e-3) / 1e9,
-                     "peak_note": f"{SM_COUNT} SMs x {INT_LANES_PER_SM_CLK} int ops/clk x median SM clock "
-                                  f"{sm_mhz:.0f} MHz sampled in the timed region; "
-                                  f"{MD5_OPS_PER_SECTOR} algorithmic ops per sector",
-                     "hash_hbm_roofline_GBps": roof_gbs,
-                     "frac_of_hash_hbm_roofline": (nbytes / (kms * 1e-3) / 1e9) / roof_gbs,
-                     "hbm_peak_GBps_measured": hbm, "int_peak_measured": int_peak},
-        "clocks": clocks,
-        "e2e": e2e,
-        "signatures": sigs,
-        "tables": tables,
-        "fragments": frags,
-        "table_sweep": sweep,
-        "gpu_launches": launches,
-    }
+    roof = scan_roofline(kms, sectors, hit_sectors, clocks, int_peak, args)
+    emit_section(args, "roofline_detail", roof.pop("detail"))
     master.close()
+    batched = served = None
     if not args.no_batch:
-        line["batched"] = run_batched(torch, cv, synth, args, stream)
+        batched = run_batched(torch, cv, synth, args, stream)
+        emit_section(args, "batched", batched)
     if not args.no_serve:
-        line["served"] = run_served(torch, cv, synth, args, host)
-        line["p99_served_ms"] = line["served"]["p99_ms"]
+        served = run_served(torch, cv, synth, args, host)
+        emit_section(args, "served", served)
     del host
+    cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(plan, args.cpu_sample_pieces)
+        cpu = cpu_baseline(plan, args.cpu_sample_pieces)
+        emit_section(args, "cpu_baseline", cpu)
+    line = headline(value=value, world=world, args=args, ms=ms, nbytes=nbytes, sectors=sectors, plan=plan,
+                    kernel_config=cv.kernel_configs()[args.kernel_config - 1] if args.kernel_config else "default",
+                    matches=matches, exact=exact, roof=roof, clocks=clocks, e2e=e2e, cpu=cpu, launches=launches,
+                    batched=batched, served=served)
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(line, separators=(",", ":")), flush=True)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
