@@ -218,6 +218,10 @@ typedef struct {
   float total_ms;          /* device time from the first copy to the last result copy */
   uint32_t kernel_launches; /* kernels the call launched (scan, offsets, expand) */
   uint32_t reserved;
+  uint64_t confirm_rejected; /* 64-bit signatures: candidate (disk sector, master sector or
+                                fragment) pairs whose signatures were equal but whose bytes
+                                differed, dropped by the byte confirmation (Section 3.1); 0 for
+                                MD5 tables and for batched, served and allocation-free scans */
 } cv_scan_stats;
 
 int cv_scan_get_stats(const cv_result* r, cv_scan_stats* st);
@@ -268,6 +272,39 @@ int cv_last_cuda_error(void);
  * stream and returns without waiting. Errors: CV_EINVAL, CV_ECUDA, CV_ENODEV.
  */
 int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t* trivial, void* stream);
+
+/*
+ * The sector signature of n_sectors consecutive 512-byte sectors under any CV_SIG_* (paper
+ * Section 2.1 for MD5 and MD5 without padding, Eq. 1 for djb2-64, Section 2.1's generator for
+ * CRC64), computed by the same kernel code that hashes sectors in a scan and in a table build.
+ * It lets a caller (or a test) compare the library's signatures value by value with another
+ * implementation: a wrong but deterministic 64-bit signature would leave every match list
+ * unchanged, since equal bytes hash equally and byte confirmation drops every false candidate.
+ *   in       device pointer, 16-byte aligned, n_sectors * 512 bytes.
+ *   out      device pointer, 16-byte aligned, 16 bytes per sector:
+ *              CV_SIG_MD5        the digest (RFC 1321 byte order);
+ *              CV_SIG_MD5_NOPAD  the state A, B, C, D after the 8 data blocks, same byte order;
+ *              CV_SIG_DJB2_64, CV_SIG_CRC64  bytes 0-7 the 64-bit signature (little-endian),
+ *                                bytes 8-15 the library's mixing of it (a SplitMix64 finalizer;
+ *                                the table's Bloom bits come from it).
+ *   trivial  device pointer to one byte per sector set to 1 when all 512 bytes are equal, or NULL.
+ * Runs on stream and returns without waiting. Errors: CV_EINVAL, CV_ECUDA, CV_ENODEV.
+ */
+int cv_sector_signatures(const void* in, uint64_t n_sectors, uint32_t signature, void* out, uint8_t* trivial,
+                         void* stream);
+
+/*
+ * The signature of every 64-byte window at a 4-byte offset of a device image (paper Section 5),
+ * computed by the fragment scan's own code: window k is bytes [4k, 4k + 64), for every k with
+ * 4k + 64 <= n_bytes. signature: CV_SIG_MD5 (the 64-byte message with its padding block),
+ * CV_SIG_MD5_NOPAD (the state after the one data block) or CV_SIG_DJB2_64 (rolled from window
+ * to window as in the scan: bytes 0-7 the value, little-endian, bytes 8-15 the library's mixing
+ * of it); CV_SIG_CRC64 is refused with CV_EINVAL, as for fragment tables.
+ *   image  device pointer, 16-byte aligned; out: device pointer, 16-byte aligned, 16 bytes per
+ *          window. Fewer than 64 bytes: nothing to do.
+ * Runs on stream and returns without waiting. Errors: CV_EINVAL, CV_ECUDA, CV_ENODEV.
+ */
+int cv_window_signatures(const void* image, uint64_t n_bytes, uint32_t signature, void* out, void* stream);
 
 /* Integer throughput of this GPU: independent lop3 chains (ALU pipe), mad.lo chains (FMA pipe)
  * and the two interleaved, in operations per second, with the SM clock seen during the run.
@@ -409,8 +446,10 @@ int cv_server_get_stats(cv_server* s, cv_server_stats* st);
  * Runs on stream and returns after the work has finished. Every call shares the one scratch
  * array and finds the previous call's contents there; calls whose work could overlap on the
  * GPU must be serialized by the caller. The first call on a device performs a one-time set-up
- * (the array's device address, kernel attributes); make it before any stream capture. With a
- * position-keyed table the image's clusters are counted from its sector 0.
+ * (the array's device address, kernel attributes). No call can be captured into a CUDA graph
+ * (each one waits for its stream): on a capturing stream the call returns CV_EINVAL before any
+ * work. With a position-keyed table the image's clusters are counted from its sector 0. On any
+ * error other than CV_ERANGE the contents of out are undefined.
  * Errors: CV_EINVAL, CV_ERANGE, CV_ECUDA, CV_ETIMEOUT, CV_ECORRUPT, CV_ENODEV.
  */
 #define CV_NOALLOC_MAX_SECTORS (1u << 19)

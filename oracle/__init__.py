@@ -19,6 +19,9 @@ Functions and the passages they follow:
   kept master sectors, each disk sector's signature looked up, equal signatures reported, sorted.
 * ``match_sig(image, files, sig)`` -- the same with another signature: MD5 without padding, djb2-64
   (Eq. 1) or CRC64 (Section 2.1); candidates of the 64-bit ones are confirmed byte for byte.
+* ``signature`` / ``signatures(data, sig)`` -- one sector's (every sector's) signature under any kind;
+  ``window_signatures(image, sig)`` -- every 64-byte window's at a 4-byte offset (Section 5);
+  ``md5_blocks`` -- the MD5 state after whole blocks without padding.
 
 Parity pins (tests/test_oracle.py): MD5 against hashlib (OpenSSL) and md5sum; ``match_hash``
 against ``match_brute`` on tiny inputs with duplicates, fills and partial sectors; both against
@@ -101,6 +104,12 @@ def bind(lib):
     lib.oracle_match_position.restype = ctypes.c_int64
     lib.oracle_db_build_sig.argtypes = [vp, vp, u32, ctypes.c_int]
     lib.oracle_db_build_sig.restype = vp
+    lib.oracle_signatures.argtypes = [vp, u64, ctypes.c_int, vp]
+    lib.oracle_signatures.restype = None
+    lib.oracle_md5_blocks.argtypes = [vp, u64, vp]
+    lib.oracle_md5_blocks.restype = None
+    lib.oracle_window_signatures.argtypes = [vp, u64, ctypes.c_int, vp]
+    lib.oracle_window_signatures.restype = None
     lib.oracle_threads.argtypes = []
     lib.oracle_threads.restype = ctypes.c_int
     lib.oracle_set_threads.argtypes = [ctypes.c_int]
@@ -227,6 +236,35 @@ def signature(sector, sig: int) -> bytes:
     out = np.zeros(16, np.uint8)
     _load().oracle_signature(_ptr(a), sig, out.ctypes.data)
     return out.tobytes()
+
+
+def signatures(data, sig: int) -> np.ndarray:
+    """``signature`` of every whole 512-byte sector of data: an (n, 16) uint8 array."""
+    a = _u8(data)
+    n = a.size // SECTOR
+    out = np.zeros((n, 16), np.uint8)
+    if n:
+        _load().oracle_signatures(_ptr(a), n, int(sig), out.ctypes.data)
+    return out
+
+
+def md5_blocks(data) -> bytes:
+    """MD5 state after the whole 64-byte blocks of data, without a padding block."""
+    a = _u8(data)
+    out = np.zeros(16, np.uint8)
+    _load().oracle_md5_blocks(_ptr(a), a.size // 64, out.ctypes.data)
+    return out.tobytes()
+
+
+def window_signatures(image, sig: int) -> np.ndarray:
+    """The signature of every 64-byte window at a 4-byte offset (Section 5): (n_windows, 16)
+    uint8; djb2-64 little-endian in the first 8 bytes."""
+    a = _u8(image)
+    n = (a.size - 64) // 4 + 1 if a.size >= 64 else 0
+    out = np.zeros((n, 16), np.uint8)
+    if n:
+        _load().oracle_window_signatures(_ptr(a), a.size, int(sig), out.ctypes.data)
+    return out
 
 
 def match_sig(image, files, sig: int) -> np.ndarray:

@@ -222,6 +222,48 @@ void oracle_signature(const uint8_t* sector, int sig, uint8_t out[16]) {
   }
 }
 
+/* The signatures of n consecutive 512-byte sectors, 16 bytes each as oracle_signature writes
+ * them (independent sectors, optionally in parallel). */
+void oracle_signatures(const uint8_t* data, uint64_t n_sectors, int sig, uint8_t* out) {
+  md5_init_table();
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < (int64_t)n_sectors; i++) oracle_signature(data + (uint64_t)i * SECTOR, sig, out + 16 * i);
+}
+
+/* The MD5 state (A, B, C, D) after n_blocks 64-byte blocks of msg, with no padding block
+ * (RFC 1321 Section 3.4 applied to the blocks as they are); 16 bytes, digest byte order. For
+ * a 64-byte fragment this is Section 2.1's signature without padding, one compression. */
+void oracle_md5_blocks(const uint8_t* msg, uint64_t n_blocks, uint8_t out[16]) {
+  md5_init_table();
+  uint32_t st[4] = {0x67452301u, 0xefcdab89u, 0x98badcfeu, 0x10325476u};
+  for (uint64_t b = 0; b < n_blocks; b++) md5_block(st, msg + 64 * b);
+  for (int j = 0; j < 4; j++)
+    for (int q = 0; q < 4; q++) out[4 * j + q] = (uint8_t)(st[j] >> (8 * q));
+}
+
+/* The signature of every 64-byte window at a 4-byte offset (Section 5): window k is bytes
+ * [4k, 4k + 64) for every k with 4k + 64 <= image_bytes. 16 bytes per window: the MD5 digest of
+ * the 64 bytes (SIG_MD5), the state after its one block (SIG_MD5_NOPAD), or djb2-64 of the 64
+ * bytes little-endian in the first 8 bytes and zeros after (SIG_DJB2_64). */
+void oracle_window_signatures(const uint8_t* image, uint64_t image_bytes, int sig, uint8_t* out) {
+  md5_init_table();
+  const int64_t n_win = image_bytes >= 64 ? (int64_t)((image_bytes - 64) / 4 + 1) : 0;
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < n_win; k++) {
+    const uint8_t* w = image + 4 * (uint64_t)k;
+    uint8_t* o = out + 16 * (uint64_t)k;
+    memset(o, 0, 16);
+    if (sig == SIG_MD5) {
+      oracle_md5(w, 64, o);
+    } else if (sig == SIG_MD5_NOPAD) {
+      oracle_md5_blocks(w, 1, o);
+    } else {
+      const uint64_t h = oracle_djb2_64(w, 64);
+      for (int j = 0; j < 8; j++) o[j] = (uint8_t)(h >> (8 * j));
+    }
+  }
+}
+
 /* ------------------------------------------------------------------ the exclusion rule */
 
 /* A master sector is excluded iff all 512 of its bytes are equal. */

@@ -102,22 +102,41 @@ int cvk::digest_job(DevCtx* ctx, int cfg_i, int sig, Job& job, uint4* digests, u
 
 extern "C" {
 
-int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t* trivial, void* stream_) {
+int cv_sector_signatures(const void* in, uint64_t n_sectors, uint32_t signature, void* out, uint8_t* trivial,
+                         void* stream_) {
+  if (signature > CV_SIG_CRC64) return CV_EINVAL;
   if (n_sectors == 0) return CV_OK;
-  if (!in || !digests) return CV_EINVAL;
-  if (((uintptr_t)in & 15u) || ((uintptr_t)digests & 15u)) return CV_EINVAL;
+  if (!in || !out) return CV_EINVAL;
+  if (((uintptr_t)in & 15u) || ((uintptr_t)out & 15u)) return CV_EINVAL;
   DevCtx* ctx;
   CV_TRY(get_ctx(&ctx));
   cudaStream_t stream = (cudaStream_t)stream_;
   int cfg_i;
-  const ScanCfg& cfg = scan_config_for(ctx->cfg_index, kSigMd5, &cfg_i);
+  const ScanCfg& cfg = scan_config_for(ctx->cfg_index, (int)signature, &cfg_i);
+  if (!cfg.digest_fn[signature]) return CV_EINVAL;
   Temps tmp(ctx, stream);
   Job job;
   CV_TRY(job.add(ctx, cfg, in, n_sectors, 0, 0, false));
   uint32_t* status;
   CV_TRY(tmp.alloc(&status, 4));
   CV_CUDA(cudaMemsetAsync(status, 0, 4, stream));
-  return digest_job(ctx, cfg_i, kSigMd5, job, (uint4*)digests, trivial, status, stream, tmp);
+  return digest_job(ctx, cfg_i, (int)signature, job, (uint4*)out, trivial, status, stream, tmp);
+}
+
+int cv_sector_digests(const void* in, uint64_t n_sectors, void* digests, uint8_t* trivial, void* stream) {
+  return cv_sector_signatures(in, n_sectors, CV_SIG_MD5, digests, trivial, stream);
+}
+
+int cv_window_signatures(const void* image, uint64_t n_bytes, uint32_t signature, void* out, void* stream) {
+  if (signature != CV_SIG_MD5 && signature != CV_SIG_MD5_NOPAD && signature != CV_SIG_DJB2_64) return CV_EINVAL;
+  if (n_bytes < 64) return CV_OK;
+  if (!image || !out) return CV_EINVAL;
+  if (((uintptr_t)image & 15u) || ((uintptr_t)out & 15u)) return CV_EINVAL;
+  DevCtx* ctx;
+  CV_TRY(get_ctx(&ctx));
+  CV_CUDA((cudaError_t)frag_window_sigs((int)signature, (const uint8_t*)image, n_bytes, (uint4*)out, ctx->sms,
+                                        stream));
+  return CV_OK;
 }
 
 }  // extern "C"
@@ -213,7 +232,7 @@ int frag_scan(DevCtx* ctx, const cv_master* m, const cv_buf* images, uint32_t n_
       Segment* segs_d;
       CV_TRY(tmp.alloc(&tile_ntrip, std::max<uint64_t>(T, 1) * 8));
       CV_TRY(tmp.alloc(&tile_off, std::max<uint64_t>(T, 1) * 8));
-      CV_TRY(tmp.alloc(&seg_off_d, (n_images + 2) * 8));  // seg_off[n], total, status
+      CV_TRY(tmp.alloc(&seg_off_d, (n_images + 3) * 8));  // seg_off[n], total, status, rejected
       CV_TRY(tmp.alloc(&scratch, tile_offsets_scratch_words(T) * 8 + 8));
       CV_TRY(tmp.alloc(&list, (max_tiles + 1) * 4));
       CV_TRY(tmp.alloc(&segs_d, std::max<uint32_t>(n_images, 1) * sizeof(Segment)));
@@ -226,24 +245,27 @@ int frag_scan(DevCtx* ctx, const cv_master* m, const cv_buf* images, uint32_t n_
       if (n_images)
         CV_CUDA(cudaMemcpyAsync(segs_d, segs.data(), n_images * sizeof(Segment), cudaMemcpyHostToDevice, stream));
       uint32_t* status = (uint32_t*)(seg_off_d + n_images + 1);
-      CV_CUDA(cudaMemsetAsync(status, 0, 8, stream));
+      unsigned long long* rejected = (unsigned long long*)(seg_off_d + n_images + 2);
+      CV_CUDA(cudaMemsetAsync(status, 0, 16, stream));
       CV_CUDA(cudaEventRecord(ev[1], stream));
       for (uint32_t i = 0; i < n_images; i++) {
         if (tile_base[i + 1] == tile_base[i]) continue;
-        CV_CUDA((cudaError_t)frag_count(m->tab, dptr[i], nbytes[i], tile_base[i], tile_ntrip, status, ctx->sms, stream));
+        CV_CUDA((cudaError_t)frag_count(m->tab, dptr[i], nbytes[i], tile_base[i], tile_ntrip, status, rejected,
+                                        ctx->sms, stream));
         r->launches++;
       }
       CV_CUDA(cudaEventRecord(ev[2], stream));
       CV_CUDA((cudaError_t)launch_tile_offsets(tile_ntrip, T, tile_off, segs_d, n_images, 1, seg_off_d,
                                                seg_off_d + n_images, scratch, stream));
       r->launches += 4;
-      std::vector<uint64_t> seg_off(n_images + 2, 0);
-      CV_CUDA(cudaMemcpyAsync(seg_off.data(), seg_off_d, (n_images + 2) * 8, cudaMemcpyDeviceToHost, stream));
+      std::vector<uint64_t> seg_off(n_images + 3, 0);
+      CV_CUDA(cudaMemcpyAsync(seg_off.data(), seg_off_d, (n_images + 3) * 8, cudaMemcpyDeviceToHost, stream));
       CV_CUDA(cudaStreamSynchronize(stream));
       const uint32_t st = (uint32_t)seg_off[n_images + 1];
       if (st & kStTimeout) return CV_ETIMEOUT;
       if (st) return CV_ECORRUPT;
       const uint64_t total = seg_off[n_images];
+      r->st.confirm_rejected = seg_off[n_images + 2];
       if (total) {
         CV_CUDA(cudaMallocFromPoolAsync((void**)&r->dev_out, total * sizeof(MatchOut), ctx->pool, stream));
         for (uint32_t i = 0; i < n_images; i++) {
@@ -386,7 +408,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
       const size_t nseg = job.segs.size();
       const uint64_t nt = job.n_tiles;
       uint64_t total = 0;
-      std::vector<uint64_t> seg_off(nseg + 3, 0);
+      std::vector<uint64_t> seg_off(nseg + 4, 0);
       uint32_t* status_keep = nullptr;
       if (nseg) {
         void* ring[2] = {nullptr, nullptr};
@@ -417,10 +439,11 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         CV_TRY(tmp.alloc(&tile_nhit, n_out * 4));
         CV_TRY(tmp.alloc(&tile_ntrip, n_out * 8));
         CV_TRY(tmp.alloc(&tile_off, n_out * 8));
-        CV_TRY(tmp.alloc(&seg_off_d, (nseg + 3) * 8));  // seg_off[nseg], total, status, hit sectors
+        // seg_off[nseg], total, status, hit sectors, rejected candidates
+        CV_TRY(tmp.alloc(&seg_off_d, (nseg + 4) * 8));
         status = (uint32_t*)(seg_off_d + nseg + 1);
         status_keep = status;
-        CV_CUDA(cudaMemsetAsync(status, 0, 16, stream));
+        CV_CUDA(cudaMemsetAsync(status, 0, 24, stream));
         CV_CUDA(cudaMemcpyAsync(segs_d, job.segs.data(), nseg * sizeof(Segment), cudaMemcpyHostToDevice, stream));
         ScanParams p;
         memset(&p, 0, sizeof p);
@@ -429,6 +452,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         p.tile_nhit = tile_nhit;
         p.tile_ntrip = tile_ntrip;
         p.status = status;
+        p.rejected = (unsigned long long*)(seg_off_d + nseg + 3);
         CV_CUDA(cudaEventRecord(ev[1], stream));
         NvtxRange launches_range("cv.scan.launches");
         // device segments: one launch per run of consecutive device segments
@@ -466,13 +490,14 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
                                                  seg_off_d, total_d, off_scratch, stream));
         CV_CUDA((cudaError_t)launch_sum_u32(tile_nhit, n_out, seg_off_d + nseg + 2, ctx->sms, stream));
         r->launches += 1;
-        CV_CUDA(cudaMemcpyAsync(seg_off.data(), seg_off_d, (nseg + 3) * 8, cudaMemcpyDeviceToHost, stream));
+        CV_CUDA(cudaMemcpyAsync(seg_off.data(), seg_off_d, (nseg + 4) * 8, cudaMemcpyDeviceToHost, stream));
         CV_CUDA(cudaStreamSynchronize(stream));
         const uint32_t st = (uint32_t)seg_off[nseg + 1];
         if (st & kStTimeout) return CV_ETIMEOUT;
         if (st) return CV_ECORRUPT;
         total = seg_off[nseg];
         r->st.hit_sectors = seg_off[nseg + 2];
+        r->st.confirm_rejected = seg_off[nseg + 3];
         if (total) {
           CV_CUDA(cudaMallocFromPoolAsync((void**)&r->dev_out, total * sizeof(MatchOut), ctx->pool, stream));
           CV_CUDA((cudaError_t)launch_expand(cfg, hit_rec, tile_nhit, tile_off, n_out, segs_d, nseg32, tab,

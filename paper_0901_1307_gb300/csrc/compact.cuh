@@ -116,11 +116,14 @@ __global__ void sum_u32_kernel(const uint32_t* v, uint64_t n, unsigned long long
 // One warp per output tile (32 consecutive sectors) with hits. A hit record is {lane, post_off,
 // post_cnt, n_emit}: the sector emits n_emit triples, all of its postings, or with a 64-bit
 // signature (confirm != null) those whose master sector equals the disk sector byte for byte.
-// out_cap bounds the writes (kStOverflow when exceeded).
+// out_cap bounds the writes (kStOverflow when exceeded). When the scan before it on the stream
+// failed (a wait timed out or a lookup ran past the probe bound: its hit records are not to be
+// trusted), the pass writes nothing.
 template <int T>
 __global__ void expand_kernel(const uint4* hit_rec, const uint32_t* tile_nhit, const uint64_t* tile_off,
                               uint64_t n_out_tiles, const Segment* segs, uint32_t n_segs, const uint2* postings,
                               MatchOut* out, uint64_t out_cap, uint32_t* status, const uint8_t* confirm) {
+  if (*(volatile const uint32_t*)status & (kStTimeout | kStProbeBound | kStBadTable)) return;
   constexpr uint32_t kW = T / 32;
   const int lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);

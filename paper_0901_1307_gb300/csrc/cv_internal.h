@@ -148,6 +148,9 @@ struct ScanParams {
   // digest outputs (digest mode): indexed by segment sector_base + row
   uint4* digests;
   uint8_t* trivial;
+  // 64-bit signatures: candidates (disk sector, posting) whose signatures are equal and whose
+  // bytes differ are added here; null: not counted
+  unsigned long long* rejected;
 };
 
 // One output triple (the layout of cv_match).

@@ -60,9 +60,13 @@ int frag_digests(int sig, const uint8_t* arena, uint64_t n, uint4* dig, uint8_t*
 // for none; mask = words - 1) and the shared-memory filter l1 (kFragL1Bytes).
 int frag_bloom(const uint4* slots, uint32_t n_slots, uint32_t* words, uint32_t mask, uint32_t* l1, int sms,
                void* stream);
-// Triples per tile of one device image (16-byte aligned) into tile_ntrip[tile_base ..).
+// Triples per tile of one device image (16-byte aligned) into tile_ntrip[tile_base ..);
+// djb2 candidates dropped by the byte comparison are added to *rejected (when non-null).
 int frag_count(const TableView& tab, const uint8_t* image, uint64_t n_bytes, uint64_t tile_base, uint64_t* tile_ntrip,
-               uint32_t* status, int sms, void* stream);
+               uint32_t* status, unsigned long long* rejected, int sms, void* stream);
+// The 16-byte key of every 64-byte window at a 4-byte offset of a device image, through the
+// fragment kernels' own signature code (MD5, MD5 without padding, rolled djb2-64).
+int frag_window_sigs(int sig, const uint8_t* image, uint64_t n_bytes, uint4* out, int sms, void* stream);
 // The triples of the image's tiles that have any, at out[tile_off[tile]..]. list: scratch of
 // frag_tiles(n_bytes) + 1 u32 words. *launches counts the kernels launched.
 int frag_emit(const TableView& tab, const uint8_t* image, uint64_t n_bytes, uint64_t tile_base,

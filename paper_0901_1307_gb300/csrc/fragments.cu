@@ -78,6 +78,7 @@ struct FragParams {
   uint64_t out_cap;
   uint32_t* status;
   uint32_t one;                  // always 1 (the MD5 kernels' opaque multiplier)
+  unsigned long long* rejected;  // count: djb2 candidates dropped by the byte comparison (or null)
 };
 
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar,
@@ -89,14 +90,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
       : "memory");
 }
 
-// Base-33 Horner value of a little-endian word, byte 0 first (Eq. 1 over four bytes):
-// b0 33^3 + b1 33^2 + b2 33 + b3, as two 2-way (16-bit weight x 8-bit byte) dot products.
-__device__ __forceinline__ uint32_t horner33(uint32_t w) {
-  constexpr uint32_t kW01 = (1089u << 16) | 35937u;  // 33^2 (byte 1), 33^3 (byte 0)
-  constexpr uint32_t kW23 = (1u << 16) | 33u;         // 1 (byte 3), 33 (byte 2)
-  return __dp2a_lo(kW01, w, __dp2a_hi(kW23, w, 0u));
-}
-
 __device__ __forceinline__ uint32_t frag_bloom_bits(uint32_t d2) {
   return (1u << (d2 & 31)) | (1u << ((d2 >> 5) & 31)) | (1u << ((d2 >> 10) & 31));
 }
@@ -105,6 +98,30 @@ __device__ __forceinline__ bool frag_bloom_test(const TableView& tab, uint32_t d
   const uint32_t bits = frag_bloom_bits(d2);
   return (__ldg(reinterpret_cast<const uint32_t*>(tab.bloom) + (d3 & tab.bloom_mask)) & bits) == bits;
 }
+
+// djb2-64 of consecutive windows w0, w0 + 1, ... (ws: 32-bit words in shared memory), rolled:
+// first() computes window w0 from its 16 words, then next(i) moves to window w0 + i (called for
+// i = 1, 2, ... in order) with one new word. P holds the Horner values of the current window's
+// words, g = h - 5381 * 33^64.
+struct Djb2Roll {
+  uint32_t P[16];
+  uint64_t g;
+  __device__ __forceinline__ uint64_t first(const uint32_t* ws, uint32_t w0) {
+    g = 0;
+#pragma unroll
+    for (int q = 0; q < 16; q++) {
+      P[q] = horner33(ws[w0 + q]);
+      g = g * kD33x4 + P[q];
+    }
+    return g + kDjbInit;
+  }
+  __device__ __forceinline__ uint64_t next(const uint32_t* ws, uint32_t w0, int i) {
+    const uint32_t pin = horner33(ws[w0 + i + 15]);
+    g = g * kD33x4 - (uint64_t)P[(i - 1) & 15] * kD33x64 + pin;
+    P[(i - 1) & 15] = pin;
+    return g + kDjbInit;
+  }
+};
 
 // Key words of the window whose first word is ws[w] (shared memory), computed directly.
 template <int SIG>
@@ -143,26 +160,15 @@ __device__ __forceinline__ uint64_t frag_candidates(const FragParams& p, const u
   using G = FragGeom<SIG>;
   uint64_t cand = 0;
   if constexpr (G::kRolled) {
-    uint32_t P[16];
-    uint64_t g = 0;
-#pragma unroll
-    for (int q = 0; q < 16; q++) {
-      P[q] = horner33(ws[w0 + q]);
-      g = g * kD33x4 + P[q];
-    }
     // Every window's shared-memory test first (its bit comes from h's high word, d1, with no
     // further mixing); then, for those that passed, the mixed words d2, d3 and the global Bloom
     // words, all requested before any is tested.
+    Djb2Roll roll;
     uint64_t h[G::kWPT];
     uint32_t pass = 0;
 #pragma unroll
     for (int i = 0; i < G::kWPT; i++) {
-      if (i > 0) {
-        const uint32_t pin = horner33(ws[w0 + i + 15]);
-        g = g * kD33x4 - (uint64_t)P[(i - 1) & 15] * kD33x64 + pin;
-        P[(i - 1) & 15] = pin;
-      }
-      h[i] = g + kDjbInit;
+      h[i] = i == 0 ? roll.first(ws, w0) : roll.next(ws, w0, i);
       const uint32_t b = (uint32_t)(h[i] >> 32) >> (32 - kFragL1Log2Bits);
       if ((uint32_t)i < n_valid && (!l1 || ((l1[b >> 5] >> (b & 31)) & 1u))) pass |= 1u << i;
     }
@@ -210,15 +216,19 @@ __device__ __forceinline__ uint32_t frag_resolve(const FragParams& p, const uint
   return n;
 }
 
+// Triples of this thread's candidate windows; *rejected (when given) adds the candidates that
+// the byte comparison dropped.
 template <int SIG, int LAYOUT>
 __device__ __forceinline__ uint64_t frag_thread_count(const FragParams& p, const uint32_t* ws, uint32_t w0,
-                                                      uint64_t cand) {
+                                                      uint64_t cand, uint32_t* rejected = nullptr) {
   uint64_t n = 0;
   while (cand) {
     const int i = __ffsll((long long)cand) - 1;
     cand &= cand - 1;
     uint32_t off, cnt;
-    n += frag_resolve<SIG, LAYOUT>(p, ws, w0 + (uint32_t)i, off, cnt);
+    const uint32_t k = frag_resolve<SIG, LAYOUT>(p, ws, w0 + (uint32_t)i, off, cnt);
+    n += k;
+    if (rejected) *rejected += cnt - k;
   }
   return n;
 }
@@ -329,7 +339,9 @@ __global__ void __launch_bounds__(FragGeom<SIG>::kThreads, 1) frag_count_kernel(
     const uint32_t* ws = reinterpret_cast<const uint32_t*>(buf);
     const uint32_t w0 = (uint32_t)lane * G::kWPT;
     const uint64_t cand = frag_candidates<SIG>(p, ws, w0, frag_valid<SIG>(p, tile, w0), l1);
-    uint64_t n = frag_thread_count<SIG, LAYOUT>(p, ws, w0, cand);
+    uint32_t rej = 0;
+    uint64_t n = frag_thread_count<SIG, LAYOUT>(p, ws, w0, cand, &rej);
+    if (sig_is_weak(SIG) && rej && p.rejected) atomicAdd(p.rejected, (unsigned long long)rej);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) n += __shfl_xor_sync(0xFFFFFFFFu, n, d);
     __syncwarp();  // every lane is done with the buffer
@@ -420,6 +432,57 @@ __global__ void __launch_bounds__(FragGeom<SIG>::kThreads, 1) frag_emit_kernel(c
       }
     }
     __syncwarp();  // the buffer is free again
+  }
+}
+
+// The signature of every window of an image, 16 bytes per window, through the count kernel's
+// own arithmetic: the rolled djb2 of Djb2Roll (the same tile geometry, each lane's first window
+// computed directly and the others rolled), or frag_key for MD5. For djb2 the 16 bytes are the
+// table key words (h, then the mixing word of frag64_words). One warp per tile, staged with
+// plain loads; a test and diagnostic path, not the scan.
+template <int SIG>
+__global__ void __launch_bounds__(256) frag_window_sig_kernel(const uint8_t* image, uint64_t n_bytes,
+                                                              uint64_t n_windows, uint64_t n_tiles, uint4* out,
+                                                              uint32_t one) {
+  using G = FragGeom<SIG>;
+  extern __shared__ __align__(128) uint8_t fsm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* ws = reinterpret_cast<uint32_t*>(fsm + warp * G::kTileBytes);
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t tile = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp; tile < n_tiles; tile += warps) {
+    const uint64_t start = tile * G::kTileStep;
+    for (uint32_t j = lane; j < G::kTileBytes / 4; j += 32) {
+      const uint64_t b = start + 4ull * j;
+      uint32_t v = 0;
+      if (b + 4 <= n_bytes) {
+        v = *reinterpret_cast<const uint32_t*>(image + b);
+      } else {
+        for (uint32_t q = 0; q < 4; q++)
+          if (b + q < n_bytes) v |= (uint32_t)image[b + q] << (8 * q);
+      }
+      ws[j] = v;
+    }
+    __syncwarp();
+    const uint32_t w0 = (uint32_t)lane * G::kWPT;
+    const uint64_t k0 = tile * G::kTileWin + w0;
+    if constexpr (G::kRolled) {
+      Djb2Roll roll;
+#pragma unroll
+      for (int i = 0; i < G::kWPT; i++) {
+        const uint64_t h = i == 0 ? roll.first(ws, w0) : roll.next(ws, w0, i);
+        uint32_t d[4];
+        frag64_words(h, d);
+        if (k0 + i < n_windows) out[k0 + i] = make_uint4(d[0], d[1], d[2], d[3]);
+      }
+    } else {
+      for (int i = 0; i < G::kWPT; i++) {
+        if (k0 + i >= n_windows) break;
+        uint32_t d[4];
+        frag_key<SIG>(ws, w0 + (uint32_t)i, d, one);
+        out[k0 + i] = make_uint4(d[0], d[1], d[2], d[3]);
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -581,9 +644,43 @@ int frag_bloom(const uint4* slots, uint32_t n_slots, uint32_t* words, uint32_t m
   return (int)cudaGetLastError();
 }
 
+int frag_window_sigs(int sig, const uint8_t* image, uint64_t n_bytes, uint4* out, int sms, void* stream) {
+  const uint64_t n_win = frag_windows(n_bytes);
+  if (!n_win) return 0;
+  const void* fn;
+  uint32_t win, bytes;
+  switch (sig) {
+    case kSigMd5:
+      fn = (const void*)frag_window_sig_kernel<kSigMd5>;
+      win = FragGeom<kSigMd5>::kTileWin;
+      bytes = FragGeom<kSigMd5>::kTileBytes;
+      break;
+    case kSigMd5NoPad:
+      fn = (const void*)frag_window_sig_kernel<kSigMd5NoPad>;
+      win = FragGeom<kSigMd5NoPad>::kTileWin;
+      bytes = FragGeom<kSigMd5NoPad>::kTileBytes;
+      break;
+    case kSigDjb2:
+      fn = (const void*)frag_window_sig_kernel<kSigDjb2>;
+      win = FragGeom<kSigDjb2>::kTileWin;
+      bytes = FragGeom<kSigDjb2>::kTileBytes;
+      break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  const uint64_t tiles = (n_win + win - 1) / win;
+  const uint32_t smem = 8 * bytes;  // 8 warps of 256 threads
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  const unsigned grid = (unsigned)std::min<uint64_t>((tiles + 7) / 8, (uint64_t)sms * 8);
+  uint32_t one = 1u;
+  void* args[] = {&image, &n_bytes, (void*)&n_win, (void*)&tiles, &out, &one};
+  return (int)cudaLaunchKernel(fn, dim3(grid), dim3(256), args, smem, (cudaStream_t)stream);
+}
+
 int frag_count(const TableView& tab, const uint8_t* image, uint64_t n_bytes, uint64_t tile_base, uint64_t* tile_ntrip,
-               uint32_t* status, int sms, void* stream) {
+               uint32_t* status, unsigned long long* rejected, int sms, void* stream) {
   FragParams p = make_params(tab, image, n_bytes, tile_base, status);
+  p.rejected = rejected;
   if (!p.n_tiles) return 0;
   FragDev* d;
   int rc = frag_device(&d);

@@ -18,8 +18,11 @@
 //     else they read. Two calls whose work overlaps on the GPU (different streams or host
 //     threads without ordering) race on the array and give wrong results: serialize them.
 //   - The first call on each device does a one-time set-up with that device current (the
-//     array's device address, kernel attributes, occupancy). Make that first call before any
-//     stream capture begins.
+//     array's device address, kernel attributes, occupancy). Every call copies its segment
+//     descriptor from host memory and waits for its stream, so no call can be captured into a
+//     CUDA graph: a call on a capturing stream is refused with CV_EINVAL before any work.
+//   - On an error return the output buffer's contents are undefined; when the scan failed (a
+//     device wait timed out or a lookup ran past its bound) nothing is written to it.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -120,6 +123,12 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
     return CV_ENODEV;
   }
   if (dev != mdev) return CV_EINVAL;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream_, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return CV_EINVAL;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return CV_EINVAL;
   if (S == 0) return CV_OK;
   NoAllocDev* d;
   int rc = setup(dev, &d);

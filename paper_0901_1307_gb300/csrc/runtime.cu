@@ -247,6 +247,7 @@ int launch_range(DevCtx* ctx, int cfg_i, bool digest, const Job& job, const Segm
     p.status = base.status;
     p.digests = base.digests;
     p.trivial = base.trivial;
+    p.rejected = base.rejected;
     for (uint32_t k = lo; k <= hi; k++) p.maps[k - lo] = job.maps[k];
     p.map_base = lo;
     p.one = 1u;

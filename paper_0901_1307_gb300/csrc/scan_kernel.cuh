@@ -169,47 +169,41 @@ __device__ __forceinline__ uint32_t sorted_probe(const TableView& tab, uint32_t 
   return 0u;
 }
 
+// Base-33 Horner value of a little-endian word, byte 0 first (Eq. 1 over four bytes):
+// b0 33^3 + b1 33^2 + b2 33 + b3, as two 2-way (16-bit weight x 8-bit byte) dot products.
+__device__ __forceinline__ uint32_t horner33(uint32_t w) {
+  constexpr uint32_t kW01 = (1089u << 16) | 35937u;  // 33^2 (byte 1), 33^3 (byte 0)
+  constexpr uint32_t kW23 = (1u << 16) | 33u;         // 1 (byte 3), 33 (byte 2)
+  return __dp2a_lo(kW01, w, __dp2a_hi(kW23, w, 0u));
+}
+
 // djb2 over one 64-byte block (Eq. 1): four bytes at a time, h = h * 33^4 + the word's bytes
 // in Horner form (byte 0 is the word's low byte; at most 255 * 37060 < 2^32).
 __device__ __forceinline__ uint64_t djb2_block(uint64_t h, const uint32_t (&X)[16]) {
 #pragma unroll
-  for (int q = 0; q < 16; q++) {
-    const uint32_t w = X[q];
-    const uint32_t part = (((w & 0xFFu) * 33u + ((w >> 8) & 0xFFu)) * 33u + ((w >> 16) & 0xFFu)) * 33u + (w >> 24);
-    h = h * 1185921ull + part;  // 33^4
-  }
+  for (int q = 0; q < 16; q++) h = h * 1185921ull + horner33(X[q]);  // 33^4
   return h;
 }
 
-// The CRC64 byte table for the generator x^64 + x^4 + x^3 + x + 1 (most significant bit
-// first): entry i is the remainder of i(x) x^64, built at compile time by shifting i through
-// eight steps of the division.
-struct Crc64Table {
-  uint64_t v[256];
-};
-constexpr Crc64Table make_crc64_table() {
-  Crc64Table t{};
-  for (uint64_t i = 0; i < 256; i++) {
-    uint64_t c = i << 56;
-    for (int b = 0; b < 8; b++) c = (c & (1ull << 63)) ? (c << 1) ^ 0x1Bull : (c << 1);
-    t.v[i] = c;
-  }
-  return t;
-}
-__device__ constexpr Crc64Table kCrc64Table = make_crc64_table();
-
-// CRC64 over one 64-byte block, a byte at a time through the 256-entry table in shared memory:
-// crc = (crc << 8) ^ T[(crc >> 56) ^ byte], bytes in memory order.
-__device__ __forceinline__ uint64_t crc64_block(uint64_t crc, const uint32_t (&X)[16], const uint64_t* T) {
+// CRC64 with the generator G = x^64 + x^4 + x^3 + x + 1 (Section 2.1), most significant bit
+// first, over one 64-byte block, 32 message bits per step and no table.
+//
+// With R the remainder of M(x) x^64 mod G, appending a 32-bit word w gives
+//   R' = (M x^32 + w) x^64 mod G = r_lo x^32 + (r_hi + w) x^64 mod G,
+// and x^64 = x^4 + x^3 + x + 1 (mod G). For v = r_hi + w, of degree < 32, v (x^4 + x^3 + x + 1)
+// has degree < 36, so it is already reduced: R' = (r_lo << 32) ^ v(x^4 + x^3 + x + 1), which is
+// u ^ (u << 3) with u = v ^ (v << 1), a 33-bit value. Its low word is u_lo ^ (u_lo << 3); its
+// high word is (u_lo >> 29) ^ 9 u_32, where u_32 = v >> 31 is the bit shifted out of v << 1.
+// The word's first byte in memory holds the highest coefficients, hence the byte swap.
+// State: crc = {high word, low word}.
+__device__ __forceinline__ void crc64_block(uint32_t& rh, uint32_t& rl, const uint32_t (&X)[16]) {
 #pragma unroll
   for (int q = 0; q < 16; q++) {
-#pragma unroll
-    for (int b = 0; b < 4; b++) {
-      const uint32_t byte = (X[q] >> (8 * b)) & 0xFFu;
-      crc = (crc << 8) ^ T[(uint32_t)(crc >> 56) ^ byte];
-    }
+    const uint32_t v = rh ^ __byte_perm(X[q], 0u, 0x0123u);
+    const uint32_t u = v ^ (v << 1);
+    rh = rl ^ (u >> 29) ^ ((v >> 31) * 9u);
+    rl = u ^ (u << 3);
   }
-  return crc;
 }
 
 enum : int { kModeScan = 0, kModeDigest = 1 };
@@ -220,8 +214,7 @@ struct ScanSmem {
   // stages first (1024-byte aligned), then the barriers and the abort flag
   static constexpr uint32_t kBarOff = NS * kStageBytes;
   static constexpr uint32_t kMiscOff = kBarOff + 2 * NS * 8;
-  static constexpr uint32_t kCrcOff = kMiscOff + 16;  // CRC64 byte table (256 x 8 bytes)
-  static constexpr uint32_t kBytes = kCrcOff + 256 * 8;
+  static constexpr uint32_t kBytes = kMiscOff + 16;
   static constexpr uint32_t kAlloc = kBytes + 1024;  // room to align the base
 };
 
@@ -253,7 +246,6 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
   const uint32_t bar_full = base + L::kBarOff;  // NS x 8 bytes
   const uint32_t bar_empty = bar_full + NS * 8;
   volatile uint32_t* const s_abort = reinterpret_cast<uint32_t*>(gbase + L::kMiscOff);
-  uint64_t* const s_crc = reinterpret_cast<uint64_t*>(gbase + L::kCrcOff);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -266,9 +258,6 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
     }
     *s_abort = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if constexpr (SIG == kSigCrc64) {
-    for (int k = tid; k < 256; k += blockDim.x) s_crc[k] = kCrc64Table.v[k];
   }
   __syncthreads();
 
@@ -377,7 +366,11 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
           for (int k = 0; k < SPT; k++) h[k] = djb2_block(h[k], X[k]);
         } else if constexpr (SIG == kSigCrc64) {
 #pragma unroll
-          for (int k = 0; k < SPT; k++) h[k] = crc64_block(h[k], X[k], s_crc);
+          for (int k = 0; k < SPT; k++) {
+            uint32_t rh = (uint32_t)(h[k] >> 32), rl = (uint32_t)h[k];
+            crc64_block(rh, rl, X[k]);
+            h[k] = ((uint64_t)rh << 32) | rl;
+          }
         } else if constexpr (SPT == 2) {
           md5_compress_x2<PIPE>(st[0], X[0], st[1], X[1], p.one);
         } else {
@@ -418,6 +411,7 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
             n_emit = 0;
             for (uint32_t q = 0; q < post_cnt; q++)
               n_emit += sectors_equal(mine, p.tab.confirm + (uint64_t)(post_off + q) * kSector) ? 1u : 0u;
+            if (p.rejected && n_emit < post_cnt) atomicAdd(p.rejected, (unsigned long long)(post_cnt - n_emit));
           }
         }
         const bool hit = n_emit != 0u;

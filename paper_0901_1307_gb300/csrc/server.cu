@@ -11,9 +11,16 @@
 //   - Every engine iteration takes, for each live request, its units that have landed on the
 //     device (in order) and scans all of them in one launch (continuous batching). The whole
 //     arena is one allocation, so one tensor map covers every unit.
-//   - A unit's sorted matches are appended to its request; a request is complete when its last
-//     unit has been scanned. Units of one request are always scanned in order, so its matches
-//     stay sorted and equal a solo cv_scan of the image.
+//   - The engine never waits for the GPU. Two scan batches are in flight at once, each on its
+//     own stream: a batch's scan and offset pass are launched and their counts copied back;
+//     once the counts have landed (an event query) its expansion and the copy of its matches
+//     are launched; once those have landed the batch is retired. Meanwhile the engine keeps
+//     issuing copies and launches the next batch's scan, so one batch's expansion and readback
+//     overlap the next one's scan.
+//   - Batches retire in the order they were launched, and a unit's sorted matches are appended
+//     to its request then; a request is complete when its last unit has been retired. Units of
+//     one request are always scanned in order, so its matches stay sorted and equal a solo
+//     cv_scan of the image.
 // One engine thread per server; cv_submit and cv_poll may be called from any thread.
 #include <stddef.h>
 #include <stdlib.h>
@@ -65,6 +72,40 @@ struct Request {
   cv_result* result = nullptr;
 };
 
+// One scan batch in flight: its stream, events and per-batch device and pinned buffers (grown
+// on demand), and the units it scans.
+struct ScanBatch {
+  enum { kFree = 0, kCounting = 1, kExpanding = 2 };
+  int state = kFree;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t counts_ready = nullptr;  // offsets, total and status are on the host
+  cudaEvent_t matches_ready = nullptr;  // the matches are on the host
+  struct Ref {
+    Request* r;
+    size_t unit;
+  };
+  std::vector<Ref> refs;  // segment k scans refs[k]
+  size_t nseg = 0;
+  uint64_t n_out = 0;
+  uint64_t total = 0;
+  uint64_t cap_tiles = 0, cap_segs = 0, cap_out = 0;
+  Segment* segs_d = nullptr;
+  uint4* hit_rec = nullptr;
+  uint32_t* tile_nhit = nullptr;
+  uint64_t* tile_ntrip = nullptr;
+  uint64_t* tile_off = nullptr;
+  uint64_t* off_scratch = nullptr;
+  uint64_t* counters_d = nullptr;  // seg_off[nseg], total, status
+  uint64_t* counters_h = nullptr;
+  MatchOut* out_d = nullptr;
+  MatchOut* out_h = nullptr;
+
+  int ensure_buffers(uint64_t tiles, uint64_t segs, uint64_t out);
+  void release();
+};
+
+constexpr int kBatchesInFlight = 2;
+
 }  // namespace
 
 struct cv_server {
@@ -82,19 +123,8 @@ struct cv_server {
   std::vector<cudaStream_t> copy_streams;
   std::vector<cudaEvent_t> slot_event;  // copy of the unit in the slot finished
   std::vector<int> free_slots;
-  cudaStream_t stream = nullptr;  // scans
-  // per-iteration device/pinned buffers, grown on demand
-  uint64_t cap_tiles = 0, cap_segs = 0, cap_out = 0;
-  Segment* segs_d = nullptr;
-  uint4* hit_rec = nullptr;
-  uint32_t* tile_nhit = nullptr;
-  uint64_t* tile_ntrip = nullptr;
-  uint64_t* tile_off = nullptr;
-  uint64_t* off_scratch = nullptr;
-  uint64_t* counters_d = nullptr;
-  uint64_t* counters_h = nullptr;
-  MatchOut* out_d = nullptr;
-  MatchOut* out_h = nullptr;
+  ScanBatch batch[kBatchesInFlight];
+  std::deque<int> in_flight;  // batches not yet retired, in launch order
 
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -118,11 +148,16 @@ struct cv_server {
 
   void run();
   int iterate(bool* did_work);
-  int ensure_buffers(uint64_t tiles, uint64_t segs, uint64_t out);
+  int issue_copies(const std::vector<Request*>& work);
+  int launch_scan(ScanBatch& b, const std::vector<Request*>& work, bool* launched);
+  int launch_expand_of(ScanBatch& b);
+  void retire(ScanBatch& b);
   void finish(Request* r);
 };
 
-int cv_server::ensure_buffers(uint64_t tiles, uint64_t segs, uint64_t out) {
+namespace {
+
+int ScanBatch::ensure_buffers(uint64_t tiles, uint64_t segs, uint64_t out) {
   if (tiles > cap_tiles || !hit_rec) {
     uint64_t c = std::max<uint64_t>(tiles, cap_tiles * 2);
     for (void* p : {(void*)hit_rec, (void*)tile_nhit, (void*)tile_ntrip, (void*)tile_off, (void*)off_scratch})
@@ -156,6 +191,22 @@ int cv_server::ensure_buffers(uint64_t tiles, uint64_t segs, uint64_t out) {
   return CV_OK;
 }
 
+void ScanBatch::release() {
+  if (stream) {
+    cudaStreamSynchronize(stream);
+    cudaStreamDestroy(stream);
+  }
+  if (counts_ready) cudaEventDestroy(counts_ready);
+  if (matches_ready) cudaEventDestroy(matches_ready);
+  for (void* p : {(void*)segs_d, (void*)hit_rec, (void*)tile_nhit, (void*)tile_ntrip, (void*)tile_off,
+                  (void*)off_scratch, (void*)counters_d, (void*)out_d})
+    if (p) cudaFree(p);
+  if (counters_h) cudaFreeHost(counters_h);
+  if (out_h) cudaFreeHost(out_h);
+}
+
+}  // namespace
+
 void cv_server::finish(Request* r) {
   r->done = true;
   r->done_at = Clock::now();
@@ -173,23 +224,10 @@ void cv_server::finish(Request* r) {
   }
 }
 
-// One engine iteration: admit, issue copies, scan every unit that has landed.
-int cv_server::iterate(bool* did_work) {
-  NvtxRange nvtx_range("cv.server.iteration");
-  *did_work = false;
-  std::vector<Request*> work;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    while (!pending.empty() && live.size() < max_live) {
-      live.push_back(pending.front());
-      pending.pop_front();
-    }
-    work = live;
-  }
-  if (work.empty()) return CV_OK;
-  // copies: round robin over live requests, one unit per request per pass, while slots and the
-  // copy cap last; the request with the fewest bytes left to copy goes first, so a small request
-  // is not queued behind the rest of a large one
+// Copies: round robin over live requests, one unit per request per pass, while slots and the
+// copy cap last; the request with the fewest bytes left to copy goes first, so a small request
+// is not queued behind the rest of a large one.
+int cv_server::issue_copies(const std::vector<Request*>& work) {
   std::vector<Request*> order;
   for (Request* r : work)
     if (!r->device && r->next_copy < r->units.size()) order.push_back(r);
@@ -218,18 +256,20 @@ int cv_server::iterate(bool* did_work) {
       issued = true;
     }
   }
-  // gather the units that are on the device, in order per request
+  return CV_OK;
+}
+
+// Gather every unit that is on the device (in order per request) into batch b and launch its
+// scan, offset pass and the copy of its counts; *launched is false when no unit was ready.
+int cv_server::launch_scan(ScanBatch& b, const std::vector<Request*>& work, bool* launched) {
+  *launched = false;
   Job job;
-  struct Ref {
-    Request* r;
-    size_t unit;
-  };
-  std::vector<Ref> refs;
   int n_ops = 0;
   const ScanCfg& cfg = scan_configs(&n_ops)[cfg_i];
   int live_in_batch = 0;
   job.maps.push_back(arena_map);
   job.map_base.push_back((uintptr_t)arena);
+  b.refs.clear();
   for (Request* r : work) {
     bool any = false;
     while (r->next_scan < r->units.size()) {
@@ -240,83 +280,97 @@ int cv_server::iterate(bool* did_work) {
         if (q == cudaErrorNotReady) break;
         if (q != cudaSuccess) return cuda_fail(q);
         copy_queued -= u.n_sectors * kSector;  // each unit is gathered once
-        Segment s;
-        s.n_sectors = u.n_sectors;
-        s.tile_base = job.n_tiles;
-        s.sector_base = u.first_sector;
-        s.row_base = (uint64_t)u.slot * unit_sectors;
-        s.image = (uint32_t)refs.size();
-        s.map = 0;
-        s.bytes = arena + (uint64_t)u.slot * unit_bytes;
-        job.segs.push_back(s);
+        Segment sg;
+        sg.n_sectors = u.n_sectors;
+        sg.tile_base = job.n_tiles;
+        sg.sector_base = u.first_sector;
+        sg.row_base = (uint64_t)u.slot * unit_sectors;
+        sg.image = (uint32_t)b.refs.size();
+        sg.map = 0;
+        sg.bytes = arena + (uint64_t)u.slot * unit_bytes;
+        job.segs.push_back(sg);
         job.n_tiles += (u.n_sectors + cfg.T - 1) / cfg.T;
         job.n_sectors += u.n_sectors;
       } else {
         const size_t before = job.segs.size();
         CV_TRY(job.add(ctx, cfg, r->data + u.first_sector * kSector, u.n_sectors, u.first_sector,
-                       (uint32_t)refs.size(), true));
+                       (uint32_t)b.refs.size(), true));
         if (job.segs.size() != before + 1) return CV_EINVAL;  // units never exceed a segment
       }
-      refs.push_back(Ref{r, r->next_scan});
+      b.refs.push_back(ScanBatch::Ref{r, r->next_scan});
       r->next_scan++;
       any = true;
     }
     live_in_batch += any ? 1 : 0;
   }
-  if (refs.empty()) return CV_OK;
-  *did_work = true;
-  const size_t nseg = job.segs.size();
-  const uint64_t n_out = job.n_tiles * (uint64_t)(cfg.T / 32);
-  CV_TRY(ensure_buffers(n_out, nseg, 0));
-  CV_CUDA(cudaMemcpyAsync(segs_d, job.segs.data(), nseg * sizeof(Segment), cudaMemcpyHostToDevice, stream));
-  uint32_t* status = (uint32_t*)(counters_d + nseg + 1);
-  CV_CUDA(cudaMemsetAsync(status, 0, 8, stream));
+  if (b.refs.empty()) return CV_OK;
+  *launched = true;
+  b.nseg = job.segs.size();
+  b.n_out = job.n_tiles * (uint64_t)(cfg.T / 32);
+  CV_TRY(b.ensure_buffers(b.n_out, b.nseg, 0));
+  CV_CUDA(cudaMemcpyAsync(b.segs_d, job.segs.data(), b.nseg * sizeof(Segment), cudaMemcpyHostToDevice, b.stream));
+  uint32_t* status = (uint32_t*)(b.counters_d + b.nseg + 1);
+  CV_CUDA(cudaMemsetAsync(status, 0, 8, b.stream));
   ScanParams p;
   memset(&p, 0, sizeof p);
   p.tab = tab;
-  p.hit_rec = hit_rec;
-  p.tile_nhit = tile_nhit;
-  p.tile_ntrip = tile_ntrip;
+  p.hit_rec = b.hit_rec;
+  p.tile_nhit = b.tile_nhit;
+  p.tile_ntrip = b.tile_ntrip;
   p.status = status;
-  CV_TRY(launch_range(ctx, cfg_i, false, job, segs_d, 0, nseg, p, stream));
-  CV_CUDA((cudaError_t)launch_tile_offsets(tile_ntrip, n_out, tile_off, segs_d, (uint32_t)nseg,
-                                           (uint32_t)(cfg.T / 32), counters_d, counters_d + nseg, off_scratch,
-                                           stream));
-  CV_CUDA(cudaMemcpyAsync(counters_h, counters_d, (nseg + 2) * 8, cudaMemcpyDeviceToHost, stream));
-  CV_CUDA(cudaStreamSynchronize(stream));
-  const uint64_t total = counters_h[nseg];
-  const uint32_t st0 = (uint32_t)counters_h[nseg + 1];
+  CV_TRY(launch_range(ctx, cfg_i, false, job, b.segs_d, 0, b.nseg, p, b.stream));
+  CV_CUDA((cudaError_t)launch_tile_offsets(b.tile_ntrip, b.n_out, b.tile_off, b.segs_d, (uint32_t)b.nseg,
+                                           (uint32_t)(cfg.T / 32), b.counters_d, b.counters_d + b.nseg,
+                                           b.off_scratch, b.stream));
+  CV_CUDA(cudaMemcpyAsync(b.counters_h, b.counters_d, (b.nseg + 2) * 8, cudaMemcpyDeviceToHost, b.stream));
+  CV_CUDA(cudaEventRecord(b.counts_ready, b.stream));
+  b.state = ScanBatch::kCounting;
+  st.iterations++;
+  st.units += b.refs.size();
+  live_sum += live_in_batch;
+  return CV_OK;
+}
+
+// The counts of batch b are on the host: check its status and launch its expansion and the copy
+// of its matches.
+int cv_server::launch_expand_of(ScanBatch& b) {
+  b.total = b.counters_h[b.nseg];
+  const uint32_t st0 = (uint32_t)b.counters_h[b.nseg + 1];
   if (st0 & kStTimeout) return CV_ETIMEOUT;
   if (st0) return CV_ECORRUPT;
-  std::vector<uint64_t> seg_off(counters_h, counters_h + nseg + 1);
-  if (total) {
-    CV_TRY(ensure_buffers(0, 0, total));
-    CV_CUDA((cudaError_t)launch_expand(cfg, hit_rec, tile_nhit, tile_off, n_out, segs_d, (uint32_t)nseg, tab, out_d,
-                                       cap_out, status, ctx->sms, stream));
-    CV_CUDA(cudaMemcpyAsync(out_h, out_d, total * sizeof(MatchOut), cudaMemcpyDeviceToHost, stream));
-    CV_CUDA(cudaStreamSynchronize(stream));
+  if (b.total) {
+    int n_ops = 0;
+    const ScanCfg& cfg = scan_configs(&n_ops)[cfg_i];
+    CV_TRY(b.ensure_buffers(0, 0, b.total));
+    uint32_t* status = (uint32_t*)(b.counters_d + b.nseg + 1);
+    CV_CUDA((cudaError_t)launch_expand(cfg, b.hit_rec, b.tile_nhit, b.tile_off, b.n_out, b.segs_d,
+                                       (uint32_t)b.nseg, tab, b.out_d, b.cap_out, status, ctx->sms, b.stream));
+    CV_CUDA(cudaMemcpyAsync(b.out_h, b.out_d, b.total * sizeof(MatchOut), cudaMemcpyDeviceToHost, b.stream));
   }
-  // scan and expand (which rereads units for byte confirmation) are done: the slots are free
-  for (const Ref& f : refs) {
-    Unit& u = f.r->units[f.unit];
+  CV_CUDA(cudaEventRecord(b.matches_ready, b.stream));
+  b.state = ScanBatch::kExpanding;
+  return CV_OK;
+}
+
+// Batch b's matches are on the host: free its arena slots (scan and expand, which rereads units
+// for byte confirmation, are done) and append each unit's matches to its request.
+void cv_server::retire(ScanBatch& b) {
+  std::vector<Request*> completed;
+  for (size_t k = 0; k < b.refs.size(); k++) {
+    Request* r = b.refs[k].r;
+    Unit& u = r->units[b.refs[k].unit];
     if (u.slot >= 0) {
       free_slots.push_back(u.slot);
       bytes_in_flight -= u.n_sectors * kSector;
       u.slot = -1;
     }
     u.scanned = true;
+    const uint64_t lo = b.counters_h[k], hi = (k + 1 < b.nseg) ? b.counters_h[k + 1] : b.total;
+    r->matches.insert(r->matches.end(), b.out_h + lo, b.out_h + hi);
+    if (b.refs[k].unit + 1 == r->units.size()) completed.push_back(r);
   }
-  // distribute: segment k belongs to refs[k] (one segment per unit)
-  std::vector<Request*> completed;
-  for (size_t k = 0; k < refs.size(); k++) {
-    Request* r = refs[k].r;
-    const uint64_t a = seg_off[k], b = (k + 1 < nseg) ? seg_off[k + 1] : total;
-    r->matches.insert(r->matches.end(), out_h + a, out_h + b);
-    if (refs[k].unit + 1 == r->units.size()) completed.push_back(r);
-  }
-  st.iterations++;
-  st.units += refs.size();
-  live_sum += live_in_batch;
+  b.refs.clear();
+  b.state = ScanBatch::kFree;
   {
     std::lock_guard<std::mutex> lk(mu);
     for (Request* r : completed) {
@@ -325,6 +379,55 @@ int cv_server::iterate(bool* did_work) {
     }
   }
   if (!completed.empty()) cv_done.notify_all();
+}
+
+// One engine iteration: admit, issue copies, retire the oldest batch when its matches have
+// landed, start the expansion of every batch whose counts have landed, and launch a scan of the
+// units that have landed into a free batch. Nothing here waits for the GPU.
+int cv_server::iterate(bool* did_work) {
+  NvtxRange nvtx_range("cv.server.iteration");
+  *did_work = false;
+  std::vector<Request*> work;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    while (!pending.empty() && live.size() < max_live) {
+      live.push_back(pending.front());
+      pending.pop_front();
+    }
+    work = live;
+  }
+  if (work.empty() && in_flight.empty()) return CV_OK;
+  CV_TRY(issue_copies(work));
+  while (!in_flight.empty()) {
+    ScanBatch& b = batch[in_flight.front()];
+    if (b.state != ScanBatch::kExpanding) break;
+    const cudaError_t q = cudaEventQuery(b.matches_ready);
+    if (q == cudaErrorNotReady) break;
+    if (q != cudaSuccess) return cuda_fail(q);
+    in_flight.pop_front();
+    retire(b);
+    *did_work = true;
+  }
+  for (int i : in_flight) {
+    ScanBatch& b = batch[i];
+    if (b.state != ScanBatch::kCounting) continue;
+    const cudaError_t q = cudaEventQuery(b.counts_ready);
+    if (q == cudaErrorNotReady) continue;
+    if (q != cudaSuccess) return cuda_fail(q);
+    CV_TRY(launch_expand_of(b));
+    *did_work = true;
+  }
+  for (int i = 0; i < kBatchesInFlight; i++) {
+    ScanBatch& b = batch[i];
+    if (b.state != ScanBatch::kFree) continue;
+    bool launched = false;
+    CV_TRY(launch_scan(b, work, &launched));
+    if (launched) {
+      in_flight.push_back(i);
+      *did_work = true;
+    }
+    break;  // one new batch per iteration
+  }
   return CV_OK;
 }
 
@@ -351,9 +454,9 @@ void cv_server::run() {
       return;
     }
     std::unique_lock<std::mutex> lk(mu);
-    if (stopping && live.empty() && pending.empty()) return;
+    if (stopping && live.empty() && pending.empty() && in_flight.empty()) return;
     if (!did) {
-      if (live.empty() && pending.empty()) {
+      if (live.empty() && pending.empty() && in_flight.empty()) {
         cv_work.wait(lk, [&] { return stopping || !pending.empty(); });
       } else {
         lk.unlock();
@@ -408,7 +511,11 @@ int cv_server_create(const cv_master* m, const cv_server_opts* opts, cv_server**
   auto body = [&]() -> int {
     CV_CUDA(cudaMalloc((void**)&s->arena, slots * unit));
     CV_TRY(make_tmap(ctx, cfgs[cfg_i], s->arena, slots * unit / kSector, &s->arena_map));
-    CV_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    for (ScanBatch& b : s->batch) {
+      CV_CUDA(cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking));
+      CV_CUDA(cudaEventCreateWithFlags(&b.counts_ready, cudaEventDisableTiming));
+      CV_CUDA(cudaEventCreateWithFlags(&b.matches_ready, cudaEventDisableTiming));
+    }
     for (uint32_t k = 0; k < n_copy; k++) {
       cudaStream_t cs;
       CV_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -541,17 +648,12 @@ void cvk_server_free(void* h) {
     if (kv.second->result) cv_free(kv.second->result);
     delete kv.second;
   }
-  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (ScanBatch& b : s->batch) b.release();
   for (cudaStream_t cs : s->copy_streams) {
     cudaStreamSynchronize(cs);
     cudaStreamDestroy(cs);
   }
   for (cudaEvent_t e : s->slot_event) cudaEventDestroy(e);
-  if (s->stream) cudaStreamDestroy(s->stream);
-  for (void* p : {(void*)s->arena, (void*)s->segs_d, (void*)s->hit_rec, (void*)s->tile_nhit, (void*)s->tile_ntrip,
-                  (void*)s->tile_off, (void*)s->off_scratch, (void*)s->counters_d, (void*)s->out_d})
-    if (p) cudaFree(p);
-  if (s->counters_h) cudaFreeHost(s->counters_h);
-  if (s->out_h) cudaFreeHost(s->out_h);
+  if (s->arena) cudaFree(s->arena);
   delete s;
 }

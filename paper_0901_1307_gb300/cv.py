@@ -41,7 +41,7 @@ EXPORTS = ("cv_master_build", "cv_master_get_info", "cv_scan", "cv_matches", "cv
            "cv_kernel_config_name", "cv_scan_noalloc", "cv_batch_create", "cv_batch_run", "cv_batch_wait",
            "cv_batch_matches", "cv_batch_get_info", "cv_server_create", "cv_submit", "cv_poll",
            "cv_server_get_stats", "cv_int_peak", "cv_selftest_wait_timeout", "cv_master_save", "cv_master_load",
-           "cv_probe_profile")
+           "cv_probe_profile", "cv_sector_signatures", "cv_window_signatures")
 CV_EAGAIN = -9
 CV_EIO = -10
 CV_BATCH_BLOOM_AUTO = 0
@@ -82,7 +82,7 @@ class cv_master_info(ctypes.Structure):
 class cv_scan_stats(ctypes.Structure):
     _fields_ = [("sectors", ctypes.c_uint64), ("matches", ctypes.c_uint64), ("hit_sectors", ctypes.c_uint64),
                 ("kernel_ms", ctypes.c_float), ("total_ms", ctypes.c_float), ("kernel_launches", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("reserved", ctypes.c_uint32), ("confirm_rejected", ctypes.c_uint64)]
 
 
 class cv_probe_stats(ctypes.Structure):
@@ -160,6 +160,10 @@ def load(path: str = LIB_PATH):
         lib.cv_last_cuda_error.restype = i32
         lib.cv_sector_digests.argtypes = [vp, u64, vp, vp, vp]
         lib.cv_sector_digests.restype = i32
+        lib.cv_sector_signatures.argtypes = [vp, u64, u32, vp, vp, vp]
+        lib.cv_sector_signatures.restype = i32
+        lib.cv_window_signatures.argtypes = [vp, u64, u32, vp, vp]
+        lib.cv_window_signatures.restype = i32
         lib.cv_kernel_config_count.argtypes = []
         lib.cv_kernel_config_count.restype = i32
         lib.cv_kernel_config_name.argtypes = [i32]
@@ -407,6 +411,19 @@ def sector_digests(in_ptr: int, n_sectors: int, out_ptr: int, trivial_ptr: int =
     """cv_sector_digests: MD5 of n_sectors device sectors into device memory (asynchronous)."""
     _check(load().cv_sector_digests(in_ptr, n_sectors, out_ptr, trivial_ptr or None, _stream(stream)),
            "cv_sector_digests")
+
+
+def sector_signatures(in_ptr: int, n_sectors: int, signature: int, out_ptr: int, trivial_ptr: int = 0,
+                      stream=None) -> None:
+    """cv_sector_signatures: 16 bytes per device sector under any CV_SIG_* (asynchronous)."""
+    _check(load().cv_sector_signatures(in_ptr, n_sectors, signature, out_ptr, trivial_ptr or None, _stream(stream)),
+           "cv_sector_signatures")
+
+
+def window_signatures(in_ptr: int, n_bytes: int, signature: int, out_ptr: int, stream=None) -> None:
+    """cv_window_signatures: 16 bytes per 64-byte window at a 4-byte offset (asynchronous)."""
+    _check(load().cv_window_signatures(in_ptr, n_bytes, signature, out_ptr, _stream(stream)),
+           "cv_window_signatures")
 
 
 def scan_noalloc(master: Master, image, out, out_capacity: int, stream=None, check: bool = True):

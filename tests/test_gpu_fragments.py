@@ -126,10 +126,25 @@ def test_djb2_collisions_are_confirmed(cv):
             img[pos:pos + FRAG] = col
             img[pos + 1000:pos + 1000 + FRAG] = frag
     want = oracle.frag_match(img, logos)
+    # candidates the confirmation must drop: windows whose djb2 equals a kept fragment's while
+    # their bytes differ
+    wsig = oracle.window_signatures(img, 2)[:, :8].copy().view("<u8").ravel()
+    frags = {}
+    for lg in logos:
+        for j in range(lg.size // FRAG):
+            fr = lg[j * FRAG:(j + 1) * FRAG]
+            if not oracle.fragment_trivial(fr):
+                frags.setdefault(oracle.djb2_64(fr), []).append(fr)
+    rejected = 0
+    for k in np.nonzero(np.isin(wsig, np.array(list(frags), dtype=np.uint64)))[0]:
+        w = img[4 * k:4 * k + FRAG]
+        rejected += sum(int(not np.array_equal(w, fr)) for fr in frags[int(wsig[k])])
+    assert rejected >= 35
     with frag_master(cv, logos, 2) as m:
         d, keep = dev(img)
         with cv.scan(m, [d]) as r:
             assert np.array_equal(r.matches(0), want)
+            assert r.stats()["confirm_rejected"] == rejected
     assert want.size == sum(len(range(0, 20, 3)) for _ in logos)
 
 

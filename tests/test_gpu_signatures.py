@@ -44,17 +44,43 @@ def workload_with_collisions(seed):
     return img, files
 
 
+def expected_rejected(img, files, sig):
+    """Candidates the byte confirmation must drop: (disk sector, kept master sector) pairs whose
+    signatures (the oracle's) are equal while their bytes differ."""
+    if sig not in (2, 3):
+        return 0
+    by_sig = {}
+    for f in files:
+        secs = f[: f.size // SECTOR * SECTOR].reshape(-1, SECTOR)
+        sigs = oracle.signatures(secs, sig)[:, :8].copy().view("<u8").ravel()
+        for s, h in zip(secs, sigs):
+            if not oracle.sector_trivial(s):
+                by_sig.setdefault(int(h), []).append(s)
+    disk = img[: img.size // SECTOR * SECTOR].reshape(-1, SECTOR)
+    dsig = oracle.signatures(disk, sig)[:, :8].copy().view("<u8").ravel()
+    n = 0
+    for d, h in zip(disk, dsig):
+        for s in by_sig.get(int(h), ()):
+            n += int(not np.array_equal(d, s))
+    return n
+
+
 @pytest.mark.parametrize("sig", SIGS)
 def test_scan_signature_equals_definition(cv, sig):
     img, files = workload_with_collisions(70 + sig)
     want = oracle.match_brute(img, files)
     assert np.array_equal(oracle.match_sig(img, files, sig), want)
+    rejected = expected_rejected(img, files, sig)
+    if sig in (2, 3):
+        assert rejected >= 35  # the planted collisions (a few overwritten by later plants) reach it
     with cv.master_build(files, signature=sig) as m:
         assert m.info()["signature"] == sig
         with cv.scan(m, [torch.from_numpy(img).cuda()]) as r:
             assert np.array_equal(r.matches(0), want)
+            assert r.stats()["confirm_rejected"] == rejected
         with cv.scan(m, [img], chunk_bytes=1 << 20) as r:  # host image
             assert np.array_equal(r.matches(0), want)
+            assert r.stats()["confirm_rejected"] == rejected
 
 
 @pytest.mark.parametrize("sig", SIGS)

@@ -168,3 +168,55 @@ def test_match_sig_equals_definition(sig, seed):
     image = np.concatenate([image[: image.size // SECTOR * SECTOR], djb2_collision(m, 10), crc_collision(m, 99), m])
     want = py_match(image.tobytes(), [f.tobytes() for f in files])
     assert as_list(oracle.match_sig(image, files, sig)) == want
+
+
+def test_batch_signatures_equal_single_ones():
+    rng = np.random.default_rng(21)
+    data = rng.integers(0, 256, SECTOR * 37, dtype=np.uint8)
+    data[SECTOR * 3: SECTOR * 4] = 0
+    data[SECTOR * 5: SECTOR * 6] = 0x41
+    for sig in (oracle.SIG_MD5, oracle.SIG_MD5_NOPAD, oracle.SIG_DJB2_64, oracle.SIG_CRC64):
+        got = oracle.signatures(np.concatenate([data, data[:100]]), sig)  # a partial tail is ignored
+        assert got.shape == (37, 16)
+        for i in range(37):
+            assert got[i].tobytes() == oracle.signature(data[SECTOR * i: SECTOR * (i + 1)], sig)
+
+
+def test_md5_blocks_then_rfc_padding_is_md5():
+    # the RFC's padding for a 64-byte message: 0x80, zeros, then the bit length 512 as a 64-bit
+    # little-endian integer, all in one more block
+    pad = np.zeros(64, np.uint8)
+    pad[0] = 0x80
+    pad[56:64] = np.frombuffer((512).to_bytes(8, "little"), np.uint8)
+    rng = np.random.default_rng(22)
+    for _ in range(30):
+        w = rng.integers(0, 256, 64, dtype=np.uint8)
+        assert oracle.md5_blocks(np.concatenate([w, pad])) == hashlib.md5(w.tobytes()).digest()
+        assert oracle.md5_blocks(w) != hashlib.md5(w.tobytes()).digest()
+    x = rng.integers(0, 256, SECTOR, dtype=np.uint8)
+    assert oracle.md5_blocks(x) == oracle.md5_nopad(x)
+
+
+def _djb2_py(b: bytes) -> int:
+    h = 5381
+    for c in b:
+        h = (h * 33 + c) & M64
+    return h
+
+
+def test_window_signatures_follow_their_definitions():
+    rng = np.random.default_rng(23)
+    img = rng.integers(0, 256, 64 * 5 + 23, dtype=np.uint8)  # windows do not end on the grid
+    img[100:180] = 0
+    n_win = (img.size - 64) // 4 + 1
+    md5 = oracle.window_signatures(img, oracle.SIG_MD5)
+    nop = oracle.window_signatures(img, oracle.SIG_MD5_NOPAD)
+    djb = oracle.window_signatures(img, oracle.SIG_DJB2_64)
+    assert md5.shape == nop.shape == djb.shape == (n_win, 16)
+    for k in range(n_win):
+        w = img[4 * k: 4 * k + 64].tobytes()
+        assert md5[k].tobytes() == hashlib.md5(w).digest()
+        assert nop[k].tobytes() == oracle.md5_blocks(np.frombuffer(w, np.uint8))
+        assert djb[k].tobytes() == _djb2_py(w).to_bytes(8, "little") + bytes(8)
+    assert oracle.window_signatures(img[:63], oracle.SIG_MD5).shape == (0, 16)
+    assert oracle.window_signatures(img[:64], oracle.SIG_DJB2_64).shape == (1, 16)
