@@ -333,23 +333,35 @@ int cv_selftest_wait_timeout(uint32_t timeout_us, void* stream);
  *
  * Images must be device buffers (16-byte aligned), borrowed for the life of the batch: each run
  * reads their current contents. Matches of the last run stay in device memory owned by the
- * batch. With autotune set, cv_batch_create times every kernel configuration, with and without
- * the Bloom prefilter, on the batch itself and keeps the fastest; the choice is cached per
- * process and, when tune_cache names a file, in that file (one line per workload key).
+ * batch. With autotune set, cv_batch_create times on the batch itself every kernel
+ * configuration x table layout x Bloom use, and keeps the fastest: the layouts are the master's
+ * own and, for a CV_LAYOUT_HASH master, a sorted copy (CV_LAYOUT_SORTED, Section 4's binary
+ * search); Bloom use is off, or on with the master's filter, or, for a master without one, with
+ * a 16-bit-per-key filter the batch builds. A copy or filter the choice uses is owned by the
+ * batch (its device memory is freed with it). The choice is cached per process and, when
+ * tune_cache names a file, in that file (one line per workload key). cv_batch_get_info reports
+ * the configuration, layout and Bloom use in effect. Section 3.2 notes that the best
+ * concurrency has to be found again for every GPU generation.
  */
 typedef struct cv_batch cv_batch;
 
 #define CV_BATCH_BLOOM_AUTO 0u /* use the table's Bloom filter when it has one */
 #define CV_BATCH_BLOOM_OFF 1u  /* probe the table directly */
+#define CV_BATCH_BLOOM_ON 2u   /* the table's filter, or for a table without one a 16-bit-per-key
+                                  filter the batch builds and owns */
 
 typedef struct {
   uint32_t struct_size;     /* sizeof(cv_batch_opts) */
-  uint32_t autotune;        /* 1: tune the kernel configuration and Bloom use on this batch */
+  uint32_t autotune;        /* 1: tune kernel configuration, table layout and Bloom use on this batch */
   void* stream;             /* cudaStream_t for set-up and tuning */
   uint64_t match_capacity;  /* output room in matches; 0 = size it from one scan at set-up */
   uint32_t kernel_config;   /* 0 = default (or tuned); k + 1 = configuration k */
-  uint32_t bloom;           /* CV_BATCH_BLOOM_AUTO / CV_BATCH_BLOOM_OFF (ignored when tuning) */
+  uint32_t bloom;           /* CV_BATCH_BLOOM_* (ignored when tuning) */
   const char* tune_cache;   /* file for tuned choices, or NULL */
+  uint32_t sorted_copy;     /* 1: scan a sorted copy of a CV_LAYOUT_HASH master (the batch builds
+                               and owns it; ignored when tuning). The size without this field and
+                               the next (40 bytes on LP64) is accepted and means 0. */
+  uint32_t reserved;        /* 0 */
 } cv_batch_opts;
 
 typedef struct {
@@ -360,7 +372,7 @@ typedef struct {
   uint32_t kernel_launches;   /* kernel nodes per run */
   uint32_t tensor_maps;
   uint32_t segments;
-  uint32_t reserved;
+  uint32_t layout;            /* CV_LAYOUT_HASH or CV_LAYOUT_SORTED: the table layout scanned */
   uint64_t sectors;
   uint64_t match_capacity;
   float scan_ms;              /* device time of the scan launch(es) of the last finished run */

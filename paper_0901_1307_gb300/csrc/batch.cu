@@ -5,10 +5,14 @@
 // offset pass and one expand pass produce every image's sorted matches. The whole sequence is
 // captured once and replayed with a single graph launch per run.
 //
-// An optional autotuner times every kernel configuration (tile rows, staging width, ring
-// stages, pipe split of the MD5 additions) with and without the Bloom prefilter on the batch
-// itself and keeps the fastest; results are cached in-process and, when a cache file is named,
-// on disk (one line per key).
+// An optional autotuner times, on the batch itself, every kernel configuration (tile rows,
+// sectors per thread, staging width, ring stages, pipe split of the MD5 additions) x table layout
+// (the master's; for a hash-layout master also a sorted copy, Section 4's binary search) x Bloom
+// prefilter (off; on with the master's filter, or with one the batch builds when the master has
+// none), and keeps the fastest; results are cached in-process and, when a cache file is named,
+// on disk (one line per key). Section 3.2 notes that the best concurrency has to be found again
+// on every GPU generation.
+#include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -98,7 +102,10 @@ int enqueue_run(DevCtx* ctx, int cfg_i, const TableView& tab, const Job& job, co
 
 // ------------------------------------------------------------------------- tune cache
 std::mutex g_tune_mutex;
-std::map<std::string, std::pair<int, int>> g_tune;  // key -> (config, bloom)
+struct TuneChoice {
+  int cfg, bloom, layout;
+};
+std::map<std::string, TuneChoice> g_tune;  // key -> choice
 
 // table_kind: signature, layout and position keying of the table (they change the probe's cost).
 std::string tune_key(const char* gpu, int sms, uint64_t sectors, uint32_t images, uint64_t unique, bool bloom_avail,
@@ -111,18 +118,23 @@ std::string tune_key(const char* gpu, int sms, uint64_t sectors, uint32_t images
     }
     return b;
   };
+  // the device name goes in with its blanks replaced: a cache line is blank-separated
+  std::string name(gpu);
+  for (char& ch : name)
+    if (ch == ' ' || ch == '\t') ch = '_';
   char buf[256];
-  snprintf(buf, sizeof buf, "%s|%d|s%d|i%d|u%d|b%d|t%u", gpu, sms, lg(sectors), lg(images), lg(unique),
+  snprintf(buf, sizeof buf, "%s|%d|s%d|i%d|u%d|b%d|t%u", name.c_str(), sms, lg(sectors), lg(images), lg(unique),
            bloom_avail ? 1 : 0, table_kind);
   return buf;
 }
 
-bool tune_lookup(const std::string& key, const char* path, int* cfg, int* bloom) {
+// Cache lines are "key config_name bloom layout"; lines written before the layout was tuned
+// ("key config_name bloom") mean the master's own layout (-1).
+bool tune_lookup(const std::string& key, const char* path, TuneChoice* c) {
   std::lock_guard<std::mutex> lk(g_tune_mutex);
   auto it = g_tune.find(key);
   if (it != g_tune.end()) {
-    *cfg = it->second.first;
-    *bloom = it->second.second;
+    *c = it->second;
     return true;
   }
   if (!path) return false;
@@ -132,31 +144,31 @@ bool tune_lookup(const std::string& key, const char* path, int* cfg, int* bloom)
   bool found = false;
   while (fgets(line, sizeof line, f)) {
     char k[300], name[64];
-    int bl;
-    if (sscanf(line, "%299[^ ] %63s %d", k, name, &bl) == 3 && key == k) {
+    int bl, lay = -1;
+    const int got = sscanf(line, "%299[^ ] %63s %d %d", k, name, &bl, &lay);
+    if (got >= 3 && key == k) {
       int n;
-      const ScanCfg* c = scan_configs(&n);
+      const ScanCfg* cf = scan_configs(&n);
       for (int i = 0; i < n; i++)
-        if (strcmp(c[i].name, name) == 0) {
-          *cfg = i;
-          *bloom = bl;
+        if (strcmp(cf[i].name, name) == 0) {
+          *c = TuneChoice{i, bl, got == 4 ? lay : -1};
           found = true;
         }
     }
   }
   fclose(f);
-  if (found) g_tune[key] = {*cfg, *bloom};
+  if (found) g_tune[key] = *c;
   return found;
 }
 
-void tune_store(const std::string& key, const char* path, int cfg, int bloom) {
+void tune_store(const std::string& key, const char* path, const TuneChoice& c) {
   std::lock_guard<std::mutex> lk(g_tune_mutex);
-  g_tune[key] = {cfg, bloom};
+  g_tune[key] = c;
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
   int n;
-  fprintf(f, "%s %s %d\n", key.c_str(), scan_configs(&n)[cfg].name, bloom);
+  fprintf(f, "%s %s %d %d\n", key.c_str(), scan_configs(&n)[c.cfg].name, c.bloom, c.layout);
   fclose(f);
 }
 
@@ -167,7 +179,11 @@ struct cv_batch {
   int dev;
   int cfg_i;
   int bloom;
+  int layout;  // kLayout* scanned
   TableView tab;
+  void* own_slots = nullptr;  // the batch's sorted copy of a hash table (records, key words)
+  void* own_keys0 = nullptr;
+  void* own_bloom = nullptr;  // the batch's Bloom filter for a master without one
   Job job;
   uint32_t n_images;
   std::vector<size_t> first_seg;  // n_images + 1
@@ -180,7 +196,6 @@ struct cv_batch {
   int launches;
   bool ran;
   bool tuned;
-  float tune_ms[64][2];
 };
 
 extern "C" {
@@ -189,7 +204,8 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
                     cv_batch** out) {
   if (!m || !out || (n_images && !images)) return CV_EINVAL;
   *out = nullptr;
-  if (opts && opts->struct_size < sizeof(cv_batch_opts)) return CV_EINVAL;
+  if (opts && opts->struct_size < offsetof(cv_batch_opts, sorted_copy)) return CV_EINVAL;
+  const bool want_sorted = opts && opts->struct_size >= sizeof(cv_batch_opts) && opts->sorted_copy;
   TableView tab;
   int mdev;
   if (master_view(m, &tab, &mdev) != CV_OK || tab.unit != kUnitSector) return CV_EINVAL;
@@ -214,7 +230,9 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
     cfg_i = (int)opts->kernel_config - 1;
   }
   scan_config_for(cfg_i, table_kind(tab), &cfg_i);
+  if (opts && opts->bloom > CV_BATCH_BLOOM_ON) return CV_EINVAL;
   if (opts && opts->bloom == CV_BATCH_BLOOM_OFF) bloom = 0;
+  if (opts && opts->bloom == CV_BATCH_BLOOM_ON) bloom = 1;
 
   cv_batch* b = new (std::nothrow) cv_batch();
   if (!b) return CV_ENOMEM;
@@ -228,7 +246,6 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
   b->launches = 0;
   b->ran = false;
   b->tuned = false;
-  memset(b->tune_ms, 0, sizeof b->tune_ms);
 
   auto build_job = [&](int k, Job* job, std::vector<size_t>* first) -> int {
     first->assign(n_images + 1, 0);
@@ -247,6 +264,34 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
     CV_CUDA(cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming));
     uint64_t total_sectors = 0;
     for (uint32_t i = 0; i < n_images; i++) total_sectors += images[i].n_bytes / kSector;
+    // ---------------------------------------------------------- table variants
+    // Variant v of the table: layout (0: the master's own, 1: a sorted copy of a hash master)
+    // and Bloom use (the master's filter, or the batch's own when the master has none).
+    TableView sorted_tab = tab, bloom_tab = tab;
+    bool have_sorted = false, have_bloom = bloom_avail;
+    auto need_sorted = [&]() -> int {
+      if (have_sorted || tab.layout != kLayoutHash) return CV_OK;
+      CV_TRY(table_sorted_copy(tab, stream, &sorted_tab, &b->own_slots, &b->own_keys0));
+      have_sorted = true;
+      return CV_OK;
+    };
+    auto need_bloom = [&]() -> int {
+      if (have_bloom) return CV_OK;
+      CV_TRY(table_bloom(tab, 16, stream, &bloom_tab, &b->own_bloom));
+      have_bloom = true;
+      return CV_OK;
+    };
+    auto variant = [&](int sorted, int bl) {
+      TableView t = sorted ? sorted_tab : tab;
+      if (bl && !bloom_avail) {  // the batch's own filter over the same keys
+        t.bloom = bloom_tab.bloom;
+        t.bloom_mask = bloom_tab.bloom_mask;
+      }
+      t.use_bloom = (uint32_t)bl;
+      return t;
+    };
+    // index into the variants: 0 the master's layout, 1 the sorted copy
+    int layout_choice = (want_sorted && tab.layout == kLayoutHash) ? 1 : 0;
     // ---------------------------------------------------------------- autotune
     if (opts && opts->autotune && total_sectors) {
       cudaDeviceProp prop;
@@ -254,14 +299,17 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
       const uint64_t unique = tab.layout == kLayoutSorted ? tab.n_keys : (uint64_t)tab.slot_mask + 1;
       const uint32_t tkey = (uint32_t)table_kind(tab) * 2u + (tab.tau_mask ? 1u : 0u);
       const std::string key = tune_key(prop.name, ctx->sms, total_sectors, n_images, unique, bloom_avail, tkey);
-      int tc, tb;
-      if (tune_lookup(key, opts->tune_cache, &tc, &tb)) {
-        cfg_i = tc;
-        bloom = tb;
+      TuneChoice tc;
+      if (tune_lookup(key, opts->tune_cache, &tc)) {
+        cfg_i = tc.cfg;
+        bloom = tc.bloom;
+        layout_choice = (tc.layout == (int)kLayoutSorted && tab.layout == kLayoutHash) ? 1 : 0;
       } else {
+        CV_TRY(need_sorted());
+        CV_TRY(need_bloom());
+        const int n_layouts = have_sorted ? 2 : 1;
         float best = 1e30f;
-        for (int k = 0; k < ncfg && k < 64; k++) {
-          if (!cfgs[k].scan_fn[table_kind(tab)]) continue;  // not built for this table kind
+        for (int k = 0; k < ncfg; k++) {
           Job job;
           std::vector<size_t> first;
           CV_TRY(build_job(k, &job, &first));
@@ -271,44 +319,57 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
             tb_.release();
             return rc;
           }
-          for (int bl = 0; bl <= (bloom_avail ? 1 : 0); bl++) {
-            TableView t = tab;
-            t.use_bloom = (uint32_t)bl;
-            float ms_min = 1e30f;
-            for (int rep = 0; rep < 3; rep++) {
-              rc = enqueue_run(ctx, k, t, job, tb_, 0, nullptr, stream, b->ev0, b->ev1, nullptr);
-              if (rc != CV_OK) break;
-              if (cudaEventSynchronize(b->ev1) != cudaSuccess) {
-                rc = CV_ECUDA;
-                break;
+          for (int lay = 0; lay < n_layouts && rc == CV_OK; lay++) {
+            for (int bl = 0; bl <= 1 && rc == CV_OK; bl++) {
+              const TableView t = variant(lay, bl);
+              if (!cfgs[k].scan_fn[table_kind(t)]) continue;  // not built for this table kind
+              float ms_min = 1e30f;
+              for (int rep = 0; rep < 3; rep++) {
+                rc = enqueue_run(ctx, k, t, job, tb_, 0, nullptr, stream, b->ev0, b->ev1, nullptr);
+                if (rc != CV_OK) break;
+                if (cudaEventSynchronize(b->ev1) != cudaSuccess) {
+                  rc = CV_ECUDA;
+                  break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+                if (rep) ms_min = std::min(ms_min, ms);  // the first run warms up
               }
-              float ms = 0.f;
-              cudaEventElapsedTime(&ms, b->ev0, b->ev1);
-              if (rep) ms_min = std::min(ms_min, ms);  // first run warms up
-            }
-            if (rc != CV_OK) {
-              cudaStreamSynchronize(stream);
-              tb_.release();
-              return rc;
-            }
-            b->tune_ms[k][bl] = ms_min;
-            if (ms_min < best) {
-              best = ms_min;
-              cfg_i = k;
-              bloom = bl;
+              if (rc == CV_OK && ms_min < best) {
+                best = ms_min;
+                cfg_i = k;
+                bloom = bl;
+                layout_choice = lay;
+              }
             }
           }
           cudaStreamSynchronize(stream);
           tb_.release();
+          if (rc != CV_OK) return rc;
         }
-        tune_store(key, opts->tune_cache, cfg_i, bloom);
+        tune_store(key, opts->tune_cache,
+                   TuneChoice{cfg_i, bloom, (int)(layout_choice ? kLayoutSorted : tab.layout)});
         b->tuned = true;
       }
     }
+    // keep only what the choice uses
+    if (layout_choice) CV_TRY(need_sorted());
+    if (bloom && !bloom_avail) CV_TRY(need_bloom());
+    if (!layout_choice && b->own_slots) {
+      cudaFree(b->own_slots);
+      cudaFree(b->own_keys0);
+      b->own_slots = b->own_keys0 = nullptr;
+    }
+    if (!bloom && b->own_bloom) {
+      cudaFree(b->own_bloom);
+      b->own_bloom = nullptr;
+    }
+    const TableView chosen = variant(layout_choice, bloom);
+    scan_config_for(cfg_i, table_kind(chosen), &cfg_i);
     b->cfg_i = cfg_i;
     b->bloom = bloom;
-    b->tab = tab;
-    b->tab.use_bloom = (uint32_t)bloom;
+    b->tab = chosen;
+    b->layout = (int)chosen.layout;
     CV_TRY(build_job(cfg_i, &b->job, &b->first_seg));
     const size_t nseg = b->job.segs.size();
     CV_CUDA(cudaMallocHost((void**)&b->counters_h, (nseg + 2) * 8));
@@ -407,6 +468,7 @@ int cv_batch_get_info(const cv_batch* b, cv_batch_info* info) {
   info->kernel_config = b->cfg_i;
   info->config_name = scan_configs(&n)[b->cfg_i].name;
   info->bloom = (uint32_t)b->bloom;
+  info->layout = (uint32_t)b->layout;
   info->tuned = b->tuned ? 1u : 0u;
   info->kernel_launches = (uint32_t)b->launches;
   info->tensor_maps = (uint32_t)b->job.maps.size();
@@ -432,6 +494,8 @@ void cvk_batch_free(void* h) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->buf.release();
+  for (void* p : {b->own_slots, b->own_keys0, b->own_bloom})
+    if (p) cudaFree(p);
   if (b->counters_h) cudaFreeHost(b->counters_h);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);

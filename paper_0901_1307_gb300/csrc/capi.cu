@@ -112,7 +112,7 @@ int cv_sector_signatures(const void* in, uint64_t n_sectors, uint32_t signature,
   CV_TRY(get_ctx(&ctx));
   cudaStream_t stream = (cudaStream_t)stream_;
   int cfg_i;
-  const ScanCfg& cfg = scan_config_for(ctx->cfg_index, (int)signature, &cfg_i);
+  const ScanCfg& cfg = digest_config_for(ctx->cfg_index, (int)signature, &cfg_i);
   if (!cfg.digest_fn[signature]) return CV_EINVAL;
   Temps tmp(ctx, stream);
   Job job;

@@ -20,15 +20,20 @@ struct ScanCfg {
 };
 
 const ScanCfg* scan_configs(int* n);
+// The configurations of each instantiation unit, in table order (scan_cfgs_{a,b,c}.cu).
+const ScanCfg* scan_cfgs_a(int* n);
+const ScanCfg* scan_cfgs_b(int* n);
+const ScanCfg* scan_cfgs_c(int* n);
 
 // Scan kernels are selected by signature and table layout: kind = sig + 4 * layout.
 constexpr int kTableKinds = 8;
 inline int table_kind(const TableView& t) { return (int)t.sig + 4 * (int)t.layout; }
 
-// Configuration cfg_i if it has a scan kernel for table kind `kind` (table_kind, or a bare kSig*
-// for the digest pass), else the default one (index 0, which has every kind); *used receives the
-// index in use.
+// Configuration cfg_i if it has a scan kernel for table kind `kind` (table_kind), else the
+// default one (index 0, which has every kind); *used receives the index in use.
 const ScanCfg& scan_config_for(int cfg_i, int kind, int* used);
+// Configuration cfg_i if it has a digest-mode kernel for signature sig, else the default one.
+const ScanCfg& digest_config_for(int cfg_i, int sig, int* used);
 
 // The expand pass over n_out_tiles output tiles (see expand_kernel). Returns a CUDA error code.
 int launch_expand(const ScanCfg& cfg, const uint4* hit_rec, const uint32_t* tile_nhit, const uint64_t* tile_off,

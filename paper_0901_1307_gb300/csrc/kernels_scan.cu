@@ -1,10 +1,107 @@
-// Instantiations of the scan kernel (hash + probe + first compaction pass) and of the second
-// compaction pass, one per tuned configuration.
+// The scan configurations (assembled from scan_cfgs_*.cu), the offset pass and the launch of the
+// second compaction pass.
+#include <vector>
+
 #include "compact.cuh"
 #include "cv_launch.h"
 #include "scan_kernel.cuh"
 
 namespace cvk {
+
+// ------------------------------------------------------------ offset pass (first of two)
+// Block-wide inclusive scan of one u64 per thread (1024 threads).
+__device__ __forceinline__ uint64_t block_inclusive_scan(uint64_t x, uint64_t* warp_buf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t v = __shfl_up_sync(0xFFFFFFFFu, x, d);
+    if (lane >= d) x += v;
+  }
+  if (lane == 31) warp_buf[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t w = warp_buf[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t v = __shfl_up_sync(0xFFFFFFFFu, w, d);
+      if (lane >= d) w += v;
+    }
+    warp_buf[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  return x + (warp ? warp_buf[warp - 1] : 0ull);
+}
+
+__global__ void __launch_bounds__(kOffThreads) chunk_sums_kernel(const uint64_t* v, uint64_t n, uint64_t* sums) {
+  __shared__ uint64_t wb[32];
+  const uint64_t base = (uint64_t)blockIdx.x * kOffChunk;
+  uint64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kOffItems; k++) {
+    const uint64_t i = base + (uint64_t)k * kOffThreads + threadIdx.x;
+    if (i < n) s += v[i];
+  }
+  const uint64_t incl = block_inclusive_scan(s, wb);
+  if (threadIdx.x == kOffThreads - 1) sums[blockIdx.x] = incl;
+}
+
+// In place: sums[0..m) -> exclusive offsets; *total = the sum of all.
+__global__ void __launch_bounds__(kOffThreads) scan_sums_kernel(uint64_t* sums, uint64_t m, uint64_t* total) {
+  __shared__ uint64_t wb[32];
+  __shared__ uint64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint64_t base = 0; base < m; base += kOffThreads) {
+    const uint64_t i = base + threadIdx.x;
+    const uint64_t x = i < m ? sums[i] : 0ull;
+    const uint64_t incl = block_inclusive_scan(x, wb);
+    const uint64_t c = carry;
+    if (i < m) sums[i] = c + incl - x;
+    __syncthreads();
+    if (threadIdx.x == kOffThreads - 1) carry = c + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kOffThreads) chunk_scan_kernel(const uint64_t* v, uint64_t n, const uint64_t* offs,
+                                                                 uint64_t* out) {
+  __shared__ uint64_t wb[32];
+  const uint64_t first = (uint64_t)blockIdx.x * kOffChunk + (uint64_t)threadIdx.x * kOffItems;
+  uint64_t x[kOffItems];
+  uint64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kOffItems; k++) {
+    x[k] = (first + k < n) ? v[first + k] : 0ull;
+    s += x[k];
+  }
+  uint64_t run = block_inclusive_scan(s, wb) - s + offs[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kOffItems; k++) {
+    if (first + k < n) out[first + k] = run;
+    run += x[k];
+  }
+}
+
+// seg_off[s] = offset of the first output tile of segment s (output tiles per scan tile: scale).
+__global__ void segment_offsets_kernel(const uint64_t* tile_off, uint64_t n, const Segment* segs, uint32_t n_segs,
+                                       uint32_t scale, const uint64_t* total, uint64_t* seg_off) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_segs; s += gridDim.x * blockDim.x) {
+    const uint64_t u = segs[s].tile_base * scale;
+    seg_off[s] = u < n ? tile_off[u] : *total;
+  }
+}
+
+// The sum of n u32 values added to *out: the disk sectors with at least one match, from the
+// per-tile hit counts.
+__global__ void sum_u32_kernel(const uint32_t* v, uint64_t n, unsigned long long* out) {
+  unsigned long long s = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    s += v[i];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, d);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
 
 // Self-test of the bounded wait: one thread waits on an mbarrier that nothing completes. The
 // wait gives up after timeout_ns, sets kStTimeout and the kernel returns normally.
@@ -21,58 +118,42 @@ __global__ void wait_timeout_selftest_kernel(uint32_t* status, uint64_t timeout_
 }
 
 
-#define CV_KS(T, SPT, NS, B, MODE, P, MB, SIG) (const void*)scan_kernel<T, SPT, NS, B, MODE, P, MB, SIG, kLayoutHash>
-#define CV_KSS(T, SPT, NS, B, P, MB, SIG) (const void*)scan_kernel<T, SPT, NS, B, kModeScan, P, MB, SIG, kLayoutSorted>
-
-// A configuration with MD5 kernels for the hash layout only.
-#define CV_SCAN_CFG(T, SPT, NS, B, P, MB)                                                                  \
-  ScanCfg {                                                                                                \
-    "t" #T "_x" #SPT "_s" #NS "_b" #B "_p" #P, T, SPT, T / SPT + 32, NS, B,                                 \
-        {CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigMd5), nullptr, nullptr, nullptr,                       \
-         nullptr, nullptr, nullptr, nullptr},                                                              \
-        {CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigMd5), nullptr, nullptr, nullptr},                    \
-        (const void*)expand_kernel<T>, ScanSmem<T, NS, B>::kAlloc                                          \
-  }
-
-// A configuration with kernels for every signature and both table layouts.
-#define CV_SCAN_CFG_ALL(T, SPT, NS, B, P, MB)                                                              \
-  ScanCfg {                                                                                                \
-    "t" #T "_x" #SPT "_s" #NS "_b" #B "_p" #P, T, SPT, T / SPT + 32, NS, B,                                 \
-        {CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigMd5), CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigMd5NoPad), \
-         CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigDjb2), CV_KS(T, SPT, NS, B, kModeScan, P, MB, kSigCrc64),   \
-         CV_KSS(T, SPT, NS, B, P, MB, kSigMd5), CV_KSS(T, SPT, NS, B, P, MB, kSigMd5NoPad),                     \
-         CV_KSS(T, SPT, NS, B, P, MB, kSigDjb2), CV_KSS(T, SPT, NS, B, P, MB, kSigCrc64)},                      \
-        {CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigMd5),                                                \
-         CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigMd5NoPad),                                           \
-         CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigDjb2),                                               \
-         CV_KS(T, SPT, NS, B, kModeDigest, P, MB, kSigCrc64)},                                             \
-        (const void*)expand_kernel<T>, ScanSmem<T, NS, B>::kAlloc                                          \
-  }
-
-// The first entry is the default configuration (the fastest measured on GB300 for the 32 GiB
-// image workload) and the only one built for every signature and the sorted layout; the others
-// stay selectable and are what the batch autotuner tries.
-static const ScanCfg kConfigs[] = {
-    CV_SCAN_CFG_ALL(256, 1, 2, 64, 3, 0),
-    CV_SCAN_CFG(480, 1, 2, 64, 3, 3),
-    CV_SCAN_CFG(256, 1, 2, 64, 0, 0),
-    CV_SCAN_CFG(256, 1, 2, 64, 2, 0),
-    CV_SCAN_CFG(256, 2, 2, 64, 3, 0),
-    CV_SCAN_CFG(256, 2, 2, 128, 3, 0),
-    CV_SCAN_CFG(256, 1, 3, 64, 3, 0),
-    CV_SCAN_CFG(128, 1, 2, 128, 2, 0),
-    CV_SCAN_CFG(128, 1, 4, 64, 0, 0),
-};
+// The configurations in table order. The first is the default (the fastest measured on GB300
+// for the 32 GiB image workload) and the only one with digest-mode kernels; every one has scan
+// kernels for all eight table kinds (four signatures x two layouts), so the batch autotuner can
+// pick any of them for any table. The kernels are instantiated in scan_cfgs_{a,b,c}.cu, which
+// compile in parallel.
+static const std::vector<ScanCfg>& all_configs() {
+  static const std::vector<ScanCfg> v = [] {
+    std::vector<ScanCfg> out;
+    for (auto part : {scan_cfgs_a, scan_cfgs_b, scan_cfgs_c}) {
+      int n = 0;
+      const ScanCfg* c = part(&n);
+      out.insert(out.end(), c, c + n);
+    }
+    return out;
+  }();
+  return v;
+}
 
 const ScanCfg* scan_configs(int* n) {
-  *n = (int)(sizeof(kConfigs) / sizeof(kConfigs[0]));
-  return kConfigs;
+  const std::vector<ScanCfg>& v = all_configs();
+  *n = (int)v.size();
+  return v.data();
 }
 
 const ScanCfg& scan_config_for(int cfg_i, int kind, int* used) {
   int n;
   const ScanCfg* c = scan_configs(&n);
   if (cfg_i < 0 || cfg_i >= n || kind < 0 || kind >= kTableKinds || !c[cfg_i].scan_fn[kind]) cfg_i = 0;
+  if (used) *used = cfg_i;
+  return c[cfg_i];
+}
+
+const ScanCfg& digest_config_for(int cfg_i, int sig, int* used) {
+  int n;
+  const ScanCfg* c = scan_configs(&n);
+  if (cfg_i < 0 || cfg_i >= n || sig < 0 || sig > kSigCrc64 || !c[cfg_i].digest_fn[sig]) cfg_i = 0;
   if (used) *used = cfg_i;
   return c[cfg_i];
 }

@@ -214,6 +214,54 @@ int gather_master_units(DevCtx* ctx, const cv_buf* files, uint32_t n_files, cons
   return rc;
 }
 
+// The sorted layout of a hash table's occupied slots (Section 4: binary search for high
+// occupancy): the nu occupied records, compacted in slot order, then sorted by h0 =
+// tau_home(d0, tau) (a stable sort, so the order is deterministic), and their h0 words. The
+// caller owns *slots_out (nu records of 32 bytes) and *keys0_out (nu words); *steps receives
+// ceil(log2 nu), the bisection steps of a lookup. Returns after the work has finished.
+int sorted_from_hash(DevCtx* ctx, const uint4* slots, uint64_t n_slots, uint32_t nu, Temps& tmp, cudaStream_t stream,
+                     void** slots_out, void** keys0_out, uint32_t* steps) {
+  uint32_t *ck, *cv, *ck2, *cv2, *kr, *vr;
+  CV_TRY(tmp.alloc(&ck, n_slots * 4));
+  CV_TRY(tmp.alloc(&cv, n_slots * 4));
+  CV_TRY(tmp.alloc(&ck2, n_slots * 4));
+  CV_TRY(tmp.alloc(&cv2, n_slots * 4));
+  const unsigned gs = grid_for(n_slots, 256, ctx->sms);
+  occupied_keys_kernel<<<gs, 256, 0, stream>>>(slots, (uint32_t)n_slots, ck, cv);
+  CV_CUDA(cudaGetLastError());
+  CV_TRY(radix_sort_pairs(ck, cv, ck2, cv2, n_slots, 1, tmp, stream, &kr, &vr));
+  uint32_t* kfree = kr == ck ? ck2 : ck;  // the other key buffer is free for the h0 keys
+  uint32_t* vfree = vr == cv ? cv2 : cv;
+  const unsigned gu = grid_for(std::max<uint32_t>(nu, 1), 256, ctx->sms);
+  h0_keys_kernel<<<gu, 256, 0, stream>>>(slots, vr, nu, kfree);
+  CV_CUDA(cudaGetLastError());
+  uint32_t *hk, *hv;
+  CV_TRY(radix_sort_pairs(kfree, vr, kr, vfree, nu, 32, tmp, stream, &hk, &hv));
+  void* out = nullptr;
+  void* keys0 = nullptr;
+  CV_CUDA(cudaMalloc(&out, std::max<uint64_t>(nu, 1) * 32));
+  cudaError_t e = cudaMalloc(&keys0, std::max<uint64_t>(nu, 1) * 4);
+  if (e != cudaSuccess) {
+    cudaFree(out);
+    return cuda_fail(e);
+  }
+  gather_slots_kernel<<<gu, 256, 0, stream>>>(slots, hv, nu, (uint4*)out);
+  e = cudaGetLastError();
+  if (e == cudaSuccess && nu) e = cudaMemcpyAsync(keys0, hk, (uint64_t)nu * 4, cudaMemcpyDeviceToDevice, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    cudaFree(out);
+    cudaFree(keys0);
+    return cuda_fail(e);
+  }
+  *slots_out = out;
+  *keys0_out = keys0;
+  uint32_t st = 0;
+  while ((1ull << st) < nu) st++;
+  *steps = st;
+  return CV_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -245,7 +293,7 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
   DevCtx* ctx;
   CV_TRY(get_ctx(&ctx));
   int cfg_i;
-  const ScanCfg& cfg = scan_config_for(ctx->cfg_index, sig, &cfg_i);
+  const ScanCfg& cfg = digest_config_for(ctx->cfg_index, sig, &cfg_i);
 
   // whole units (sectors or fragments) of every file, concatenated
   std::vector<uint64_t> file_base(n_files + 1, 0);
@@ -361,34 +409,11 @@ int cv_master_build(const cv_buf* files, uint32_t n_files, const cv_master_opts*
         layout = (double)hc[2] > (bpk ? 0.8 : 0.5) * (double)n_slots ? CV_LAYOUT_SORTED : CV_LAYOUT_HASH;
       uint32_t steps = 0;  // binary-search steps of the sorted layout
       if (layout == CV_LAYOUT_SORTED) {
-        // the occupied slots, compacted in slot order, sorted by h0 (stable: deterministic)
-        const uint32_t nu = hc[2];
-        uint32_t *ck, *cv, *ck2, *cv2, *kr, *vr;
-        CV_TRY(tmp.alloc(&ck, n_slots * 4));
-        CV_TRY(tmp.alloc(&cv, n_slots * 4));
-        CV_TRY(tmp.alloc(&ck2, n_slots * 4));
-        CV_TRY(tmp.alloc(&cv2, n_slots * 4));
-        const unsigned gs = grid_for(n_slots, 256, ctx->sms);
-        occupied_keys_kernel<<<gs, 256, 0, stream>>>((const uint4*)m->slots, (uint32_t)n_slots, ck, cv);
-        CV_CUDA(cudaGetLastError());
-        CV_TRY(radix_sort_pairs(ck, cv, ck2, cv2, n_slots, 1, tmp, stream, &kr, &vr));
-        uint32_t* kfree = kr == ck ? ck2 : ck;  // the other key buffer is free for the h0 keys
-        uint32_t* vfree = vr == cv ? cv2 : cv;
-        const unsigned gu = grid_for(std::max<uint32_t>(nu, 1), 256, ctx->sms);
-        h0_keys_kernel<<<gu, 256, 0, stream>>>((const uint4*)m->slots, vr, nu, kfree);
-        CV_CUDA(cudaGetLastError());
-        uint32_t *hk, *hv;
-        CV_TRY(radix_sort_pairs(kfree, vr, kr, vfree, nu, 32, tmp, stream, &hk, &hv));
         void* sorted_slots = nullptr;
-        CV_CUDA(cudaMalloc(&sorted_slots, std::max<uint64_t>(nu, 1) * 32));
-        CV_CUDA(cudaMalloc(&m->keys0, std::max<uint64_t>(nu, 1) * 4));
-        gather_slots_kernel<<<gu, 256, 0, stream>>>((const uint4*)m->slots, hv, nu, (uint4*)sorted_slots);
-        CV_CUDA(cudaGetLastError());
-        if (nu) CV_CUDA(cudaMemcpyAsync(m->keys0, hk, (uint64_t)nu * 4, cudaMemcpyDeviceToDevice, stream));
-        CV_CUDA(cudaStreamSynchronize(stream));
+        CV_TRY(sorted_from_hash(ctx, (const uint4*)m->slots, n_slots, hc[2], tmp, stream, &sorted_slots, &m->keys0,
+                                &steps));
         cudaFree(m->slots);
         m->slots = sorted_slots;
-        while ((1ull << steps) < nu) steps++;
       }
       m->tab.slots = (const uint4*)m->slots;
       m->tab.keys0 = (const uint32_t*)m->keys0;
@@ -637,3 +662,59 @@ int cv_master_load(const char* path, void* stream_, cv_master** out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- variants of a built table
+// (the batch autotuner scans with whichever layout and Bloom use it measures fastest)
+
+int cvk::table_sorted_copy(const TableView& tab, cudaStream_t stream, TableView* out, void** slots_out,
+                           void** keys0_out) {
+  if (tab.layout != kLayoutHash || tab.unit != kUnitSector) return CV_EINVAL;
+  DevCtx* ctx;
+  CV_TRY(get_ctx(&ctx));
+  const uint64_t n_slots = (uint64_t)tab.slot_mask + 1;
+  // the occupied slots: n_keys is kept for the hash layout too (distinct keys)
+  const uint32_t nu = tab.n_keys;
+  uint32_t steps = 0;
+  int rc;
+  {
+    Temps tmp(ctx, stream);
+    rc = sorted_from_hash(ctx, tab.slots, n_slots, nu, tmp, stream, slots_out, keys0_out, &steps);
+  }
+  if (rc != CV_OK) return rc;
+  CV_CUDA(cudaStreamSynchronize(stream));  // temporaries returned
+  *out = tab;
+  out->slots = (const uint4*)*slots_out;
+  out->keys0 = (const uint32_t*)*keys0_out;
+  out->layout = kLayoutSorted;
+  out->n_keys = nu;
+  return CV_OK;
+}
+
+int cvk::table_bloom(const TableView& tab, uint32_t bits_per_key, cudaStream_t stream, TableView* out,
+                     void** bloom_out) {
+  if (tab.unit != kUnitSector || bits_per_key == 0 || bits_per_key > 64) return CV_EINVAL;
+  DevCtx* ctx;
+  CV_TRY(get_ctx(&ctx));
+  const uint64_t n_records = tab.layout == kLayoutSorted ? (uint64_t)tab.n_keys : (uint64_t)tab.slot_mask + 1;
+  const uint64_t keys = std::max<uint64_t>(tab.n_keys, 1);
+  const uint64_t n_blocks = next_pow2((keys * bits_per_key + 255) / 256);
+  void* bloom = nullptr;
+  CV_CUDA(cudaMalloc(&bloom, n_blocks * 32));
+  cudaError_t e = cudaMemsetAsync(bloom, 0, n_blocks * 32, stream);
+  if (e == cudaSuccess && n_records) {
+    bloom_kernel<<<grid_for(n_records, 256, ctx->sms), 256, 0, stream>>>(tab.slots, (uint32_t)n_records,
+                                                                         (uint32_t*)bloom, (uint32_t)(n_blocks - 1));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    cudaFree(bloom);
+    return cuda_fail(e);
+  }
+  *bloom_out = bloom;
+  *out = tab;
+  out->bloom = (const uint4*)bloom;
+  out->bloom_mask = (uint32_t)(n_blocks - 1);
+  out->use_bloom = 1u;
+  return CV_OK;
+}

@@ -89,7 +89,7 @@ int cv_probe_profile(const cv_master* m, const void* image, uint64_t n_bytes, ui
   st->sectors = n;
   if (n == 0) return CV_OK;
   int cfg_i;
-  const ScanCfg& cfg = scan_config_for(ctx->cfg_index, (int)tab.sig, &cfg_i);
+  const ScanCfg& cfg = digest_config_for(ctx->cfg_index, (int)tab.sig, &cfg_i);
   Temps tmp(ctx, stream);
   uint4* dig;
   unsigned long long* acc;

@@ -79,24 +79,29 @@ int get_ctx(DevCtx** out) {
     c.address_range = (q == cudaDriverEntryPointSuccess) ? (PFN_cuMemGetAddressRange_v3020)fn : nullptr;
     int n;
     const ScanCfg* cfgs = scan_configs(&n);
-    c.blocks_per_sm.assign(n, 0);
+    c.blocks_per_sm.assign(n, std::array<int, kTableKinds>{});
     c.blocks_per_sm_digest.assign(n, 0);
     for (int i = 0; i < n; i++) {
-      for (int kind = 0; kind < kTableKinds; kind++)
-        if (cfgs[i].scan_fn[kind])
-          CV_CUDA(cudaFuncSetAttribute(cfgs[i].scan_fn[kind], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)cfgs[i].smem));
-      for (int sig = 0; sig < 4; sig++) {
-        if (cfgs[i].digest_fn[sig])
-          CV_CUDA(cudaFuncSetAttribute(cfgs[i].digest_fn[sig], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)cfgs[i].smem));
+      for (int kind = 0; kind < kTableKinds; kind++) {
+        if (!cfgs[i].scan_fn[kind]) continue;
+        CV_CUDA(cudaFuncSetAttribute(cfgs[i].scan_fn[kind], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)cfgs[i].smem));
+        CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.blocks_per_sm[i][kind], cfgs[i].scan_fn[kind],
+                                                              cfgs[i].threads, cfgs[i].smem));
+        if (c.blocks_per_sm[i][kind] < 1) return CV_ECUDA;
       }
-      CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.blocks_per_sm[i], cfgs[i].scan_fn[0], cfgs[i].threads,
-                                                            cfgs[i].smem));
-      CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.blocks_per_sm_digest[i], cfgs[i].digest_fn[0],
-                                                            cfgs[i].threads, cfgs[i].smem));
-      if (c.blocks_per_sm[i] < 1 || c.blocks_per_sm_digest[i] < 1) return CV_ECUDA;
+      for (int sig = 0; sig < 4; sig++) {
+        if (!cfgs[i].digest_fn[sig]) continue;
+        CV_CUDA(cudaFuncSetAttribute(cfgs[i].digest_fn[sig], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)cfgs[i].smem));
+      }
+      if (cfgs[i].digest_fn[0]) {
+        CV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c.blocks_per_sm_digest[i], cfgs[i].digest_fn[0],
+                                                              cfgs[i].threads, cfgs[i].smem));
+        if (c.blocks_per_sm_digest[i] < 1) return CV_ECUDA;
+      }
     }
+    if (!cfgs[0].digest_fn[0]) return CV_ECUDA;  // the default configuration serves every digest pass
 
     c.cfg_index = 0;
     const char* env = getenv("CV_SCAN_CONFIG");
@@ -224,7 +229,8 @@ int launch_range(DevCtx* ctx, int cfg_i, bool digest, const Job& job, const Segm
   const ScanCfg& cfg = scan_configs(&n)[cfg_i];
   const void* fn = digest ? cfg.digest_fn[base.tab.sig] : cfg.scan_fn[table_kind(base.tab)];
   if (!fn) return CV_EINVAL;  // the caller picks a configuration built for the signature
-  const int bps = digest ? ctx->blocks_per_sm_digest[cfg_i] : ctx->blocks_per_sm[cfg_i];
+  const int bps = digest ? ctx->blocks_per_sm_digest[cfg_i] : ctx->blocks_per_sm[cfg_i][table_kind(base.tab)];
+  if (bps < 1) return CV_EINVAL;
   size_t a = s0;
   while (a < s1) {
     // extend the launch while its segments' maps fit in one parameter block

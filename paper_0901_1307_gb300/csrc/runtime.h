@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -59,8 +60,8 @@ struct DevCtx {
   cudaStream_t copy_stream = nullptr;  // host-to-device copies of streamed images
   PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   PFN_cuMemGetAddressRange_v3020 address_range = nullptr;
-  std::vector<int> blocks_per_sm;  // per scan configuration (scan mode)
-  std::vector<int> blocks_per_sm_digest;
+  std::vector<std::array<int, kTableKinds>> blocks_per_sm;  // per scan configuration and table kind
+  std::vector<int> blocks_per_sm_digest;  // per scan configuration (0: no digest-mode kernels)
   int cfg_index = 0;  // default scan configuration
 };
 
@@ -118,6 +119,14 @@ unsigned grid_for(uint64_t n, int threads, int sms);
 
 // Device view of a master table (capi.cu).
 int master_view(const cv_master* m, TableView* tab, int* dev);
+
+// Variants of a built sector table (master.cu), for the batch autotuner. table_sorted_copy: the
+// sorted layout of a hash-layout table (its own record and key arrays, *slots_out and *keys0_out,
+// owned by the caller; postings, Bloom filter and confirmation copy shared). table_bloom: a
+// blocked Bloom filter of bits_per_key bits per distinct key over the table's records
+// (*bloom_out owned by the caller). Both return after the work has finished.
+int table_sorted_copy(const TableView& tab, cudaStream_t stream, TableView* out, void** slots_out, void** keys0_out);
+int table_bloom(const TableView& tab, uint32_t bits_per_key, cudaStream_t stream, TableView* out, void** bloom_out);
 
 // A one-image host result holding a copy of n triples (capi.cu).
 cv_result* make_host_result(int dev, const MatchOut* data, uint64_t n, uint64_t sectors, float total_ms);

@@ -46,6 +46,7 @@ CV_EAGAIN = -9
 CV_EIO = -10
 CV_BATCH_BLOOM_AUTO = 0
 CV_BATCH_BLOOM_OFF = 1
+CV_BATCH_BLOOM_ON = 2
 CV_NOALLOC_MAX_SECTORS = 1 << 19
 
 
@@ -94,13 +95,13 @@ class cv_probe_stats(ctypes.Structure):
 class cv_batch_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("autotune", ctypes.c_uint32), ("stream", ctypes.c_void_p),
                 ("match_capacity", ctypes.c_uint64), ("kernel_config", ctypes.c_uint32), ("bloom", ctypes.c_uint32),
-                ("tune_cache", ctypes.c_char_p)]
+                ("tune_cache", ctypes.c_char_p), ("sorted_copy", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class cv_batch_info(ctypes.Structure):
     _fields_ = [("kernel_config", ctypes.c_int), ("config_name", ctypes.c_char_p), ("bloom", ctypes.c_uint32),
                 ("tuned", ctypes.c_uint32), ("kernel_launches", ctypes.c_uint32), ("tensor_maps", ctypes.c_uint32),
-                ("segments", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("sectors", ctypes.c_uint64),
+                ("segments", ctypes.c_uint32), ("layout", ctypes.c_uint32), ("sectors", ctypes.c_uint64),
                 ("match_capacity", ctypes.c_uint64), ("scan_ms", ctypes.c_float)]
 
 
@@ -487,12 +488,13 @@ class Batch:
 
 
 def batch_create(master: Master, images, autotune: bool = False, match_capacity: int = 0, kernel_config: int = 0,
-                 bloom: int = CV_BATCH_BLOOM_AUTO, tune_cache: str | None = None, stream=None) -> Batch:
+                 bloom: int = CV_BATCH_BLOOM_AUTO, tune_cache: str | None = None, stream=None,
+                 sorted_copy: bool = False) -> Batch:
     """cv_batch_create: a graph over device images (kept alive by the returned Batch)."""
     images = list(images)
     arr, keep = _bufs(images)
     o = cv_batch_opts(ctypes.sizeof(cv_batch_opts), 1 if autotune else 0, _stream(stream), match_capacity,
-                      kernel_config, bloom, tune_cache.encode() if tune_cache else None)
+                      kernel_config, bloom, tune_cache.encode() if tune_cache else None, 1 if sorted_copy else 0, 0)
     h = ctypes.c_void_p()
     _check(load().cv_batch_create(master.handle, arr, len(images), ctypes.byref(o), ctypes.byref(h)),
            "cv_batch_create")

@@ -161,6 +161,12 @@ class Plan:
             _host_lib().synth_image(*self._args(), first, n, out.ctypes.data)
         return out
 
+    def image_host_into(self, out_ptr: int, first: int, n: int) -> None:
+        """Write image sectors [first, first+n) to host memory at out_ptr (n*512 bytes), e.g. a
+        slot of a pinned pool; the host generator runs on all cores (OpenMP)."""
+        if n:
+            _host_lib().synth_image(*self._args(), first, n, out_ptr)
+
     def master_host(self, f: int, s0: int = 0, n: int | None = None) -> np.ndarray:
         if n is None:
             n = int(self.file_nsect[f]) - s0

@@ -12,7 +12,7 @@ def _plan():
 
 
 def _args(**kw):
-    a = dict(steps=20, warmup=5, config="scale", kernel_config=0, sections_out="")
+    a = dict(steps=20, warmup=5, config="scale", kernel_config=0, sections_out="", signature=0)
     a.update(kw)
     return types.SimpleNamespace(**a)
 

@@ -286,6 +286,73 @@ def test_batch_graph_equals_oracle_per_image(cv, autotune, tmp_path):
                 assert b2.info()["tuned"] == 0  # served from the cache
 
 
+@pytest.mark.parametrize("sig", [0, 2])
+@pytest.mark.parametrize("sorted_copy", [False, True])
+@pytest.mark.parametrize("bloom_mode", ["off", "on"])
+def test_batch_table_variants_equal_oracle(cv, sig, sorted_copy, bloom_mode):
+    """Every table variant the batch tuner can choose, forced one at a time on a hash-layout
+    master without a Bloom filter: the master's own table or its sorted copy, probed directly or
+    through a filter the batch builds. Each must give the oracle's result per image."""
+    files, whole, images, wants = _batch_images(30, 41 + sig)
+    bloom = cv.CV_BATCH_BLOOM_ON if bloom_mode == "on" else cv.CV_BATCH_BLOOM_OFF
+    with cv.master_build(files, signature=sig, bloom_bits_per_key=0, max_load=0.9) as m:
+        assert m.info()["bloom_bytes"] == 0 and m.info()["layout"] == cv.CV_LAYOUT_HASH
+        with cv.batch_create(m, images, bloom=bloom, sorted_copy=sorted_copy) as b:
+            info = b.info()
+            assert info["layout"] == (cv.CV_LAYOUT_SORTED if sorted_copy else cv.CV_LAYOUT_HASH)
+            assert info["bloom"] == (1 if bloom_mode == "on" else 0)
+            for run in range(2):
+                b.run()
+                assert b.wait() == sum(w.size for w in wants)
+                for k in range(len(images)):
+                    assert_same(cv.device_matches_to_numpy(b.matches(k)), wants[k], f"run {run} image {k}")
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_batch_tuner_reports_its_choice(cv, layout, tmp_path):
+    """The tuner searches configuration x layout x Bloom on the batch and reports what it chose;
+    whatever it chose, the results are the oracle's, and a second batch takes the choice from the
+    cache file."""
+    files, whole, images, wants = _batch_images(30, 45)
+    cache = str(tmp_path / "tune.txt")
+    with cv.master_build(files, bloom_bits_per_key=0, max_load=0.9, layout=layout) as m:
+        with cv.batch_create(m, images, autotune=True, tune_cache=cache) as b:
+            info = b.info()
+            assert info["tuned"] == 1
+            assert info["layout"] in (cv.CV_LAYOUT_HASH, cv.CV_LAYOUT_SORTED)
+            if layout == cv.CV_LAYOUT_SORTED:
+                assert info["layout"] == cv.CV_LAYOUT_SORTED  # a sorted master has no hash copy
+            b.run()
+            assert b.wait() == sum(w.size for w in wants)
+            for k in range(len(images)):
+                assert_same(cv.device_matches_to_numpy(b.matches(k)), wants[k], f"image {k}")
+        line = open(cache).read().split()
+        assert len(line) == 4 and line[1] == info["config_name"]
+        assert int(line[3]) == info["layout"] and int(line[2]) == info["bloom"]
+        with cv.batch_create(m, images, autotune=True, tune_cache=cache) as b2:
+            i2 = b2.info()
+            assert i2["tuned"] == 0
+            assert (i2["kernel_config"], i2["layout"], i2["bloom"]) == (info["kernel_config"], info["layout"],
+                                                                        info["bloom"])
+            b2.run()
+            b2.wait()
+            for k in range(len(images)):
+                assert_same(cv.device_matches_to_numpy(b2.matches(k)), wants[k], f"cached, image {k}")
+
+
+@pytest.mark.parametrize("cfg", range(9))
+def test_every_kernel_config_serves_every_table_kind(cv, cfg):
+    """Each kernel configuration is built for all four signatures and both layouts: scans with it
+    give the oracle's result for a 64-bit signature and the sorted layout alike."""
+    assert len(cv.kernel_configs()) == 9
+    files, whole, images, wants = _batch_images(6, 47)
+    img, want = images[0], wants[0]
+    for sig, layout in ((3, cv.CV_LAYOUT_SORTED), (1, cv.CV_LAYOUT_HASH)):
+        with cv.master_build(files, signature=sig, layout=layout) as m:
+            with cv.scan(m, [img], kernel_config=cfg + 1) as r:
+                assert_same(r.matches(0), want, f"config {cfg} sig {sig}")
+
+
 def test_batch_capacity_overflow_reported(cv):
     files, whole, images, wants = _batch_images(12, 33)
     total = sum(w.size for w in wants)
