@@ -716,11 +716,26 @@ def run_batch_tuner_occupancy(torch, cv, synth, images, expects, stream, file_ns
     return out
 
 
-def run_served(torch, cv, synth, args, host):
+def h2d_link_gbps(torch, host, stream, nbytes=8 << 30):
+    """One plain host-to-device copy of nbytes of the pinned buffer, timed with CUDA events."""
+    probe = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    probe.copy_(host[:nbytes], non_blocking=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    del probe
+    return nbytes / (ev0.elapsed_time(ev1) * 1e-3) / 1e9
+
+
+def run_served(torch, cv, synth, args, host, rate=None, n_requests=None):
     """Poisson arrivals of host-resident requests (80% 64 KiB-4 MiB stream chunks, 20%
-    256 MiB-16 GiB drive images, windows of one pinned pool) against one 8M-sector table."""
+    256 MiB-16 GiB drive images, windows of one pinned pool) against one 8M-sector table. The
+    host link is timed right before and after the run (a plain 8 GiB copy from the pool)."""
     import threading
 
+    rate = rate or args.serve_rate
     m, file_nsect, mseed, build_s = build_master_set(torch, cv, synth, "m8m")
     pool_sectors = host.numel() // SECTOR
     plan = synth.make_plan_density(5, pool_sectors, file_nsect, args.serve_density, mseed)
@@ -732,8 +747,8 @@ def run_served(torch, cv, synth, args, host):
     torch.cuda.synchronize()
     expect = plan.expected_intact()
     rng = np.random.default_rng(5)
-    n = args.serve_requests
-    gaps = rng.exponential(1.0 / args.serve_rate, size=n)
+    n = n_requests or args.serve_requests
+    gaps = rng.exponential(1.0 / rate, size=n)
     drive = rng.random(n) < 0.2
     size_b = np.where(drive, np.exp(rng.uniform(np.log(256 << 20), np.log(16 << 30), n)),
                       np.exp(rng.uniform(np.log(64 << 10), np.log(4 << 20), n)))
@@ -754,6 +769,7 @@ def run_served(torch, cv, synth, args, host):
                 time.sleep(wait)
             tickets[k] = srv.submit((base + int(start[k]) * SECTOR, int(size_s[k]) * SECTOR), tag=k)
 
+    link_before = h2d_link_gbps(torch, host, torch.cuda.current_stream())
     th = threading.Thread(target=submitter)
     t0 = time.perf_counter()
     th.start()
@@ -773,8 +789,9 @@ def run_served(torch, cv, synth, args, host):
     st = srv.stats()
     srv.close()
     m.close()
+    link_after = h2d_link_gbps(torch, host, torch.cuda.current_stream())
     total_b = int(size_s.sum()) * SECTOR
-    return {"workload": f"{n} requests, Poisson {args.serve_rate:g}/s, 80% 64 KiB-4 MiB / 20% 256 MiB-16 GiB, "
+    return {"workload": f"{n} requests, Poisson {rate:g}/s, 80% 64 KiB-4 MiB / 20% 256 MiB-16 GiB, "
                         f"windows of a {pool_sectors * SECTOR / 2**30:.0f} GiB pinned pool, "
                         f"{int(file_nsect.sum())}-sector table, HBM budget {args.serve_budget_gb} GB",
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
@@ -782,9 +799,13 @@ def run_served(torch, cv, synth, args, host):
             "drives_p50_ms": float(np.percentile(lat[drive], 50)), "drives_p99_ms": float(np.percentile(lat[drive], 99)),
             "drives_copy_floor_p99_ms": float(np.percentile(size_s[drive] * SECTOR / (args.h2d_link_gbps * 1e9) * 1e3,
                                                             99)),
+            "h2d_link_GBps_before": link_before, "h2d_link_GBps_after": link_after,
+            "offered_GBps": float(size_s.mean()) * SECTOR * rate / 1e9,
+            "littles_law_mean_live": rate * st["mean_ms"] * 1e-3,
             "host_memory": "cudaHostAlloc (torch pin_memory)",
             "throughput_GBps": total_b / st["wall_s"] / 1e9 if st["wall_s"] else None, "wall_s": wall,
             "bytes": total_b, "iterations": st["iterations"], "units": st["units"],
+            "units_per_scan_launch": st["units"] / max(st["iterations"], 1),
             "mean_live_per_iteration": st["mean_live_per_iteration"],
             "peak_bytes_in_flight": st["peak_bytes_in_flight"], "completed": st["completed"], "failed": st["failed"],
             "bit_exact_vs_plant_log": bool(exact)}
@@ -926,6 +947,9 @@ def main():
     ap.add_argument("--serve-copy-gib", type=float, default=0.0, help="copy bytes queued at once (0: the library's)")
     ap.add_argument("--h2d-link-gbps", type=float, default=211.0, help="host link rate for the drives' copy floor")
     ap.add_argument("--serve-only", action="store_true", help="run only the served section and print its JSON")
+    ap.add_argument("--serve-rate-high", type=float, default=200.0,
+                    help="a second served run at this arrival rate (0: none), to show continuous batching")
+    ap.add_argument("--serve-requests-high", type=int, default=1000)
     ap.add_argument("--sections-out", default="", help="also append every section's JSON line to this file")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -1111,8 +1135,16 @@ def main():
         batched = run_batched(torch, cv, synth, args, stream)
         emit_section(args, "batched", batched)
     if not args.no_serve:
+        # serving gets a pinned pool of its own, allocated here (the e2e buffer above was rewritten
+        # by the host generator of the streamed variant)
+        serve_host = torch.empty(host.numel(), dtype=torch.uint8, pin_memory=True)
+        del host
+        host = serve_host
         served = run_served(torch, cv, synth, args, host)
         emit_section(args, "served", served)
+        if args.serve_rate_high:
+            emit_section(args, "served_high_rate", run_served(torch, cv, synth, args, host, args.serve_rate_high,
+                                                              args.serve_requests_high))
     del host
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -107,9 +107,10 @@ struct TuneChoice {
 };
 std::map<std::string, TuneChoice> g_tune;  // key -> choice
 
-// table_kind: signature, layout and position keying of the table (they change the probe's cost).
-std::string tune_key(const char* gpu, int sms, uint64_t sectors, uint32_t images, uint64_t unique, bool bloom_avail,
-                     uint32_t table_kind) {
+// table_kind: signature, layout and position keying of the table; unique and occupancy (in
+// tenths of the slots): they change the probe's cost and so the choice.
+std::string tune_key(const char* gpu, int sms, uint64_t sectors, uint32_t images, uint64_t unique, uint32_t occupancy,
+                     bool bloom_avail, uint32_t table_kind) {
   auto lg = [](uint64_t x) {
     int b = 0;
     while (x > 1) {
@@ -123,8 +124,8 @@ std::string tune_key(const char* gpu, int sms, uint64_t sectors, uint32_t images
   for (char& ch : name)
     if (ch == ' ' || ch == '\t') ch = '_';
   char buf[256];
-  snprintf(buf, sizeof buf, "%s|%d|s%d|i%d|u%d|b%d|t%u", name.c_str(), sms, lg(sectors), lg(images), lg(unique),
-           bloom_avail ? 1 : 0, table_kind);
+  snprintf(buf, sizeof buf, "%s|%d|s%d|i%d|u%d|o%u|b%d|t%u", name.c_str(), sms, lg(sectors), lg(images), lg(unique),
+           occupancy, bloom_avail ? 1 : 0, table_kind);
   return buf;
 }
 
@@ -296,9 +297,11 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
     if (opts && opts->autotune && total_sectors) {
       cudaDeviceProp prop;
       CV_CUDA(cudaGetDeviceProperties(&prop, ctx->dev));
-      const uint64_t unique = tab.layout == kLayoutSorted ? tab.n_keys : (uint64_t)tab.slot_mask + 1;
+      const uint64_t n_slots = tab.layout == kLayoutSorted ? tab.n_keys : (uint64_t)tab.slot_mask + 1;
+      const uint32_t tenths = (uint32_t)(10ull * tab.n_keys / std::max<uint64_t>(n_slots, 1));
       const uint32_t tkey = (uint32_t)table_kind(tab) * 2u + (tab.tau_mask ? 1u : 0u);
-      const std::string key = tune_key(prop.name, ctx->sms, total_sectors, n_images, unique, bloom_avail, tkey);
+      const std::string key =
+          tune_key(prop.name, ctx->sms, total_sectors, n_images, tab.n_keys, tenths, bloom_avail, tkey);
       TuneChoice tc;
       if (tune_lookup(key, opts->tune_cache, &tc)) {
         cfg_i = tc.cfg;

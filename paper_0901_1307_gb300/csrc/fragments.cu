@@ -34,24 +34,43 @@
 #include "cv_launch.h"
 #include "scan_kernel.cuh"
 
+// The djb2 count kernel's block size, tile buffers per warp and Bloom pipeline depth: the
+// fastest measured on GB300 (4 GiB fragment workload, count kernel, all exact): 512 threads, two
+// buffers, depth 12: 1,431 GB/s; depth 8: 1,425; depth 17: 1,298. With more warps per SM the
+// kernel exceeds its register share and spills: 1024 threads, one buffer, depth 6 / 8 / 12:
+// 1,312 / 971 / 834; 640 threads, two buffers, depth 8: 892; 768, one buffer, depth 8: 883.
+#ifndef CV_FRAG_DJB2_THREADS
+#define CV_FRAG_DJB2_THREADS 512
+#endif
+#ifndef CV_FRAG_DJB2_BUFS
+#define CV_FRAG_DJB2_BUFS 2
+#endif
+#ifndef CV_FRAG_DJB2_BLOOM_DEPTH
+#define CV_FRAG_DJB2_BLOOM_DEPTH 12
+#endif
+
 namespace cvk {
 
 // Tile geometry per signature (a tile is one warp's work).
 template <int SIG>
 struct FragGeom {
   static constexpr bool kRolled = SIG == kSigDjb2;
-  static constexpr int kThreads = kRolled ? 512 : 256;  // block size
+  static constexpr int kThreads = kRolled ? CV_FRAG_DJB2_THREADS : 256;  // block size
   static constexpr int kWarps = kThreads / 32;
   static constexpr int kWPT = kRolled ? 17 : 33;        // windows per lane per tile (odd)
+  static constexpr int kBufs = kRolled ? CV_FRAG_DJB2_BUFS : 2;  // tile buffers per warp (count kernel)
+  static constexpr int kBloomDepth = CV_FRAG_DJB2_BLOOM_DEPTH;  // Bloom words in flight per lane
   static constexpr uint32_t kTileWin = 32 * kWPT;
   static constexpr uint32_t kTileStep = kTileWin * kFragStride;  // bytes between tile starts
   static constexpr uint32_t kTileBytes = kTileStep + 64;         // bytes staged per tile
   static constexpr bool kL1 = kRolled;                           // shared-memory filter
-  static constexpr uint32_t kL1Off = 2 * kWarps * kTileBytes;    // filter after the warps' buffers
+  static constexpr uint32_t kL1Off = kBufs * kWarps * kTileBytes;  // filter after the warps' buffers
   static constexpr uint32_t kSmemCount = kL1Off + (kL1 ? kFragL1Bytes : 0);
   static constexpr uint32_t kSmemEmit = kWarps * kTileBytes;
   static_assert(kWPT % 2 == 1 && kWPT <= 64 && (!kRolled || kWPT <= 32), "odd window count, masks of 64/32 bits");
   static_assert(kTileBytes % 16 == 0 && kTileStep % 16 == 0, "bulk copies of whole 16-byte chunks");
+  static_assert(kBufs == 1 || kBufs == 2, "one or two tile buffers per warp");
+  static_assert(kSmemCount <= 227 * 1024, "shared memory of one block");
 };
 
 __host__ __device__ constexpr uint64_t pow33(int e) {
@@ -160,35 +179,40 @@ __device__ __forceinline__ uint64_t frag_candidates(const FragParams& p, const u
   using G = FragGeom<SIG>;
   uint64_t cand = 0;
   if constexpr (G::kRolled) {
-    // Every window's shared-memory test first (its bit comes from h's high word, d1, with no
-    // further mixing); then, for those that passed, the mixed words d2, d3 and the global Bloom
-    // words, all requested before any is tested.
-    Djb2Roll roll;
-    uint64_t h[G::kWPT];
-    uint32_t pass = 0;
-#pragma unroll
-    for (int i = 0; i < G::kWPT; i++) {
-      h[i] = i == 0 ? roll.first(ws, w0) : roll.next(ws, w0, i);
-      const uint32_t b = (uint32_t)(h[i] >> 32) >> (32 - kFragL1Log2Bits);
-      if ((uint32_t)i < n_valid && (!l1 || ((l1[b >> 5] >> (b & 31)) & 1u))) pass |= 1u << i;
-    }
-    if (!p.tab.use_bloom) return pass;
+    // Window by window: the rolled hash, its shared-memory filter bit (from h's high word, d1,
+    // with no further mixing) and, when that passes, the request of its one-word Bloom filter
+    // word (mixed words d2, d3); each Bloom word is tested kBloomDepth windows later, so that
+    // many requests are in flight per lane while only kBloomDepth are held in registers. A window
+    // that did not pass keeps (word 0, bits 1), which fails the test.
+    constexpr int D = G::kBloomDepth < G::kWPT ? G::kBloomDepth : G::kWPT;
     const uint32_t* bloom = reinterpret_cast<const uint32_t*>(p.tab.bloom);
-    uint32_t wv[G::kWPT], wbits[G::kWPT];
+    const bool use_bloom = p.tab.use_bloom != 0u;
+    Djb2Roll roll;
+    uint32_t wv[D], wbits[D];
 #pragma unroll
-    for (int i = 0; i < G::kWPT; i++) {
-      wv[i] = 0u;
-      wbits[i] = 1u;
-      if ((pass >> i) & 1u) {
-        uint32_t d[4];
-        frag64_words(h[i], d);
-        wbits[i] = frag_bloom_bits(d[2]);
-        wv[i] = __ldg(bloom + (d[3] & p.tab.bloom_mask));
+    for (int i = 0; i < G::kWPT + D; i++) {
+      if (use_bloom && i >= D) {  // window i - D's word, before window i takes its ring slot
+        const int j = i - D;
+        if ((wv[j % D] & wbits[j % D]) == wbits[j % D]) cand |= 1ull << j;
+      }
+      if (i < G::kWPT) {
+        const uint64_t h = i == 0 ? roll.first(ws, w0) : roll.next(ws, w0, i);
+        const uint32_t b = (uint32_t)(h >> 32) >> (32 - kFragL1Log2Bits);
+        const bool pass = (uint32_t)i < n_valid && (!l1 || ((l1[b >> 5] >> (b & 31)) & 1u));
+        if (!use_bloom) {
+          if (pass) cand |= 1ull << i;
+        } else {
+          wv[i % D] = 0u;
+          wbits[i % D] = 1u;
+          if (pass) {
+            uint32_t d[4];
+            frag64_words(h, d);
+            wbits[i % D] = frag_bloom_bits(d[2]);
+            wv[i % D] = __ldg(bloom + (d[3] & p.tab.bloom_mask));
+          }
+        }
       }
     }
-#pragma unroll
-    for (int i = 0; i < G::kWPT; i++)
-      if ((wv[i] & wbits[i]) == wbits[i]) cand |= 1ull << i;
   } else {
 #pragma unroll 1
     for (uint32_t i = 0; i < n_valid; i++) {
@@ -294,14 +318,16 @@ template <int SIG, int LAYOUT>
 __global__ void __launch_bounds__(FragGeom<SIG>::kThreads, 1) frag_count_kernel(const __grid_constant__ FragParams p) {
   using G = FragGeom<SIG>;
   extern __shared__ __align__(128) uint8_t fsm[];
-  __shared__ __align__(8) uint64_t bars[2 * G::kWarps + 1];  // two per warp, the shared-memory filter
+  constexpr int B = G::kBufs;
+  __shared__ __align__(8) uint64_t bars[B * G::kWarps + 1];  // B per warp, the shared-memory filter
   __shared__ uint32_t abort_flag[G::kWarps + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t* l1 = G::kL1 ? reinterpret_cast<const uint32_t*>(fsm + G::kL1Off) : nullptr;
-  uint8_t* mybuf = fsm + 2 * warp * G::kTileBytes;
-  const uint32_t bar0 = smem_addr(&bars[2 * warp]);
+  uint8_t* mybuf = fsm + B * warp * G::kTileBytes;
+  const uint32_t bar0 = smem_addr(&bars[B * warp]);
+  const uint32_t bar_l1 = smem_addr(&bars[B * G::kWarps]);
   if (tid == 0) {
-    for (int b = 0; b < 2 * G::kWarps + 1; b++) mbar_init(smem_addr(&bars[b]), 1);
+    for (int b = 0; b < B * G::kWarps + 1; b++) mbar_init(smem_addr(&bars[b]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (tid <= G::kWarps) abort_flag[tid] = 0;
@@ -309,28 +335,28 @@ __global__ void __launch_bounds__(FragGeom<SIG>::kThreads, 1) frag_count_kernel(
   const uint64_t policy = l2_evict_first_policy();
   const uint64_t n_warps = (uint64_t)gridDim.x * G::kWarps;
   const uint64_t first = (uint64_t)blockIdx.x * G::kWarps + warp;
-  // Buffer s of a warp holds the tiles of its iterations i with i & 1 == s; the k-th of them
-  // completes phase k of the buffer's barrier. Lane 0 issues the first two tiles, then each tile
-  // two iterations ahead.
+  // Buffer s of a warp holds the tiles of its iterations i with i mod B == s; the k-th of them
+  // completes phase k of the buffer's barrier. Lane 0 issues the first B tiles, then each tile
+  // B iterations ahead.
   if (tid == 0 && G::kL1) {
-    mbar_arrive_expect_tx(smem_addr(&bars[2 * G::kWarps]), kFragL1Bytes);
-    bulk_load(smem_addr(fsm + G::kL1Off), p.tab.frag_l1, kFragL1Bytes, smem_addr(&bars[2 * G::kWarps]), policy);
+    mbar_arrive_expect_tx(bar_l1, kFragL1Bytes);
+    bulk_load(smem_addr(fsm + G::kL1Off), p.tab.frag_l1, kFragL1Bytes, bar_l1, policy);
   }
   if (lane == 0)
-    for (int s = 0; s < 2; s++) {
+    for (int s = 0; s < B; s++) {
       const uint64_t t = first + s * n_warps;
       if (t < p.n_tiles) frag_issue<SIG>(p, t, smem_addr(mybuf + s * G::kTileBytes), bar0 + 8 * s, policy);
     }
   bool ok = true;
-  if constexpr (G::kL1) ok = mbar_wait(smem_addr(&bars[2 * G::kWarps]), 0u, &abort_flag[G::kWarps], p.status);
+  if constexpr (G::kL1) ok = mbar_wait(bar_l1, 0u, &abort_flag[G::kWarps], p.status);
   bool aborted = !__syncthreads_and(ok);  // the only block-wide barrier: the filter is in place
   uint64_t i = 0;
   for (; !aborted; i++) {
     const uint64_t tile = first + i * n_warps;
     if (tile >= p.n_tiles) break;
-    const int s = (int)(i & 1);
+    const int s = (int)(i % B);
     uint8_t* buf = mybuf + s * G::kTileBytes;
-    ok = mbar_wait(bar0 + 8 * s, (uint32_t)(i >> 1) & 1u, &abort_flag[warp], p.status);
+    ok = mbar_wait(bar0 + 8 * s, (uint32_t)(i / B) & 1u, &abort_flag[warp], p.status);
     if (!__all_sync(0xFFFFFFFFu, ok)) {
       aborted = true;
       break;
@@ -347,7 +373,7 @@ __global__ void __launch_bounds__(FragGeom<SIG>::kThreads, 1) frag_count_kernel(
     __syncwarp();  // every lane is done with the buffer
     if (lane == 0) {
       p.tile_ntrip[p.tile_base + tile] = n;
-      const uint64_t next = tile + 2 * n_warps;
+      const uint64_t next = tile + B * n_warps;
       if (next < p.n_tiles) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         frag_issue<SIG>(p, next, smem_addr(buf), bar0 + 8 * s, policy);
@@ -356,12 +382,12 @@ __global__ void __launch_bounds__(FragGeom<SIG>::kThreads, 1) frag_count_kernel(
     __syncwarp();
   }
   if (aborted && lane == 0) {
-    // The filter (lane 0 of warp 0) and this warp's iterations i and i + 1 may have copies issued
-    // and not waited for: let them land, each wait bounded, before shared memory goes away.
+    // The filter (lane 0 of warp 0) and this warp's iterations i .. i + B - 1 may have copies
+    // issued and not waited for: let them land, each wait bounded, before shared memory goes away.
     volatile uint32_t never = 0;
-    if (G::kL1 && tid == 0) mbar_wait(smem_addr(&bars[2 * G::kWarps]), 0u, &never, p.status);
-    for (uint64_t j = i; j < i + 2 && first + j * n_warps < p.n_tiles; j++)
-      if (!mbar_wait(bar0 + 8 * (j & 1), (uint32_t)(j >> 1) & 1u, &never, p.status)) break;
+    if (G::kL1 && tid == 0) mbar_wait(bar_l1, 0u, &never, p.status);
+    for (uint64_t j = i; j < i + B && first + j * n_warps < p.n_tiles; j++)
+      if (!mbar_wait(bar0 + 8 * (j % B), (uint32_t)(j / B) & 1u, &never, p.status)) break;
   }
 }
 
