@@ -138,14 +138,19 @@ typedef struct {
   uint32_t flags;             /* CV_KEEP_ON_DEVICE */
   void* stream;               /* cudaStream_t */
   uint64_t chunk_bytes;       /* host images are streamed in chunks of this size; 0 = 256 MiB */
-  uint32_t kernel_config;     /* 0 = the tuned default; k + 1 selects configuration k */
+  uint32_t kernel_config;     /* 0 = the default for the table's signature (MD5 and MD5 without
+                                 padding: configuration 0; djb2-64 and CRC64, whose scans are
+                                 bound by the staging of the image: 128-byte stages of
+                                 128-sector tiles), or the CV_SCAN_CONFIG environment variable's
+                                 configuration (by name) when set; k + 1 selects configuration k */
   uint32_t reserved;
   uint64_t base_offset;       /* position-keyed tables: disk sector of the first cluster (only its
                                  value mod 8 matters); ignored for CV_POSITION_ANY tables. The
                                  size without it (32 bytes) is accepted and means 0. */
 } cv_scan_opts;
 
-/* Kernel configurations of the scan (tile rows, ring stages, staging width). Every
+/* Kernel configurations of the scan (tile rows, sectors per thread, ring stages, staging width,
+ * pipe split of the MD5 additions); each is built for every signature and table layout. Every
  * configuration gives the same results; they differ in speed. */
 int cv_kernel_config_count(void);
 const char* cv_kernel_config_name(int k); /* NULL when k is out of range */
@@ -355,7 +360,7 @@ typedef struct {
   uint32_t autotune;        /* 1: tune kernel configuration, table layout and Bloom use on this batch */
   void* stream;             /* cudaStream_t for set-up and tuning */
   uint64_t match_capacity;  /* output room in matches; 0 = size it from one scan at set-up */
-  uint32_t kernel_config;   /* 0 = default (or tuned); k + 1 = configuration k */
+  uint32_t kernel_config;   /* 0 = the signature's default (or tuned); k + 1 = configuration k */
   uint32_t bloom;           /* CV_BATCH_BLOOM_* (ignored when tuning) */
   const char* tune_cache;   /* file for tuned choices, or NULL */
   uint32_t sorted_copy;     /* 1: scan a sorted copy of a CV_LAYOUT_HASH master (the batch builds
@@ -407,7 +412,7 @@ typedef struct {
   uint32_t max_live;         /* requests admitted at once; 0 = 64 */
   uint64_t hbm_budget_bytes; /* device arena for request data in flight; 0 = 8 GiB */
   uint64_t work_unit_bytes;  /* request data per work unit (multiple of 512); 0 = 64 MiB */
-  uint32_t kernel_config;    /* 0 = default; k + 1 = configuration k */
+  uint32_t kernel_config;    /* 0 = the signature's default; k + 1 = configuration k */
   uint32_t copy_streams;     /* host-to-device copy streams; 0 = 2 */
   uint64_t max_copy_bytes;   /* request data queued on the copy streams at once, at least one work
                                 unit; more is issued as copies land, first to the live request with

@@ -224,7 +224,7 @@ int cv_batch_create(const cv_master* m, const cv_buf* images, uint32_t n_images,
     if (k != kDevice) return CV_EINVAL;
   }
   const bool bloom_avail = tab.use_bloom != 0;
-  int cfg_i = ctx->cfg_index;
+  int cfg_i = ctx->default_config(table_kind(tab));
   int bloom = bloom_avail ? 1 : 0;
   if (opts && opts->kernel_config) {
     if (opts->kernel_config > (uint32_t)ncfg) return CV_EINVAL;

@@ -335,7 +335,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
   if (m->tab.unit == kUnitFragment) return frag_scan(ctx, m, images, n_images, flags, stream, out);
   int ncfg;
   scan_configs(&ncfg);
-  int cfg_i = ctx->cfg_index;
+  int cfg_i = ctx->default_config(table_kind(m->tab));
   if (opts && opts->kernel_config) {
     if (opts->kernel_config > (uint32_t)ncfg) return CV_EINVAL;
     cfg_i = (int)opts->kernel_config - 1;

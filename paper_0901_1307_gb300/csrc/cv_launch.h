@@ -32,6 +32,8 @@ inline int table_kind(const TableView& t) { return (int)t.sig + 4 * (int)t.layou
 // Configuration cfg_i if it has a scan kernel for table kind `kind` (table_kind), else the
 // default one (index 0, which has every kind); *used receives the index in use.
 const ScanCfg& scan_config_for(int cfg_i, int kind, int* used);
+// The default scan configuration for a table kind (the fastest measured for its signature).
+int preferred_config(int kind);
 // Configuration cfg_i if it has a digest-mode kernel for signature sig, else the default one.
 const ScanCfg& digest_config_for(int cfg_i, int sig, int* used);
 

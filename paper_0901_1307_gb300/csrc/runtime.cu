@@ -103,7 +103,7 @@ int get_ctx(DevCtx** out) {
     }
     if (!cfgs[0].digest_fn[0]) return CV_ECUDA;  // the default configuration serves every digest pass
 
-    c.cfg_index = 0;
+    c.cfg_index = -1;
     const char* env = getenv("CV_SCAN_CONFIG");
     if (env && *env) {
       int k = find_cfg(env);

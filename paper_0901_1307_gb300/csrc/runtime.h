@@ -62,7 +62,10 @@ struct DevCtx {
   PFN_cuMemGetAddressRange_v3020 address_range = nullptr;
   std::vector<std::array<int, kTableKinds>> blocks_per_sm;  // per scan configuration and table kind
   std::vector<int> blocks_per_sm_digest;  // per scan configuration (0: no digest-mode kernels)
-  int cfg_index = 0;  // default scan configuration
+  int cfg_index = -1;  // scan configuration forced by CV_SCAN_CONFIG, or -1: per table kind
+
+  // The scan configuration for a table kind when the caller asks for the default.
+  int default_config(int kind) const { return cfg_index >= 0 ? cfg_index : preferred_config(kind); }
 };
 
 int get_ctx(DevCtx** out);

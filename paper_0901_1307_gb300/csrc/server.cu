@@ -481,7 +481,7 @@ int cv_server_create(const cv_master* m, const cv_server_opts* opts, cv_server**
   if (ctx->dev != mdev) return CV_EINVAL;
   int ncfg;
   const ScanCfg* cfgs = scan_configs(&ncfg);
-  int cfg_i = ctx->cfg_index;
+  int cfg_i = ctx->default_config(table_kind(tab));
   if (opts && opts->kernel_config) {
     if (opts->kernel_config > (uint32_t)ncfg) return CV_EINVAL;
     cfg_i = (int)opts->kernel_config - 1;
