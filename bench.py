@@ -259,16 +259,22 @@ def expected_window(expect: np.ndarray, a: int, n: int) -> np.ndarray:
 
 def run_signatures(torch, cv, synth, plan, image, stream, steps):
     """The same device-resident scan with the paper's other signatures: MD5 without padding,
-    djb2-64 and CRC64 (64-bit ones confirmed byte for byte on the device)."""
+    djb2-64 and CRC64 (64-bit ones confirmed byte for byte on the device), each with its default
+    kernel configuration and each result checked against the plant log."""
     masters, files = device_masters(torch, plan)
     out = {}
-    ref_matches = None
+    want = plan.expected_intact()
+    names = cv.kernel_configs()
     for sig, name in ((0, "md5"), (1, "md5_nopad"), (2, "djb2_64"), (3, "crc64")):
         m = cv.master_build(files, signature=sig)
         wall, kms, matches = time_scans(torch, cv, m, image, stream, steps)
-        ref_matches = matches if ref_matches is None else ref_matches
+        r = cv.scan(m, [image], stream=stream)
+        exact = bool(np.array_equal(r.matches(0), want))
+        st = r.stats()
+        r.close()
         out[name] = {"GBps": plan.n_bytes / wall / 1e9, "kernel_GBps": plan.n_bytes / (kms * 1e-3) / 1e9,
-                     "matches": matches, "same_matches_as_md5": matches == ref_matches}
+                     "matches": matches, "bit_exact_vs_plant_log": exact, "kernel_config": names[st["kernel_config"]],
+                     "confirm_rejected": st["confirm_rejected"]}
         m.close()
     # the paper's position-keyed tables S_tau on the same image (clusters from sector 0)
     m = cv.master_build(files, position_mode=cv.CV_POSITION_CLUSTER)
@@ -1041,7 +1047,7 @@ def main():
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    kernel_ms, matches, launches, hit_sectors = [], 0, 0, 0
+    kernel_ms, matches, launches, hit_sectors, used_config = [], 0, 0, 0, 0
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -1053,6 +1059,7 @@ def main():
             kernel_ms.append(st["kernel_ms"])
             matches = st["matches"]
             hit_sectors = st["hit_sectors"]
+            used_config = st["kernel_config"]
             launches += st["kernel_launches"]
             r.close()
         e1.record(stream)
@@ -1149,7 +1156,7 @@ def main():
         cpu = cpu_baseline(plan, args.cpu_sample_pieces)
         emit_section(args, "cpu_baseline", cpu)
     line = headline(value=value, world=world, args=args, ms=ms, nbytes=nbytes, sectors=sectors, plan=plan,
-                    kernel_config=cv.kernel_configs()[args.kernel_config - 1] if args.kernel_config else "default",
+                    kernel_config=cv.kernel_configs()[used_config] + ("" if args.kernel_config else " (default)"),
                     matches=matches, exact=exact, roof=roof, clocks=clocks, e2e=e2e, cpu=cpu, launches=launches,
                     batched=batched, served=served)
     if rank == 0:

@@ -222,7 +222,8 @@ typedef struct {
   float kernel_ms;         /* device time of the hashing/probe launches */
   float total_ms;          /* device time from the first copy to the last result copy */
   uint32_t kernel_launches; /* kernels the call launched (scan, offsets, expand) */
-  uint32_t reserved;
+  int32_t kernel_config;   /* the scan configuration used (cv_kernel_config_name), -1 for
+                              fragment scans and results of the serving loop */
   uint64_t confirm_rejected; /* 64-bit signatures: candidate (disk sector, master sector or
                                 fragment) pairs whose signatures were equal but whose bytes
                                 differed, dropped by the byte confirmation (Section 3.1); 0 for

@@ -159,6 +159,7 @@ cv_result* make_host_result(int dev, const MatchOut* data, uint64_t n, uint64_t 
   r->st.sectors = sectors;
   r->st.matches = n;
   r->st.total_ms = total_ms;
+  r->st.kernel_config = -1;
   r->launches = 0;
   if (n) {
     r->host = (MatchOut*)malloc(n * sizeof(MatchOut));
@@ -294,6 +295,7 @@ int frag_scan(DevCtx* ctx, const cv_master* m, const cv_buf* images, uint32_t n_
       CV_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[3]));
       r->st.total_ms = ms;
       r->st.kernel_launches = (uint32_t)r->launches;
+      r->st.kernel_config = -1;
       if (total && !r->on_device) {
         CV_CUDA(cudaFreeAsync(r->dev_out, stream));
         r->dev_out = nullptr;
@@ -529,6 +531,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
       CV_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[3]));
       r->st.total_ms = ms;
       r->st.kernel_launches = (uint32_t)r->launches;
+      r->st.kernel_config = cfg_i;
       if (total && !r->on_device) {
         CV_CUDA(cudaFreeAsync(r->dev_out, stream));
         r->dev_out = nullptr;

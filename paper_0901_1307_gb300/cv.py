@@ -83,7 +83,7 @@ class cv_master_info(ctypes.Structure):
 class cv_scan_stats(ctypes.Structure):
     _fields_ = [("sectors", ctypes.c_uint64), ("matches", ctypes.c_uint64), ("hit_sectors", ctypes.c_uint64),
                 ("kernel_ms", ctypes.c_float), ("total_ms", ctypes.c_float), ("kernel_launches", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("confirm_rejected", ctypes.c_uint64)]
+                ("kernel_config", ctypes.c_int32), ("confirm_rejected", ctypes.c_uint64)]
 
 
 class cv_probe_stats(ctypes.Structure):

@@ -353,6 +353,26 @@ def test_every_kernel_config_serves_every_table_kind(cv, cfg):
                 assert_same(r.matches(0), want, f"config {cfg} sig {sig}")
 
 
+def test_scan_reports_configuration_and_signature_defaults(cv):
+    """cv_scan_stats.kernel_config names the configuration a scan used: by default configuration
+    0 for MD5 and MD5 without padding, the 128-byte-stage one for djb2-64 and CRC64 (their scans
+    are bound by staging), or the one the caller selects; the result is the same in every case."""
+    files, whole, images, wants = _batch_images(6, 49)
+    names = cv.kernel_configs()
+    light = names.index("t128_x1_s2_b128_p2")
+    for sig, expect in ((0, 0), (1, 0), (2, light), (3, light)):
+        with cv.master_build(files, signature=sig) as m:
+            with cv.scan(m, [images[1]]) as r:
+                assert r.stats()["kernel_config"] == expect
+                assert_same(r.matches(0), wants[1], f"sig {sig}")
+            with cv.scan(m, [images[1]], kernel_config=3) as r:
+                assert r.stats()["kernel_config"] == 2
+                assert_same(r.matches(0), wants[1], f"sig {sig} config 2")
+    frag_files = [f[: f.size // 64 * 64] for f in files]
+    with cv.master_build(frag_files, unit=cv.CV_UNIT_FRAGMENT) as m, cv.scan(m, [images[1]]) as r:
+        assert r.stats()["kernel_config"] == -1
+
+
 def test_batch_capacity_overflow_reported(cv):
     files, whole, images, wants = _batch_images(12, 33)
     total = sum(w.size for w in wants)
