@@ -1109,7 +1109,7 @@ def main():
         e2e["h2d_link_GBps_before"] = link_before
         e2e["h2d_link_GBps"] = link
         e2e["frac_of_h2d_link"] = e2e["value"] / world / max(link, link_before)
-        if not args.no_streamed:
+        if not args.no_streamed and rank == 0:  # host-bound and not part of the scaled metric
             e2e["streamed"] = run_streamed(torch, cv, synth, plan, master, host, stream, args.streamed_gib, link)
 
     if e2e is not None:
@@ -1136,10 +1136,11 @@ def main():
     emit_section(args, "roofline_detail", roof.pop("detail"))
     master.close()
     batched = served = None
-    if not args.no_batch:
+    # the batched and served workloads are single-GPU configurations: rank 0 runs them
+    if not args.no_batch and rank == 0:
         batched = run_batched(torch, cv, synth, args, stream)
         emit_section(args, "batched", batched)
-    if not args.no_serve:
+    if not args.no_serve and rank == 0:
         # serving gets a pinned pool of its own, allocated here (the e2e buffer above was rewritten
         # by the host generator of the streamed variant)
         serve_host = torch.empty(host.numel(), dtype=torch.uint8, pin_memory=True)
