@@ -23,7 +23,7 @@ MUTANTS = {
     "round-3 message index": ("(5 + 3 * j) % 16", "(3 + 5 * j) % 16"),
     "round-3 function": ("return x ^ y ^ z;", "return x ^ y ^ ~z;"),
     "round-4 function": ("return y ^ (x | ~z);", "return y ^ (x | z);"),
-    "round-1 function": ("return (x & y) | (~x & z);", "return (x & y) | (x & z);"),
+    "MD5 F function (first 16 operations)": ("return (x & y) | (~x & z);", "return (x & y) | (x & z);"),
     "sine index": ("T_sine[i + 1]", "T_sine[i]"),
     "sine scale": ("4294967296.0 * fabs", "4294967295.0 * fabs"),
     "padding boundary": ("(rem < 56) ? 64 : 128", "(rem <= 56) ? 64 : 128"),
