@@ -97,14 +97,21 @@ struct ScanBatch {
   uint64_t* off_scratch = nullptr;
   uint64_t* counters_d = nullptr;  // seg_off[nseg], total, status
   uint64_t* counters_h = nullptr;
+  Segment* segs_h = nullptr;       // pinned staging of the segment list
   MatchOut* out_d = nullptr;
   MatchOut* out_h = nullptr;
+  cudaMemPool_t pool = nullptr;           // device buffers: stream-ordered on `stream`
+  std::vector<void*> retired_host;        // pinned buffers outgrown, freed with the batch
 
   int ensure_buffers(uint64_t tiles, uint64_t segs, uint64_t out);
   void release();
 };
 
 constexpr int kBatchesInFlight = 2;
+// Work units one scan launch takes at most (64 MiB units: 4 GiB of data, about a millisecond of
+// scanning), so that each batch's buffers are sized once, when the server is made.
+constexpr size_t kMaxUnitsPerBatch = 64;
+constexpr uint64_t kInitialMatches = 1ull << 22;  // matches a batch holds before it must grow
 
 }  // namespace
 
@@ -157,34 +164,52 @@ struct cv_server {
 
 namespace {
 
+// Buffers for tiles output tiles, segs segments and out matches. They are sized once when the
+// server is made (kMaxUnitsPerBatch units, kInitialMatches matches) and grow only if a batch
+// needs more: device buffers are then reallocated in stream order on the batch's stream (no
+// device-wide synchronization, so copies queued on the copy streams keep flowing), and the
+// outgrown pinned host buffers are kept until the server is freed (freeing pinned memory
+// synchronizes the device).
 int ScanBatch::ensure_buffers(uint64_t tiles, uint64_t segs, uint64_t out) {
+  auto dev_alloc = [&](void** p, size_t bytes) -> int {
+    CV_CUDA(cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, stream));
+    return CV_OK;
+  };
+  auto dev_free = [&](void* p) {
+    if (p) cudaFreeAsync(p, stream);
+  };
   if (tiles > cap_tiles || !hit_rec) {
     uint64_t c = std::max<uint64_t>(tiles, cap_tiles * 2);
     for (void* p : {(void*)hit_rec, (void*)tile_nhit, (void*)tile_ntrip, (void*)tile_off, (void*)off_scratch})
-      if (p) cudaFree(p);
+      dev_free(p);
     hit_rec = nullptr;
-    CV_CUDA(cudaMalloc((void**)&hit_rec, c * 32 * sizeof(uint4)));
-    CV_CUDA(cudaMalloc((void**)&tile_nhit, c * 4));
-    CV_CUDA(cudaMalloc((void**)&tile_ntrip, c * 8));
-    CV_CUDA(cudaMalloc((void**)&tile_off, c * 8));
-    CV_CUDA(cudaMalloc((void**)&off_scratch, tile_offsets_scratch_words(c) * 8));
+    CV_TRY(dev_alloc((void**)&hit_rec, c * 32 * sizeof(uint4)));
+    CV_TRY(dev_alloc((void**)&tile_nhit, c * 4));
+    CV_TRY(dev_alloc((void**)&tile_ntrip, c * 8));
+    CV_TRY(dev_alloc((void**)&tile_off, c * 8));
+    CV_TRY(dev_alloc((void**)&off_scratch, tile_offsets_scratch_words(c) * 8));
     cap_tiles = c;
   }
   if (segs > cap_segs || !segs_d) {
     uint64_t c = std::max<uint64_t>(segs, cap_segs * 2);
-    if (segs_d) cudaFree(segs_d);
-    if (counters_d) cudaFree(counters_d);
-    if (counters_h) cudaFreeHost(counters_h);
-    CV_CUDA(cudaMalloc((void**)&segs_d, c * sizeof(Segment)));
-    CV_CUDA(cudaMalloc((void**)&counters_d, (c + 2) * 8));
+    dev_free(segs_d);
+    dev_free(counters_d);
+    if (counters_h) retired_host.push_back(counters_h);
+    if (segs_h) retired_host.push_back(segs_h);
+    counters_h = nullptr;
+    segs_h = nullptr;
+    CV_TRY(dev_alloc((void**)&segs_d, c * sizeof(Segment)));
+    CV_TRY(dev_alloc((void**)&counters_d, (c + 2) * 8));
     CV_CUDA(cudaMallocHost((void**)&counters_h, (c + 2) * 8));
+    CV_CUDA(cudaMallocHost((void**)&segs_h, c * sizeof(Segment)));
     cap_segs = c;
   }
   if (out > cap_out || !out_d) {
     uint64_t c = std::max<uint64_t>(std::max<uint64_t>(out, 1024), cap_out * 2);
-    if (out_d) cudaFree(out_d);
-    if (out_h) cudaFreeHost(out_h);
-    CV_CUDA(cudaMalloc((void**)&out_d, c * sizeof(MatchOut)));
+    dev_free(out_d);
+    if (out_h) retired_host.push_back(out_h);
+    out_h = nullptr;
+    CV_TRY(dev_alloc((void**)&out_d, c * sizeof(MatchOut)));
     CV_CUDA(cudaMallocHost((void**)&out_h, c * sizeof(MatchOut)));
     cap_out = c;
   }
@@ -193,16 +218,18 @@ int ScanBatch::ensure_buffers(uint64_t tiles, uint64_t segs, uint64_t out) {
 
 void ScanBatch::release() {
   if (stream) {
+    for (void* p : {(void*)segs_d, (void*)hit_rec, (void*)tile_nhit, (void*)tile_ntrip, (void*)tile_off,
+                    (void*)off_scratch, (void*)counters_d, (void*)out_d})
+      if (p) cudaFreeAsync(p, stream);
     cudaStreamSynchronize(stream);
     cudaStreamDestroy(stream);
   }
   if (counts_ready) cudaEventDestroy(counts_ready);
   if (matches_ready) cudaEventDestroy(matches_ready);
-  for (void* p : {(void*)segs_d, (void*)hit_rec, (void*)tile_nhit, (void*)tile_ntrip, (void*)tile_off,
-                  (void*)off_scratch, (void*)counters_d, (void*)out_d})
-    if (p) cudaFree(p);
   if (counters_h) cudaFreeHost(counters_h);
+  if (segs_h) cudaFreeHost(segs_h);
   if (out_h) cudaFreeHost(out_h);
+  for (void* p : retired_host) cudaFreeHost(p);
 }
 
 }  // namespace
@@ -272,7 +299,7 @@ int cv_server::launch_scan(ScanBatch& b, const std::vector<Request*>& work, bool
   b.refs.clear();
   for (Request* r : work) {
     bool any = false;
-    while (r->next_scan < r->units.size()) {
+    while (r->next_scan < r->units.size() && b.refs.size() < kMaxUnitsPerBatch) {
       Unit& u = r->units[r->next_scan];
       if (!r->device) {
         if (!u.copied) break;
@@ -308,7 +335,8 @@ int cv_server::launch_scan(ScanBatch& b, const std::vector<Request*>& work, bool
   b.nseg = job.segs.size();
   b.n_out = job.n_tiles * (uint64_t)(cfg.T / 32);
   CV_TRY(b.ensure_buffers(b.n_out, b.nseg, 0));
-  CV_CUDA(cudaMemcpyAsync(b.segs_d, job.segs.data(), b.nseg * sizeof(Segment), cudaMemcpyHostToDevice, b.stream));
+  memcpy(b.segs_h, job.segs.data(), b.nseg * sizeof(Segment));
+  CV_CUDA(cudaMemcpyAsync(b.segs_d, b.segs_h, b.nseg * sizeof(Segment), cudaMemcpyHostToDevice, b.stream));
   uint32_t* status = (uint32_t*)(b.counters_d + b.nseg + 1);
   CV_CUDA(cudaMemsetAsync(status, 0, 8, b.stream));
   ScanParams p;
@@ -511,10 +539,15 @@ int cv_server_create(const cv_master* m, const cv_server_opts* opts, cv_server**
   auto body = [&]() -> int {
     CV_CUDA(cudaMalloc((void**)&s->arena, slots * unit));
     CV_TRY(make_tmap(ctx, cfgs[cfg_i], s->arena, slots * unit / kSector, &s->arena_map));
+    const uint64_t batch_units = std::min<uint64_t>(kMaxUnitsPerBatch, slots);
+    const uint64_t batch_tiles = batch_units * ((s->unit_sectors + cfgs[cfg_i].T - 1) / cfgs[cfg_i].T) *
+                                 (uint64_t)(cfgs[cfg_i].T / 32);
     for (ScanBatch& b : s->batch) {
       CV_CUDA(cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking));
       CV_CUDA(cudaEventCreateWithFlags(&b.counts_ready, cudaEventDisableTiming));
       CV_CUDA(cudaEventCreateWithFlags(&b.matches_ready, cudaEventDisableTiming));
+      b.pool = ctx->pool;
+      CV_TRY(b.ensure_buffers(batch_tiles, kMaxUnitsPerBatch, kInitialMatches));
     }
     for (uint32_t k = 0; k < n_copy; k++) {
       cudaStream_t cs;
