@@ -412,6 +412,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
       uint64_t total = 0;
       std::vector<uint64_t> seg_off(nseg + 4, 0);
       uint32_t* status_keep = nullptr;
+      bool expanded_early = false;  // the expand pass ran before the count came back, and sufficed
       if (nseg) {
         void* ring[2] = {nullptr, nullptr};
         if (!hchunks.empty()) {
@@ -492,19 +493,44 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
                                                  seg_off_d, total_d, off_scratch, stream));
         CV_CUDA((cudaError_t)launch_sum_u32(tile_nhit, n_out, seg_off_d + nseg + 2, ctx->sms, stream));
         r->launches += 1;
+        // The expand pass needs an output buffer before the exact count is known on the host.
+        // After a scan against the same table it is launched at once, with room for a quarter more
+        // than that scan's matches (one wait for the whole call); the exact count then tells
+        // whether the room sufficed (the pass writes nothing beyond it and flags the overflow),
+        // and only if not is it run again into an exact buffer.
+        const uint64_t hint = __atomic_load_n(&const_cast<cv_master*>(m)->last_matches, __ATOMIC_RELAXED);
+        uint64_t room = 0;
+        if (hint) {
+          room = hint + hint / 4 + 1024;
+          CV_CUDA(cudaMallocFromPoolAsync((void**)&r->dev_out, room * sizeof(MatchOut), ctx->pool, stream));
+          CV_CUDA((cudaError_t)launch_expand(cfg, hit_rec, tile_nhit, tile_off, n_out, segs_d, nseg32, tab,
+                                             r->dev_out, room, status, ctx->sms, stream));
+          r->launches += 1;
+        }
         CV_CUDA(cudaMemcpyAsync(seg_off.data(), seg_off_d, (nseg + 4) * 8, cudaMemcpyDeviceToHost, stream));
         CV_CUDA(cudaStreamSynchronize(stream));
         const uint32_t st = (uint32_t)seg_off[nseg + 1];
         if (st & kStTimeout) return CV_ETIMEOUT;
-        if (st) return CV_ECORRUPT;
+        if (st & ~kStOverflow) return CV_ECORRUPT;
         total = seg_off[nseg];
         r->st.hit_sectors = seg_off[nseg + 2];
         r->st.confirm_rejected = seg_off[nseg + 3];
-        if (total) {
+        __atomic_store_n(&const_cast<cv_master*>(m)->last_matches, total, __ATOMIC_RELAXED);
+        if (total > room) {
+          if (r->dev_out) {
+            CV_CUDA(cudaFreeAsync(r->dev_out, stream));
+            r->dev_out = nullptr;
+          }
+          CV_CUDA(cudaMemsetAsync(status, 0, 4, stream));
           CV_CUDA(cudaMallocFromPoolAsync((void**)&r->dev_out, total * sizeof(MatchOut), ctx->pool, stream));
           CV_CUDA((cudaError_t)launch_expand(cfg, hit_rec, tile_nhit, tile_off, n_out, segs_d, nseg32, tab,
                                              r->dev_out, total, status, ctx->sms, stream));
           r->launches += 1;
+        } else if (r->dev_out && !total) {
+          CV_CUDA(cudaFreeAsync(r->dev_out, stream));
+          r->dev_out = nullptr;
+        } else {
+          expanded_early = true;
         }
         r->launches += 4;  // the offset pass
       }
@@ -519,7 +545,8 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         CV_CUDA(cudaMemcpyAsync(r->host, r->dev_out, total * sizeof(MatchOut), cudaMemcpyDeviceToHost, stream));
       }
       uint32_t st2 = 0;
-      if (nseg && total) CV_CUDA(cudaMemcpyAsync(&st2, status_keep, 4, cudaMemcpyDeviceToHost, stream));
+      if (nseg && total && !expanded_early)
+        CV_CUDA(cudaMemcpyAsync(&st2, status_keep, 4, cudaMemcpyDeviceToHost, stream));
       CV_CUDA(cudaEventRecord(ev[3], stream));
       CV_CUDA(cudaStreamSynchronize(stream));
       if (st2) return CV_ECORRUPT;
@@ -596,10 +623,9 @@ void cv_free(void* handle) {
   } else if (magic == kMagicResult) {
     cv_result* r = (cv_result*)handle;
     r->magic = 0;
-    if (r->dev_out) {
-      cudaFreeAsync(r->dev_out, r->free_stream);
-      cudaStreamSynchronize(r->free_stream);
-    }
+    // Results are complete when cv_scan returns, so the buffer goes back to the pool in stream
+    // order, without waiting.
+    if (r->dev_out) cudaFreeAsync(r->dev_out, r->free_stream);
     free(r->host);
     delete r;
   }

@@ -29,6 +29,10 @@ struct cv_master {
   void* keys0;    // sorted layout: h0 of every record
   void* frag_l1;  // fragment tables: the shared-memory filter
   cv_master_info info;
+  // Matches of the last sector scan against this table (read and written atomically): the
+  // next scan launches its expand pass with room for a quarter more, without waiting for the
+  // exact count first.
+  uint64_t last_matches;
 };
 
 struct cv_result {
