@@ -373,6 +373,28 @@ def test_scan_reports_configuration_and_signature_defaults(cv):
         assert r.stats()["kernel_config"] == -1
 
 
+def test_scan_output_room_follows_previous_scans(cv):
+    """A scan launches its expand pass with room sized from the previous scan against the same
+    table: scans whose match counts rise (room too small: the pass reruns into an exact buffer)
+    and fall (room to spare), an image with no sectors, host and device results, all equal the
+    oracle's."""
+    big = synth.config_plan("small:60000:200:53")
+    small = synth.make_plan(54, 5000, big.file_nsect, 0.1, master_seed=big.master_seed)
+    files = big.masters_host()
+    imgs = {"big": big.image_host(), "small": small.image_host(), "empty": np.zeros(100, np.uint8)}
+    wants = {k: oracle.match_hash(v, files) for k, v in imgs.items()}
+    assert wants["big"].size > 1.25 * wants["small"].size + 1024 and wants["small"].size > 0
+    devs = {k: dev(v) for k, v in imgs.items()}
+    with cv.master_build(files) as m:
+        for step, k in enumerate(["small", "big", "big", "small", "empty", "big", "small"]):
+            with cv.scan(m, [devs[k]]) as r:
+                assert_same(r.matches(0), wants[k], f"step {step} {k}")
+            with cv.scan(m, [devs[k]], keep_on_device=True) as r:
+                assert r.count(0) == wants[k].size
+                if wants[k].size:
+                    assert_same(cv.device_matches_to_numpy(r.matches(0)), wants[k], f"step {step} {k}, on device")
+
+
 def test_batch_capacity_overflow_reported(cv):
     files, whole, images, wants = _batch_images(12, 33)
     total = sum(w.size for w in wants)
