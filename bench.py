@@ -575,6 +575,7 @@ def run_batched(torch, cv, synth, args, stream):
     e1.record(stream)
     n_match = b.wait()
     graph_ms = e0.elapsed_time(e1) / args.batch_runs
+    scan_ms = b.info()["scan_ms"]  # the scan launch of the last run, inside the graph
     exact = n_match == sum(e.size for e in expects)
     for i in range(0, len(images), max(1, len(images) // 16)):
         exact = exact and np.array_equal(cv.device_matches_to_numpy(b.matches(i)), expects[i])
@@ -598,6 +599,7 @@ def run_batched(torch, cv, synth, args, stream):
             "workload": f"{len(images)} images, {total * SECTOR / 2**30:.0f} GiB, log-uniform 1 MiB-2 GiB scaled, "
                         f"{args.batch_density:.0%} of clusters planted from a {int(file_nsect.sum())}-sector table",
             "graph_GBps": total * SECTOR / (graph_ms * 1e-3) / 1e9, "graph_ms_per_run": graph_ms,
+            "scan_launch_ms": scan_ms, "scan_launch_GBps": total * SECTOR / (scan_ms * 1e-3) / 1e9 if scan_ms else None,
             "sequential_GBps": total * SECTOR / seq_s / 1e9, "sequential_ms": seq_s * 1e3,
             "speedup_vs_sequential": (seq_s * 1e3) / graph_ms, "kernel_config": info["config_name"],
             "bloom": info["bloom"], "tuned": info["tuned"], "tune_s": tune_s, "kernel_nodes": info["kernel_launches"],

@@ -86,9 +86,14 @@ int enqueue_run(DevCtx* ctx, int cfg_i, const TableView& tab, const Job& job, co
   p.tile_nhit = b.tile_nhit;
   p.tile_ntrip = b.tile_ntrip;
   p.status = status;
-  if (ev0) CV_CUDA(cudaEventRecord(ev0, stream));
+  // Under stream capture a plain record only orders the capture; the external flag makes it an
+  // event-record node that every replay of the graph executes, so the timing events see each run.
+  cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+  CV_CUDA(cudaStreamIsCapturing(stream, &cap_st));
+  const unsigned rec_flags = cap_st == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+  if (ev0) CV_CUDA(cudaEventRecordWithFlags(ev0, stream, rec_flags));
   CV_TRY(launch_range(ctx, cfg_i, false, job, b.segs_d, 0, nseg, p, stream, launches));
-  if (ev1) CV_CUDA(cudaEventRecord(ev1, stream));
+  if (ev1) CV_CUDA(cudaEventRecordWithFlags(ev1, stream, rec_flags));
   uint64_t* total_d = b.counters_d + nseg;
   CV_CUDA((cudaError_t)launch_tile_offsets(b.tile_ntrip, n_out, b.tile_off, b.segs_d, (uint32_t)nseg,
                                            (uint32_t)(cfg.T / 32), b.counters_d, total_d, b.off_scratch, stream));

@@ -280,6 +280,8 @@ def test_batch_graph_equals_oracle_per_image(cv, autotune, tmp_path):
                 assert total == sum(w.size for w in wants)
                 for k in range(len(images)):
                     assert_same(cv.device_matches_to_numpy(b.matches(k)), wants[k], f"run {run} image {k}")
+                # the scan launch inside the graph is timed on every replay
+                assert b.info()["scan_ms"] > 0, run
         if autotune:
             assert open(cache).read().strip()
             with cv.batch_create(m, images, autotune=True, tune_cache=cache) as b2:
