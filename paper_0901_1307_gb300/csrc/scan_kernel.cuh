@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
   static_assert(T % 32 == 0 && T <= 1024 && C % 32 == 0 && T % kBoxes == 0 && kBoxRows % 8 == 0, "tile rows");
   static_assert(SPT == 1 || SPT == 2, "sectors per thread");
   static_assert(BOXB == 64 || BOXB == 128, "box width");
+  static_assert(NS <= 512 / BOXB, "at most a tile of stages in flight (the segment hand-off)");
   using L = ScanSmem<T, NS, BOXB>;
   constexpr int kChunks = 512 / BOXB;         // stages per sector
   constexpr int kBlocksPerChunk = BOXB / 64;  // MD5 blocks per stage
@@ -246,6 +247,10 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
   const uint32_t bar_full = base + L::kBarOff;  // NS x 8 bytes
   const uint32_t bar_empty = bar_full + NS * 8;
   volatile uint32_t* const s_abort = reinterpret_cast<uint32_t*>(gbase + L::kMiscOff);
+  // The segment of the block's k-th tile, found by the producer (a binary search over the
+  // launch's segments) and read by the hashing warps after the tile's first stage, so that they
+  // do not each repeat the search: two entries, by the parity of k.
+  volatile uint32_t* const s_seg = reinterpret_cast<uint32_t*>(gbase + L::kMiscOff + 8);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -257,6 +262,7 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
       mbar_init(bar_empty + 8 * s, C);
     }
     *s_abort = 0u;
+    s_seg[0] = s_seg[1] = 0u;  // in range even if a wait gives up before the producer writes
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -269,7 +275,8 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
     bool ok = true;
     for (uint64_t lt = blockIdx.x; lt < p.n_tiles && ok; lt += gridDim.x) {
       const uint64_t tile = p.tile_begin + lt;
-      const Segment& seg = p.segs[find_segment(p.segs, p.n_segs, tile)];
+      const uint32_t sg = find_segment(p.segs, p.n_segs, tile);
+      const Segment& seg = p.segs[sg];
       const CUtensorMap* map = &p.maps[seg.map - p.map_base];
       const int32_t row0 = (int32_t)(seg.row_base + (tile - seg.tile_base) * T);
       for (int c = 0; c < kChunks; c++, j++) {
@@ -278,6 +285,10 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
           ok = false;
           break;
         }
+        // published by the arrive below (release), seen after the matching wait (acquire); the
+        // entry is rewritten for the tile after next, whose first copy waits for every hashing
+        // thread to release a stage of the next tile, long after it read this one
+        if (c == 0) s_seg[(j / kChunks) & 1] = sg;
         mbar_arrive_expect_tx(bar_full + 8 * s, L::kStageBytes);
 #pragma unroll
         for (int k = 0; k < kBoxes; k++)
@@ -314,9 +325,7 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
   uint32_t j = 0;
   for (uint64_t lt = blockIdx.x; lt < p.n_tiles; lt += gridDim.x) {
     const uint64_t tile = p.tile_begin + lt;
-    const Segment& seg = p.segs[find_segment(p.segs, p.n_segs, tile)];
-    const uint64_t row0 = (tile - seg.tile_base) * T;  // within the segment
-
+    uint32_t sgi = 0;
     uint32_t st[SPT][4];
     uint64_t h[SPT];  // djb2 / CRC64 accumulators
     uint32_t diff[SPT], ref[SPT];
@@ -331,6 +340,7 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
     for (int c = 0; c < kChunks; c++, j++) {
       const uint32_t s = j % NS;
       mbar_wait(bar_full + 8 * s, (j / NS) & 1, s_abort, p.status);
+      if (c == 0) sgi = s_seg[(j / kChunks) & 1];
       const uint32_t stage = base + s * L::kStageBytes;
 #pragma unroll
       for (int b = 0; b < kBlocksPerChunk; b++) {
@@ -384,6 +394,8 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
       if constexpr (sig_is_weak(SIG)) sig64_words(h[k], st[k]);
     }
 
+    const Segment& seg = p.segs[sgi];
+    const uint64_t row0 = (tile - seg.tile_base) * T;  // within the segment
 #pragma unroll
     for (int k = 0; k < SPT; k++) {
       const uint64_t r = row0 + (uint64_t)(tid + k * C);
