@@ -226,7 +226,7 @@ int frag_scan(DevCtx* ctx, const cv_master* m, const cv_buf* images, uint32_t n_
   {
     Temps tmp(ctx, stream);
     auto body = [&]() -> int {
-      for (auto& e : ev) CV_CUDA(cudaEventCreate(&e));
+      CV_TRY(ctx->take_events(ev, 4));
       CV_CUDA(cudaEventRecord(ev[0], stream));
       uint64_t *tile_ntrip, *tile_off, *seg_off_d, *scratch;
       uint32_t* list;
@@ -304,10 +304,9 @@ int frag_scan(DevCtx* ctx, const cv_master* m, const cv_buf* images, uint32_t n_
     };
     rc = body();
   }
-  for (auto& e : ev)
-    if (e) cudaEventDestroy(e);
+  if (rc != CV_OK) cudaStreamSynchronize(stream);
+  ctx->give_events(ev, 4);
   if (rc != CV_OK) {
-    cudaStreamSynchronize(stream);
     cv_free(r);
     return rc;
   }
@@ -405,7 +404,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
   {
     Temps tmp(ctx, stream);
     auto body = [&]() -> int {
-      for (auto& e : ev) CV_CUDA(cudaEventCreate(&e));
+      CV_TRY(ctx->take_events(ev, 4));
       CV_CUDA(cudaEventRecord(ev[0], stream));
       const size_t nseg = job.segs.size();
       const uint64_t nt = job.n_tiles;
@@ -434,16 +433,19 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         Segment* segs_d;
         uint4* hit_rec;
         uint32_t *tile_nhit, *status;
-        uint64_t *tile_ntrip, *tile_off, *seg_off_d;
-        CV_TRY(tmp.alloc(&segs_d, nseg * sizeof(Segment)));
+        uint64_t *tile_ntrip, *tile_off, *seg_off_d, *off_scratch;
         // compaction works on output tiles of 32 sectors, T / 32 per scan tile
         const uint64_t n_out = nt * (uint64_t)(cfg.T / 32);
-        CV_TRY(tmp.alloc(&hit_rec, n_out * 32 * sizeof(uint4)));
-        CV_TRY(tmp.alloc(&tile_nhit, n_out * 4));
-        CV_TRY(tmp.alloc(&tile_ntrip, n_out * 8));
-        CV_TRY(tmp.alloc(&tile_off, n_out * 8));
+        Carve carve;
+        carve.add(&segs_d, nseg * sizeof(Segment));
+        carve.add(&hit_rec, n_out * 32 * sizeof(uint4));
+        carve.add(&tile_nhit, n_out * 4);
+        carve.add(&tile_ntrip, n_out * 8);
+        carve.add(&tile_off, n_out * 8);
         // seg_off[nseg], total, status, hit sectors, rejected candidates
-        CV_TRY(tmp.alloc(&seg_off_d, (nseg + 4) * 8));
+        carve.add(&seg_off_d, (nseg + 4) * 8);
+        carve.add(&off_scratch, tile_offsets_scratch_words(n_out) * 8);
+        CV_TRY(carve.commit(tmp));
         status = (uint32_t*)(seg_off_d + nseg + 1);
         status_keep = status;
         CV_CUDA(cudaMemsetAsync(status, 0, 24, stream));
@@ -487,8 +489,6 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         uint64_t* total_d = seg_off_d + nseg;
         uint32_t nseg32 = (uint32_t)nseg;
         uint64_t nt_arg = n_out;
-        uint64_t* off_scratch;
-        CV_TRY(tmp.alloc(&off_scratch, tile_offsets_scratch_words(n_out) * 8));
         CV_CUDA((cudaError_t)launch_tile_offsets(tile_ntrip, n_out, tile_off, segs_d, nseg32, (uint32_t)(cfg.T / 32),
                                                  seg_off_d, total_d, off_scratch, stream));
         CV_CUDA((cudaError_t)launch_sum_u32(tile_nhit, n_out, seg_off_d + nseg + 2, ctx->sms, stream));
@@ -567,15 +567,16 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
     };
     rc = body();
   }
-  for (auto& e : ev)
-    if (e) cudaEventDestroy(e);
+  if (rc != CV_OK) {
+    cudaStreamSynchronize(stream);
+    cudaStreamSynchronize(ctx->copy_stream);
+  }
+  ctx->give_events(ev, 4);
   for (int b = 0; b < 2; b++) {
     if (ring_copied[b]) cudaEventDestroy(ring_copied[b]);
     if (ring_free[b]) cudaEventDestroy(ring_free[b]);
   }
   if (rc != CV_OK) {
-    cudaStreamSynchronize(stream);
-    cudaStreamSynchronize(ctx->copy_stream);
     cv_free(r);
     return rc;
   }

@@ -129,6 +129,28 @@ int Temps::alloc_bytes(void** out, size_t bytes) {
   return CV_OK;
 }
 
+int DevCtx::take_events(cudaEvent_t* ev, int n) {
+  for (int i = 0; i < n; i++) ev[i] = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(ev_mutex);
+    for (int i = 0; i < n && !ev_free.empty(); i++) {
+      ev[i] = ev_free.back();
+      ev_free.pop_back();
+    }
+  }
+  for (int i = 0; i < n; i++)
+    if (!ev[i]) CV_CUDA(cudaEventCreate(&ev[i]));
+  return CV_OK;
+}
+
+void DevCtx::give_events(cudaEvent_t* ev, int n) {
+  std::lock_guard<std::mutex> lk(ev_mutex);
+  for (int i = 0; i < n; i++) {
+    if (ev[i]) ev_free.push_back(ev[i]);
+    ev[i] = nullptr;
+  }
+}
+
 int classify(DevCtx* ctx, const void* p, BufKind* kind) {
   cudaPointerAttributes a;
   cudaError_t e = cudaPointerGetAttributes(&a, p);

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include <array>
+#include <mutex>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -66,6 +67,13 @@ struct DevCtx {
 
   // The scan configuration for a table kind when the caller asks for the default.
   int default_config(int kind) const { return cfg_index >= 0 ? cfg_index : preferred_config(kind); }
+
+  // Timing events of finished calls, kept for later calls: creating and destroying four events
+  // per scan cost host time while the device waited for the next call.
+  std::mutex ev_mutex;
+  std::vector<cudaEvent_t> ev_free;
+  int take_events(cudaEvent_t* ev, int n);     // n timing events, reused or new
+  void give_events(cudaEvent_t* ev, int n);   // back for reuse (their work on the device done); nulls them
 };
 
 int get_ctx(DevCtx** out);
@@ -89,6 +97,29 @@ struct Temps {
 
 enum BufKind { kHost = 0, kDevice = 1 };
 int classify(DevCtx* ctx, const void* p, BufKind* kind);
+
+// Several device arrays carved out of one pool allocation (256-byte aligned each), so that a
+// call makes one allocation for its scratch instead of one per array.
+struct Carve {
+  struct Part {
+    void** slot;
+    size_t off;
+  };
+  std::vector<Part> parts;
+  size_t total = 0;
+  template <typename P>
+  void add(P** slot, size_t bytes) {
+    parts.push_back(Part{reinterpret_cast<void**>(slot), total});
+    total += (bytes + 255) & ~(size_t)255;
+  }
+  int commit(Temps& tmp) {
+    void* base = nullptr;
+    const int rc = tmp.alloc_bytes(&base, total);
+    if (rc != CV_OK) return rc;
+    for (const Part& q : parts) *q.slot = static_cast<char*>(base) + q.off;
+    return CV_OK;
+  }
+};
 
 // A 2-D tensor map viewing n_rows sectors at base as u32[n_rows][128] with the staging box of cfg.
 int make_tmap(DevCtx* ctx, const ScanCfg& cfg, const void* base, uint64_t n_rows, CUtensorMap* out);
