@@ -141,7 +141,7 @@ struct ScanParams {
   uint64_t n_tiles;     // tiles of this launch
   TableView tab;
   // scan outputs, indexed by global output tile (32 sectors)
-  uint4* hit_rec;        // 32 records per output tile {lane, post_off, post_cnt, 0}
+  uint4* hit_rec;        // 32 records per output tile {lane, post_off, post_cnt, triples emitted}
   uint32_t* tile_nhit;   // hit sectors per output tile
   uint64_t* tile_ntrip;  // triples per output tile
   uint32_t* status;
