@@ -248,6 +248,49 @@ def test_images_sharing_one_allocation(cv):
             assert_same(r.matches(k), wants[k], str(k))
 
 
+def test_many_segments_and_launches_every_config(cv):
+    """450 images in one scan: 300 of 0-39 sectors carved from one buffer (many segments, most
+    smaller than a tile, so a block's consecutive tiles keep changing segment) and 150 of 1-199
+    sectors, each 16 bytes into a buffer of its own so that each needs its own tensor map (more
+    than one launch carries), interleaved. Every configuration, against the oracle's result for
+    the whole image cut per image (each sector is matched on its own)."""
+    plan = synth.config_plan("small:40000:60:61")
+    full = plan.image_host()
+    files = plan.masters_host()
+    want_all = oracle.match_hash(full, files)
+
+    def want(a, n):
+        sel = want_all[(want_all["disk_sector"] >= a) & (want_all["disk_sector"] < a + n)].copy()
+        sel["disk_sector"] -= a
+        return sel
+
+    rng = np.random.default_rng(61)
+    whole = dev(full)
+    images, wants, keep = [], [], []
+    a = 0
+    for _ in range(300):
+        n = int(rng.integers(0, 40))
+        images.append((whole.data_ptr() + a * SECTOR, n * SECTOR))
+        wants.append(want(a, n))
+        a += n
+    for _ in range(150):
+        n = int(rng.integers(1, 200))
+        s0 = int(rng.integers(0, 40000 - n))
+        buf = dev(np.concatenate([np.zeros(16, np.uint8), full[s0 * SECTOR:(s0 + n) * SECTOR]]))
+        keep.append(buf)
+        images.append((buf.data_ptr() + 16, n * SECTOR))
+        wants.append(want(s0, n))
+    order = rng.permutation(len(images))
+    images = [images[i] for i in order]
+    wants = [wants[i] for i in order]
+    assert sum(w.size for w in wants) > 500
+    with cv.master_build(files) as m:
+        for cfg in range(1, len(cv.kernel_configs()) + 1):
+            with cv.scan(m, images, kernel_config=cfg) as r:
+                for k in range(len(images)):
+                    assert_same(r.matches(k), wants[k], f"configuration {cfg}, image {k}")
+
+
 def _batch_images(n_images, seed):
     """Images of uneven sizes carved out of one device buffer, plus their oracle results."""
     rng = np.random.default_rng(seed)
