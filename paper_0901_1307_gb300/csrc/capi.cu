@@ -489,10 +489,10 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         uint64_t* total_d = seg_off_d + nseg;
         uint32_t nseg32 = (uint32_t)nseg;
         uint64_t nt_arg = n_out;
+        // the offsets, and the sectors with a match summed in the same pass
         CV_CUDA((cudaError_t)launch_tile_offsets(tile_ntrip, n_out, tile_off, segs_d, nseg32, (uint32_t)(cfg.T / 32),
-                                                 seg_off_d, total_d, off_scratch, stream));
-        CV_CUDA((cudaError_t)launch_sum_u32(tile_nhit, n_out, seg_off_d + nseg + 2, ctx->sms, stream));
-        r->launches += 1;
+                                                 seg_off_d, total_d, off_scratch, stream, tile_nhit,
+                                                 seg_off_d + nseg + 2));
         // The expand pass needs an output buffer before the exact count is known on the host.
         // After a scan against the same table it is launched at once, with room for a quarter more
         // than that scan's matches (one wait for the whole call); the exact count then tells

@@ -34,14 +34,26 @@ __device__ __forceinline__ uint64_t block_inclusive_scan(uint64_t x, uint64_t* w
   return x + (warp ? warp_buf[warp - 1] : 0ull);
 }
 
-__global__ void __launch_bounds__(kOffThreads) chunk_sums_kernel(const uint64_t* v, uint64_t n, uint64_t* sums) {
+// Chunk sums of v; with nhit, also the sum of the per-tile hit counts added to *nhit_sum (the
+// disk sectors with at least one match), read in the same pass over the tiles.
+__global__ void __launch_bounds__(kOffThreads) chunk_sums_kernel(const uint64_t* v, uint64_t n, uint64_t* sums,
+                                                                 const uint32_t* nhit, unsigned long long* nhit_sum) {
   __shared__ uint64_t wb[32];
   const uint64_t base = (uint64_t)blockIdx.x * kOffChunk;
   uint64_t s = 0;
+  unsigned long long h = 0;
 #pragma unroll
   for (int k = 0; k < kOffItems; k++) {
     const uint64_t i = base + (uint64_t)k * kOffThreads + threadIdx.x;
-    if (i < n) s += v[i];
+    if (i < n) {
+      s += v[i];
+      if (nhit) h += nhit[i];
+    }
+  }
+  if (nhit) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, d);
+    if ((threadIdx.x & 31) == 0 && h) atomicAdd(nhit_sum, h);
   }
   const uint64_t incl = block_inclusive_scan(s, wb);
   if (threadIdx.x == kOffThreads - 1) sums[blockIdx.x] = incl;
@@ -92,17 +104,6 @@ __global__ void segment_offsets_kernel(const uint64_t* tile_off, uint64_t n, con
     const uint64_t u = segs[s].tile_base * scale;
     seg_off[s] = u < n ? tile_off[u] : *total;
   }
-}
-
-// The sum of n u32 values added to *out: the disk sectors with at least one match, from the
-// per-tile hit counts.
-__global__ void sum_u32_kernel(const uint32_t* v, uint64_t n, unsigned long long* out) {
-  unsigned long long s = 0;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-    s += v[i];
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, d);
-  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
 // Self-test of the bounded wait: one thread waits on an mbarrier that nothing completes. The
@@ -197,19 +198,14 @@ int launch_wait_selftest(uint32_t* status, uint64_t timeout_ns, void* stream) {
 
 uint64_t tile_offsets_scratch_words(uint64_t n_tiles) { return (n_tiles + kOffChunk - 1) / kOffChunk + 1; }
 
-int launch_sum_u32(const uint32_t* v, uint64_t n, uint64_t* out, int sms, void* stream) {
-  if (!n) return 0;
-  const unsigned g = (unsigned)std::min<uint64_t>((n + 255) / 256, (uint64_t)sms * 4);
-  sum_u32_kernel<<<g, 256, 0, (cudaStream_t)stream>>>(v, n, reinterpret_cast<unsigned long long*>(out));
-  return (int)cudaGetLastError();
-}
-
 int launch_tile_offsets(const uint64_t* tile_ntrip, uint64_t n_tiles, uint64_t* tile_off, const Segment* segs,
                         uint32_t n_segs, uint32_t scale, uint64_t* seg_off, uint64_t* total, uint64_t* scratch,
-                        void* stream_) {
+                        void* stream_, const uint32_t* tile_nhit, uint64_t* nhit_sum) {
   cudaStream_t stream = (cudaStream_t)stream_;
   const uint64_t chunks = (n_tiles + kOffChunk - 1) / kOffChunk;
-  if (chunks) chunk_sums_kernel<<<(unsigned)chunks, kOffThreads, 0, stream>>>(tile_ntrip, n_tiles, scratch);
+  if (chunks)
+    chunk_sums_kernel<<<(unsigned)chunks, kOffThreads, 0, stream>>>(
+        tile_ntrip, n_tiles, scratch, tile_nhit, reinterpret_cast<unsigned long long*>(nhit_sum));
   scan_sums_kernel<<<1, kOffThreads, 0, stream>>>(scratch, chunks, total);
   if (chunks) chunk_scan_kernel<<<(unsigned)chunks, kOffThreads, 0, stream>>>(tile_ntrip, n_tiles, scratch, tile_off);
   if (n_segs) segment_offsets_kernel<<<(n_segs + 255) / 256, 256, 0, stream>>>(tile_off, n_tiles, segs, n_segs, scale,
