@@ -508,6 +508,9 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
           r->launches += 1;
         }
         CV_CUDA(cudaMemcpyAsync(seg_off.data(), seg_off_d, (nseg + 4) * 8, cudaMemcpyDeviceToHost, stream));
+        // the call's end unless more work follows (then recorded again after it): in the common
+        // case this one wait for the stream is the call's only one
+        CV_CUDA(cudaEventRecord(ev[3], stream));
         CV_CUDA(cudaStreamSynchronize(stream));
         const uint32_t st = (uint32_t)seg_off[nseg + 1];
         if (st & kStTimeout) return CV_ETIMEOUT;
@@ -539,16 +542,20 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
       for (int64_t i = (int64_t)n_images - 1; i >= 0; i--)
         r->off[i] = (first_seg[i] < first_seg[i + 1]) ? seg_off[first_seg[i]] : r->off[i + 1];
       r->st.matches = total;
+      bool more = !nseg || (total && !expanded_early);  // device work after the first wait
       if (total && !r->on_device) {
         r->host = (MatchOut*)malloc(total * sizeof(MatchOut));
         if (!r->host) return CV_ENOMEM;
         CV_CUDA(cudaMemcpyAsync(r->host, r->dev_out, total * sizeof(MatchOut), cudaMemcpyDeviceToHost, stream));
+        more = true;
       }
       uint32_t st2 = 0;
       if (nseg && total && !expanded_early)
         CV_CUDA(cudaMemcpyAsync(&st2, status_keep, 4, cudaMemcpyDeviceToHost, stream));
-      CV_CUDA(cudaEventRecord(ev[3], stream));
-      CV_CUDA(cudaStreamSynchronize(stream));
+      if (more) {
+        CV_CUDA(cudaEventRecord(ev[3], stream));
+        CV_CUDA(cudaStreamSynchronize(stream));
+      }
       if (st2) return CV_ECORRUPT;
       float ms = 0.f;
       if (nseg) {
