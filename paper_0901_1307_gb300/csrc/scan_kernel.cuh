@@ -325,7 +325,10 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
   uint32_t j = 0;
   for (uint64_t lt = blockIdx.x; lt < p.n_tiles; lt += gridDim.x) {
     const uint64_t tile = p.tile_begin + lt;
+    // No-pad MD5 has no padding compression between the last stage and the lookup to hide the
+    // segment's loads behind, and measured faster finding its segment itself at the tile start.
     uint32_t sgi = 0;
+    if constexpr (SIG == kSigMd5NoPad) sgi = find_segment(p.segs, p.n_segs, tile);
     uint32_t st[SPT][4];
     uint64_t h[SPT];  // djb2 / CRC64 accumulators
     uint32_t diff[SPT], ref[SPT];
@@ -340,7 +343,9 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
     for (int c = 0; c < kChunks; c++, j++) {
       const uint32_t s = j % NS;
       mbar_wait(bar_full + 8 * s, (j / NS) & 1, s_abort, p.status);
-      if (c == 0) sgi = s_seg[(j / kChunks) & 1];
+      if constexpr (SIG != kSigMd5NoPad) {
+        if (c == 0) sgi = s_seg[(j / kChunks) & 1];
+      }
       const uint32_t stage = base + s * L::kStageBytes;
 #pragma unroll
       for (int b = 0; b < kBlocksPerChunk; b++) {
