@@ -96,8 +96,9 @@ int enqueue_run(DevCtx* ctx, int cfg_i, const TableView& tab, const Job& job, co
   if (ev1) CV_CUDA(cudaEventRecordWithFlags(ev1, stream, rec_flags));
   uint64_t* total_d = b.counters_d + nseg;
   CV_CUDA((cudaError_t)launch_tile_offsets(b.tile_ntrip, n_out, b.tile_off, b.segs_d, (uint32_t)nseg,
-                                           (uint32_t)(cfg.T / 32), b.counters_d, total_d, b.off_scratch, stream));
-  if (launches) *launches += 4;
+                                           (uint32_t)(cfg.T / 32), b.counters_d, total_d, b.off_scratch, stream,
+                                           status));
+  if (launches) *launches += 2;
   CV_CUDA((cudaError_t)launch_expand(cfg, b.hit_rec, b.tile_nhit, b.tile_off, n_out, b.segs_d, (uint32_t)nseg, tab,
                                      b.out_d, capacity, status, ctx->sms, stream));
   if (launches) *launches += 1;

@@ -257,8 +257,8 @@ int frag_scan(DevCtx* ctx, const cv_master* m, const cv_buf* images, uint32_t n_
       }
       CV_CUDA(cudaEventRecord(ev[2], stream));
       CV_CUDA((cudaError_t)launch_tile_offsets(tile_ntrip, T, tile_off, segs_d, n_images, 1, seg_off_d,
-                                               seg_off_d + n_images, scratch, stream));
-      r->launches += 4;
+                                               seg_off_d + n_images, scratch, stream, status));
+      r->launches += 2;
       std::vector<uint64_t> seg_off(n_images + 3, 0);
       CV_CUDA(cudaMemcpyAsync(seg_off.data(), seg_off_d, (n_images + 3) * 8, cudaMemcpyDeviceToHost, stream));
       CV_CUDA(cudaStreamSynchronize(stream));
@@ -491,7 +491,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         uint64_t nt_arg = n_out;
         // the offsets, and the sectors with a match summed in the same pass
         CV_CUDA((cudaError_t)launch_tile_offsets(tile_ntrip, n_out, tile_off, segs_d, nseg32, (uint32_t)(cfg.T / 32),
-                                                 seg_off_d, total_d, off_scratch, stream, tile_nhit,
+                                                 seg_off_d, total_d, off_scratch, stream, status, tile_nhit,
                                                  seg_off_d + nseg + 2));
         // The expand pass needs an output buffer before the exact count is known on the host.
         // After a scan against the same table it is launched at once, with room for a quarter more
@@ -535,7 +535,7 @@ int cv_scan(const cv_master* m, const cv_buf* images, uint32_t n_images, const c
         } else {
           expanded_early = true;
         }
-        r->launches += 4;  // the offset pass
+        r->launches += 2;  // the offset pass
       }
       // per-image ranges; an image without sectors gets an empty range
       r->off[n_images] = total;

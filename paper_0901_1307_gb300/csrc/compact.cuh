@@ -2,9 +2,10 @@
 // output offsets by one exclusive scan, then every hit record of every tile is expanded into
 // its (disk_sector, file_id, file_sector) triples. Tiles are in sector order, the records of a
 // tile are in sector order (ballot ranks), and each digest's postings are sorted by
-// (file_id, file_sector), so the output is sorted without a sort and without any wait between
-// thread blocks. (The paper's Section 3.2 writes matches to a host-visible buffer in no stated
-// order; the sorted triple list is this library's output format.)
+// (file_id, file_sector), so the output is sorted without a sort; the only waits between thread
+// blocks are the offset scan's bounded look-back. (The paper's Section 3.2 writes matches to a
+// host-visible buffer in no stated order; the sorted triple list is this library's output
+// format.)
 #pragma once
 #include <stdint.h>
 
@@ -12,10 +13,10 @@
 
 namespace cvk {
 
-// Exclusive scan of the per-tile triple counts in three coalesced passes: chunk sums, a scan
-// of the chunk sums (one block), and the scan within each chunk plus its chunk offset. A fourth
-// small pass reads off each segment's first offset. No block waits on another. (The kernels are
-// in kernels_scan.cu; this header holds the expand pass, instantiated with each configuration.)
+// Exclusive scan of the per-tile triple counts in one pass: each block scans a chunk and adds
+// its predecessors' published sums (decoupled look-back, every wait bounded). A second small pass
+// reads off each segment's first offset. (The kernels are in kernels_scan.cu; this header holds
+// the expand pass, instantiated with each configuration.)
 constexpr int kOffThreads = 1024;
 constexpr int kOffItems = 4;
 constexpr uint64_t kOffChunk = (uint64_t)kOffThreads * kOffItems;

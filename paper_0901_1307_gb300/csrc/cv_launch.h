@@ -48,11 +48,13 @@ uint64_t tile_offsets_scratch_words(uint64_t n_tiles);
 
 // tile_off[i] = sum of tile_ntrip[0..i) over the n_tiles output tiles; *total = sum of all;
 // seg_off[s] = offset of segment s's first output tile (segment tile_base * scale). scratch:
-// tile_offsets_scratch_words(n_tiles) u64 words. With tile_nhit, the sum of the n_tiles hit
-// counts is added to *nhit_sum (device memory, zeroed by the caller). Returns a CUDA error code.
+// tile_offsets_scratch_words(n_tiles) u64 words. status: the scan's status word (kStTimeout if
+// a wait of the pass gives up). With tile_nhit, the sum of the n_tiles hit counts is added to
+// *nhit_sum (device memory, zeroed by the caller). Returns a CUDA error code.
 int launch_tile_offsets(const uint64_t* tile_ntrip, uint64_t n_tiles, uint64_t* tile_off, const Segment* segs,
                         uint32_t n_segs, uint32_t scale, uint64_t* seg_off, uint64_t* total, uint64_t* scratch,
-                        void* stream, const uint32_t* tile_nhit = nullptr, uint64_t* nhit_sum = nullptr);
+                        void* stream, uint32_t* status, const uint32_t* tile_nhit = nullptr,
+                        uint64_t* nhit_sum = nullptr);
 
 // ---------------------------------------------------------------- fragment scans (Section 5)
 uint64_t frag_windows(uint64_t n_bytes);       // 64-byte windows at 4-byte offsets in n_bytes

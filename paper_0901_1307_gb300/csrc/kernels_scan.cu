@@ -34,62 +34,74 @@ __device__ __forceinline__ uint64_t block_inclusive_scan(uint64_t x, uint64_t* w
   return x + (warp ? warp_buf[warp - 1] : 0ull);
 }
 
-// Chunk sums of v; with nhit, also the sum of the per-tile hit counts added to *nhit_sum (the
-// disk sectors with at least one match), read in the same pass over the tiles.
-__global__ void __launch_bounds__(kOffThreads) chunk_sums_kernel(const uint64_t* v, uint64_t n, uint64_t* sums,
-                                                                 const uint32_t* nhit, unsigned long long* nhit_sum) {
+// Exclusive scan of v (n values) into out in one pass, with *total = the sum of all: chunks of
+// kOffChunk values, each scanned by one block; the blocks take chunks in ticket order and publish
+// each chunk's sum (flag 1), then its inclusive prefix (flag 2), in one 64-bit word per chunk,
+// and a block adds up its predecessors' published words back to the first inclusive one
+// (decoupled look-back). A block only waits for chunks taken by blocks that started before it,
+// and each wait is bounded in time (kStTimeout in *status on expiry). state: chunks words, then
+// the ticket, all zero before the launch. With nhit, the sum of the n hit counts is added to
+// *nhit_sum in the same pass.
+constexpr uint64_t kLbAgg = 1ull << 62, kLbIncl = 2ull << 62, kLbValue = (1ull << 62) - 1;
+
+__global__ void __launch_bounds__(kOffThreads) lookback_scan_kernel(const uint64_t* v, uint64_t n, uint64_t* out,
+                                                                    uint64_t* total, uint64_t* state, uint64_t chunks,
+                                                                    const uint32_t* nhit,
+                                                                    unsigned long long* nhit_sum, uint32_t* status) {
   __shared__ uint64_t wb[32];
-  const uint64_t base = (uint64_t)blockIdx.x * kOffChunk;
-  uint64_t s = 0;
+  __shared__ uint64_t s_chunk, s_prefix;
+  if (threadIdx.x == 0) s_chunk = atomicAdd(reinterpret_cast<unsigned long long*>(state + chunks), 1ull);
+  __syncthreads();
+  const uint64_t chunk = s_chunk;
+  const uint64_t first = chunk * kOffChunk + (uint64_t)threadIdx.x * kOffItems;
+  uint64_t x[kOffItems];
+  uint64_t sum = 0;
   unsigned long long h = 0;
 #pragma unroll
   for (int k = 0; k < kOffItems; k++) {
-    const uint64_t i = base + (uint64_t)k * kOffThreads + threadIdx.x;
-    if (i < n) {
-      s += v[i];
-      if (nhit) h += nhit[i];
-    }
+    const bool in = first + k < n;
+    x[k] = in ? v[first + k] : 0ull;
+    sum += x[k];
+    if (nhit && in) h += nhit[first + k];
   }
   if (nhit) {
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) h += __shfl_xor_sync(0xFFFFFFFFu, h, d);
     if ((threadIdx.x & 31) == 0 && h) atomicAdd(nhit_sum, h);
   }
-  const uint64_t incl = block_inclusive_scan(s, wb);
-  if (threadIdx.x == kOffThreads - 1) sums[blockIdx.x] = incl;
-}
-
-// In place: sums[0..m) -> exclusive offsets; *total = the sum of all.
-__global__ void __launch_bounds__(kOffThreads) scan_sums_kernel(uint64_t* sums, uint64_t m, uint64_t* total) {
-  __shared__ uint64_t wb[32];
-  __shared__ uint64_t carry;
-  if (threadIdx.x == 0) carry = 0;
+  const uint64_t incl = block_inclusive_scan(sum, wb);
+  if (threadIdx.x == kOffThreads - 1) {
+    volatile uint64_t* st = state;
+    uint64_t prefix = 0;
+    if (chunk == 0) {
+      st[0] = kLbIncl | incl;
+    } else {
+      st[chunk] = kLbAgg | incl;
+      uint64_t q = chunk - 1;
+      const uint64_t t0 = globaltimer_ns();
+      while (true) {
+        const uint64_t w = st[q];
+        if ((w >> 62) == 2u) {
+          prefix += w & kLbValue;
+          break;
+        }
+        if ((w >> 62) == 1u) {  // chunk 0 always ends in an inclusive word, so q stays >= 0
+          prefix += w & kLbValue;
+          q--;
+          continue;
+        }
+        if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
+          atomicOr(status, kStTimeout);
+          break;
+        }
+      }
+      st[chunk] = kLbIncl | (prefix + incl);
+    }
+    s_prefix = prefix;
+    if (chunk == chunks - 1) *total = prefix + incl;
+  }
   __syncthreads();
-  for (uint64_t base = 0; base < m; base += kOffThreads) {
-    const uint64_t i = base + threadIdx.x;
-    const uint64_t x = i < m ? sums[i] : 0ull;
-    const uint64_t incl = block_inclusive_scan(x, wb);
-    const uint64_t c = carry;
-    if (i < m) sums[i] = c + incl - x;
-    __syncthreads();
-    if (threadIdx.x == kOffThreads - 1) carry = c + incl;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *total = carry;
-}
-
-__global__ void __launch_bounds__(kOffThreads) chunk_scan_kernel(const uint64_t* v, uint64_t n, const uint64_t* offs,
-                                                                 uint64_t* out) {
-  __shared__ uint64_t wb[32];
-  const uint64_t first = (uint64_t)blockIdx.x * kOffChunk + (uint64_t)threadIdx.x * kOffItems;
-  uint64_t x[kOffItems];
-  uint64_t s = 0;
-#pragma unroll
-  for (int k = 0; k < kOffItems; k++) {
-    x[k] = (first + k < n) ? v[first + k] : 0ull;
-    s += x[k];
-  }
-  uint64_t run = block_inclusive_scan(s, wb) - s + offs[blockIdx.x];
+  uint64_t run = s_prefix + incl - sum;
 #pragma unroll
   for (int k = 0; k < kOffItems; k++) {
     if (first + k < n) out[first + k] = run;
@@ -200,14 +212,19 @@ uint64_t tile_offsets_scratch_words(uint64_t n_tiles) { return (n_tiles + kOffCh
 
 int launch_tile_offsets(const uint64_t* tile_ntrip, uint64_t n_tiles, uint64_t* tile_off, const Segment* segs,
                         uint32_t n_segs, uint32_t scale, uint64_t* seg_off, uint64_t* total, uint64_t* scratch,
-                        void* stream_, const uint32_t* tile_nhit, uint64_t* nhit_sum) {
+                        void* stream_, uint32_t* status, const uint32_t* tile_nhit, uint64_t* nhit_sum) {
   cudaStream_t stream = (cudaStream_t)stream_;
   const uint64_t chunks = (n_tiles + kOffChunk - 1) / kOffChunk;
-  if (chunks)
-    chunk_sums_kernel<<<(unsigned)chunks, kOffThreads, 0, stream>>>(
-        tile_ntrip, n_tiles, scratch, tile_nhit, reinterpret_cast<unsigned long long*>(nhit_sum));
-  scan_sums_kernel<<<1, kOffThreads, 0, stream>>>(scratch, chunks, total);
-  if (chunks) chunk_scan_kernel<<<(unsigned)chunks, kOffThreads, 0, stream>>>(tile_ntrip, n_tiles, scratch, tile_off);
+  cudaError_t e;
+  if (chunks) {
+    // the look-back words and the ticket start at zero
+    if ((e = cudaMemsetAsync(scratch, 0, (chunks + 1) * 8, stream)) != cudaSuccess) return (int)e;
+    lookback_scan_kernel<<<(unsigned)chunks, kOffThreads, 0, stream>>>(
+        tile_ntrip, n_tiles, tile_off, total, scratch, chunks, tile_nhit,
+        reinterpret_cast<unsigned long long*>(nhit_sum), status);
+  } else if ((e = cudaMemsetAsync(total, 0, 8, stream)) != cudaSuccess) {
+    return (int)e;
+  }
   if (n_segs) segment_offsets_kernel<<<(n_segs + 255) / 256, 256, 0, stream>>>(tile_off, n_tiles, segs, n_segs, scale,
                                                                                total, seg_off);
   return (int)cudaGetLastError();

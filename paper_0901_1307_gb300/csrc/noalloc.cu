@@ -198,7 +198,7 @@ extern "C" int cv_scan_noalloc(const cv_master* m, const void* image, uint64_t n
   const Segment* segc = seg_d;
   static_assert((kMaxTiles + 4095) / 4096 + 1 <= 1024 / 8, "offset scratch");
   if ((e = (cudaError_t)launch_tile_offsets(tile_ntrip, nt, tile_off, segc, one, (uint32_t)(cfg.T / 32), seg_off_d,
-                                            total_d, (uint64_t*)(sc + kOffSums), stream)) != cudaSuccess)
+                                            total_d, (uint64_t*)(sc + kOffSums), stream, status_d)) != cudaSuccess)
     return fail(e);
   if ((e = (cudaError_t)launch_expand(cfg, hit_rec, tile_nhit, tile_off, nt, segc, one, tab, (MatchOut*)out,
                                       out_capacity, status_d, d->sms, stream)) != cudaSuccess)

@@ -349,7 +349,7 @@ int cv_server::launch_scan(ScanBatch& b, const std::vector<Request*>& work, bool
   CV_TRY(launch_range(ctx, cfg_i, false, job, b.segs_d, 0, b.nseg, p, b.stream));
   CV_CUDA((cudaError_t)launch_tile_offsets(b.tile_ntrip, b.n_out, b.tile_off, b.segs_d, (uint32_t)b.nseg,
                                            (uint32_t)(cfg.T / 32), b.counters_d, b.counters_d + b.nseg,
-                                           b.off_scratch, b.stream));
+                                           b.off_scratch, b.stream, status));
   CV_CUDA(cudaMemcpyAsync(b.counters_h, b.counters_d, (b.nseg + 2) * 8, cudaMemcpyDeviceToHost, b.stream));
   CV_CUDA(cudaEventRecord(b.counts_ready, b.stream));
   b.state = ScanBatch::kCounting;
