@@ -326,9 +326,10 @@ typedef struct {
 int cv_int_peak(cv_int_peak_info* info);
 
 /* Failure-path self-test: a kernel waits on a barrier that nothing completes, using the same
- * bounded wait as the scan kernel with a limit of timeout_us microseconds (1..10^7); the wait
- * gives up, sets the device status word and the kernel returns. Expected result: CV_ETIMEOUT,
- * with the device still usable afterwards. The paper has no counterpart. */
+ * bounded wait as the scan kernel, and the offset scan's look-back waits for a chunk that no
+ * block publishes; each wait has a limit of timeout_us microseconds (1..10^7), gives up, sets
+ * its device status word and lets its kernel return. Expected result: CV_ETIMEOUT (both waits
+ * ran out), with the device still usable afterwards. The paper has no counterpart. */
 int cv_selftest_wait_timeout(uint32_t timeout_us, void* stream);
 
 /*

@@ -60,15 +60,18 @@ int cv_selftest_wait_timeout(uint32_t timeout_us, void* stream_) {
   CV_TRY(get_ctx(&ctx));
   cudaStream_t stream = (cudaStream_t)stream_;
   Temps tmp(ctx, stream);
-  uint32_t* status;
-  CV_TRY(tmp.alloc(&status, 4));
-  CV_CUDA(cudaMemsetAsync(status, 0, 4, stream));
+  uint32_t* status;  // one word per wait
+  uint64_t* words;
+  CV_TRY(tmp.alloc(&status, 8));
+  CV_TRY(tmp.alloc(&words, lookback_selftest_words() * 8));
+  CV_CUDA(cudaMemsetAsync(status, 0, 8, stream));
   CV_CUDA((cudaError_t)launch_wait_selftest(status, (uint64_t)timeout_us * 1000u, stream));
-  uint32_t st = 0;
-  CV_CUDA(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, stream));
+  CV_CUDA((cudaError_t)launch_lookback_selftest(words, status + 1, (uint64_t)timeout_us * 1000u, stream));
+  uint32_t st[2] = {0, 0};
+  CV_CUDA(cudaMemcpyAsync(st, status, 8, cudaMemcpyDeviceToHost, stream));
   CV_CUDA(cudaStreamSynchronize(stream));
-  if (st & kStTimeout) return CV_ETIMEOUT;
-  return st ? CV_ECORRUPT : CV_OK;
+  if ((st[0] | st[1]) & ~kStTimeout) return CV_ECORRUPT;
+  return (st[0] & st[1] & kStTimeout) ? CV_ETIMEOUT : CV_ECORRUPT;  // both waits must run out
 }
 
 int cv_kernel_config_count(void) {

@@ -82,6 +82,10 @@ int frag_emit(const TableView& tab, const uint8_t* image, uint64_t n_bytes, uint
 
 // One block whose single waiting thread waits on an mbarrier nothing completes (bounded by
 // timeout_ns): the status word gets the timeout bit. Returns a CUDA error code.
+// The offset scan's look-back wait running out (words: lookback_selftest_words() u64).
+int launch_lookback_selftest(uint64_t* words, uint32_t* status, uint64_t timeout_ns, void* stream);
+constexpr uint64_t lookback_selftest_words() { return 4 * 4096 + 4; }
+
 int launch_wait_selftest(uint32_t* status, uint64_t timeout_ns, void* stream);
 
 }  // namespace cvk

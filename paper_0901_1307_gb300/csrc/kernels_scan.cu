@@ -39,15 +39,17 @@ __device__ __forceinline__ uint64_t block_inclusive_scan(uint64_t x, uint64_t* w
 // each chunk's sum (flag 1), then its inclusive prefix (flag 2), in one 64-bit word per chunk,
 // and a block adds up its predecessors' published words back to the first inclusive one
 // (decoupled look-back). A block only waits for chunks taken by blocks that started before it,
-// and each wait is bounded in time (kStTimeout in *status on expiry). state: chunks words, then
-// the ticket, all zero before the launch. With nhit, the sum of the n hit counts is added to
+// and each wait is bounded by timeout_ns (kStTimeout in *status on expiry; the block then
+// publishes what it has, so no wait depends on it for longer). state: chunks words, then the
+// ticket, all zero before the launch. With nhit, the sum of the n hit counts is added to
 // *nhit_sum in the same pass.
 constexpr uint64_t kLbAgg = 1ull << 62, kLbIncl = 2ull << 62, kLbValue = (1ull << 62) - 1;
 
 __global__ void __launch_bounds__(kOffThreads) lookback_scan_kernel(const uint64_t* v, uint64_t n, uint64_t* out,
                                                                     uint64_t* total, uint64_t* state, uint64_t chunks,
                                                                     const uint32_t* nhit,
-                                                                    unsigned long long* nhit_sum, uint32_t* status) {
+                                                                    unsigned long long* nhit_sum, uint32_t* status,
+                                                                    uint64_t timeout_ns) {
   __shared__ uint64_t wb[32];
   __shared__ uint64_t s_chunk, s_prefix;
   if (threadIdx.x == 0) s_chunk = atomicAdd(reinterpret_cast<unsigned long long*>(state + chunks), 1ull);
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(kOffThreads) lookback_scan_kernel(const uint64
           q--;
           continue;
         }
-        if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
+        if (globaltimer_ns() - t0 > timeout_ns) {
           atomicOr(status, kStTimeout);
           break;
         }
@@ -208,6 +210,27 @@ int launch_wait_selftest(uint32_t* status, uint64_t timeout_ns, void* stream) {
   return (int)cudaGetLastError();
 }
 
+// Self-test of the look-back's bounded wait: two chunks and one block, whose ticket is set to 1
+// so that it scans chunk 1 and waits for chunk 0, which no block takes. words: 4 * kOffChunk + 4
+// u64 (two chunks of values, two of outputs, the total, two look-back words and the ticket),
+// zeroed here.
+static_assert(lookback_selftest_words() == 2 * kOffChunk + 2 * kOffChunk + 1 + 2 + 1, "self-test buffer");
+
+int launch_lookback_selftest(uint64_t* words, uint32_t* status, uint64_t timeout_ns, void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  uint64_t* v = words;
+  uint64_t* out = v + 2 * kOffChunk;
+  uint64_t* total = out + 2 * kOffChunk;
+  uint64_t* state = total + 1;  // state[0], state[1]: the chunks' words; state[2]: the ticket
+  cudaError_t e = cudaMemsetAsync(words, 0, lookback_selftest_words() * 8, stream);
+  if (e != cudaSuccess) return (int)e;
+  const uint64_t one = 1;
+  if ((e = cudaMemcpyAsync(state + 2, &one, 8, cudaMemcpyHostToDevice, stream)) != cudaSuccess) return (int)e;
+  lookback_scan_kernel<<<1, kOffThreads, 0, stream>>>(v, 2 * kOffChunk, out, total, state, 2, nullptr, nullptr,
+                                                      status, timeout_ns);
+  return (int)cudaGetLastError();
+}
+
 uint64_t tile_offsets_scratch_words(uint64_t n_tiles) { return (n_tiles + kOffChunk - 1) / kOffChunk + 1; }
 
 int launch_tile_offsets(const uint64_t* tile_ntrip, uint64_t n_tiles, uint64_t* tile_off, const Segment* segs,
@@ -221,7 +244,7 @@ int launch_tile_offsets(const uint64_t* tile_ntrip, uint64_t n_tiles, uint64_t* 
     if ((e = cudaMemsetAsync(scratch, 0, (chunks + 1) * 8, stream)) != cudaSuccess) return (int)e;
     lookback_scan_kernel<<<(unsigned)chunks, kOffThreads, 0, stream>>>(
         tile_ntrip, n_tiles, tile_off, total, scratch, chunks, tile_nhit,
-        reinterpret_cast<unsigned long long*>(nhit_sum), status);
+        reinterpret_cast<unsigned long long*>(nhit_sum), status, kWaitTimeoutNs);
   } else if ((e = cudaMemsetAsync(total, 0, 8, stream)) != cudaSuccess) {
     return (int)e;
   }
