@@ -339,10 +339,15 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
       diff[k] = 0;
       ref[k] = 0;
     }
-    // Chunks unrolled in pairs (MD5: fours, measured faster for it alone); with a whole number
-    // of ring turns per tile (j = tiles * kChunks + c) the stage index follows from c and is a
-    // constant within the unrolled group.
-#pragma unroll(SIG == kSigMd5 ? 4 : 2)
+    // Stages unrolled in groups; with a whole number of ring turns per tile (j = tiles * kChunks
+    // + c) the stage index follows from c and is a constant within a group. A group holds at most
+    // four MD5 compressions (two without padding): more code than that ran slower. djb2 and CRC64
+    // blocks are small and go in pairs.
+    constexpr int kCompressions = SPT * kBlocksPerChunk;  // per stage
+    constexpr int kUnroll = (SIG == kSigDjb2 || SIG == kSigCrc64) ? 2
+                            : (SIG == kSigMd5 ? 4 : 2) / kCompressions > 0 ? (SIG == kSigMd5 ? 4 : 2) / kCompressions
+                                                                            : 1;
+#pragma unroll(kUnroll)
     for (int c = 0; c < kChunks; c++, j++) {
       const uint32_t s = (kChunks % NS == 0) ? (uint32_t)c % NS : j % NS;
       mbar_wait(bar_full + 8 * s, (j / NS) & 1, s_abort, p.status);
