@@ -153,7 +153,7 @@ __device__ __forceinline__ void frag_key(const uint32_t* ws, uint32_t w, uint32_
   } else {
     md5_init(d);
     md5_compress<3>(d, X, one);
-    if constexpr (SIG == kSigMd5) md5_compress_block_padding(d);
+    if constexpr (SIG == kSigMd5) md5_compress_block_padding(d, one);
   }
 }
 
@@ -538,7 +538,7 @@ __global__ void frag_digest_kernel(const uint8_t* arena, uint64_t n, uint4* dig,
     } else {
       md5_init(d);
       md5_compress<3>(d, X, one);
-      if constexpr (SIG == kSigMd5) md5_compress_block_padding(d);
+      if constexpr (SIG == kSigMd5) md5_compress_block_padding(d, one);
     }
     dig[m] = make_uint4(d[0], d[1], d[2], d[3]);
     trivial[m] = diff == 0u ? 1 : 0;

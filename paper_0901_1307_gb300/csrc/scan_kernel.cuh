@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
     }
 #pragma unroll
     for (int k = 0; k < SPT; k++) {
-      if constexpr (SIG == kSigMd5) md5_compress_sector_padding(st[k]);
+      if constexpr (SIG == kSigMd5) md5_compress_sector_padding(st[k], p.one);
       if constexpr (sig_is_weak(SIG)) sig64_words(h[k], st[k]);
     }
 
