@@ -343,10 +343,9 @@ __global__ void __launch_bounds__(T / SPT + 32, MINB) scan_kernel(const __grid_c
     // + c) the stage index follows from c and is a constant within a group. A group holds at most
     // four MD5 compressions (two without padding): more code than that ran slower. djb2 and CRC64
     // blocks are small and go in pairs.
-    constexpr int kCompressions = SPT * kBlocksPerChunk;  // per stage
-    constexpr int kUnroll = (SIG == kSigDjb2 || SIG == kSigCrc64) ? 2
-                            : (SIG == kSigMd5 ? 4 : 2) / kCompressions > 0 ? (SIG == kSigMd5 ? 4 : 2) / kCompressions
-                                                                            : 1;
+    constexpr int kCompressions = SPT * kBlocksPerChunk;  // MD5 compressions per stage
+    constexpr int kGroupMax = SIG == kSigMd5 ? 4 : 2;     // per unrolled group
+    constexpr int kUnroll = sig_is_weak(SIG) ? 2 : (kGroupMax >= kCompressions ? kGroupMax / kCompressions : 1);
 #pragma unroll(kUnroll)
     for (int c = 0; c < kChunks; c++, j++) {
       const uint32_t s = (kChunks % NS == 0) ? (uint32_t)c % NS : j % NS;
