@@ -75,8 +75,8 @@ __device__ __forceinline__ uint32_t mad_one_imm(uint32_t one, uint32_t z) {
 // pipe. The lop3 and the rotation run on the integer ALU pipe, which otherwise also carries
 // both additions; moving a share of them to the FMA pipe balances the two pipes. PIPE 0: none;
 // 1: every third operation; 2: every other one; 3: two of three (and the third adds T[i] on the
-// FMA pipe, then X[k] and g in one three-input add: 0.5% faster on the sector scan, 1.7% without
-// padding, than both additions on the ALU); 4: all.
+// FMA pipe, then X[k] and g in one three-input add: 1.7% faster for MD5 without padding than both
+// additions on the ALU, within run-to-run variation for the full sector MD5); 4: all.
 template <int I, int PIPE>
 __host__ __device__ constexpr bool md5_fma_adds() {
   return PIPE == 4 || (PIPE == 1 && I % 3 == 0) || (PIPE == 2 && (I & 1)) || (PIPE == 3 && I % 3 != 0);
